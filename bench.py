@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the MX-scaled low-precision 2D FFT on GB300.
+
+One step = the whole hot path over one batch: the forward MX-FFT of a batch of
+phantom k-space slices plus the round trip (forward then inverse) of the
+matching image-domain batch: 3 transforms of every slice.  The value is
+points x transforms per second (Mpts/s) of the whole job; inputs are resident
+in HBM when the timed region starts and the L2 is flushed (a 256 MiB write)
+between timed steps.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl mxfft|reference]
+
+Under torchrun each rank runs the full batch on its own GPU (weak scaling, no
+collective on the data path; the only collectives are the barrier and the
+max-over-ranks of the timings).  --impl reference times the CPU oracle on the
+host cores instead.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MXFP8 2D-FFT Mpts/s, % HBM roofline, NRMSE vs FP64, serving p50/p99"
+
+WORKLOADS = {
+    "batch64_256x256": dict(n0=256, n1=256, nslices=64, ncoils=1, fmt="e4m3", k=32, config_id=2,
+                            desc="64 slices 256x256 complex64 phantom k-space, MXFP8 e4m3, "
+                                 "k=32, tau=1e-3; forward + round trip"),
+    "single_128x128": dict(n0=128, n1=128, nslices=1, ncoils=1, fmt="e4m3", k=32, config_id=1,
+                           desc="single 128x128 phantom, MXFP8 e4m3, k=32; forward + round trip"),
+    "multicoil_16x32_512x512": dict(n0=512, n1=512, nslices=32, ncoils=16, fmt="e4m3", k=32,
+                                    config_id=3, desc="16 coils x 32 slices 512x512, MXFP8 e4m3, "
+                                                      "k=32; forward + round trip"),
+    "large_8_2048x2048": dict(n0=2048, n1=2048, nslices=8, ncoils=1, fmt="e4m3", k=32,
+                              config_id=5, desc="8 x 2048x2048 phantoms, MXFP8 e4m3, k=32; "
+                                                "forward + round trip"),
+}
+DEFAULT_WORKLOAD = "batch64_256x256"
+TRANSFORMS_PER_STEP = 3          # forward + (forward + inverse) of the round trip
+ALG_BYTES_PER_PT = 16            # read complex64 once + write once, per transform
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["mxfft", "reference"], default="mxfft")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(w, rank):
+    from paper_2512_04317_gb300 import phantom
+    # each rank gets its own slices (weak scaling): distinct config seeds
+    cid = w["config_id"] * 1000 + rank
+    ksp = phantom.mri_batch(w["n0"], w["n1"], w["nslices"], w["ncoils"], config_id=cid)
+    img = phantom.mri_batch(w["n0"], w["n1"], w["nslices"], w["ncoils"], config_id=cid,
+                            domain="image")
+    return ksp, img
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_04317_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload, pts_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    ent = rec.get(kernel, {})
+    if ent.get("source_digest") != source_digest():
+        return None
+    per_pt = ent.get("dram_bytes_per_point_per_launch")
+    return None if per_pt is None else float(per_pt) * pts_per_launch
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def run_reference(args, w, world, rank):
+    """The CPU oracle timed on the host cores on a bounded sample per step."""
+    if world > 1 and rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2512_04317_gb300 import phantom
+    oracle.build()
+    cores = oracle.num_threads()
+    ns = min(w["nslices"] * w["ncoils"], max(cores, 1))
+    n0, n1 = w["n0"], w["n1"]
+    if n0 * n1 >= 1 << 20:
+        ns = 1
+    ksp = phantom.mri_batch(n0, n1, ns, 1, config_id=w["config_id"])
+    img = phantom.mri_batch(n0, n1, ns, 1, config_id=w["config_id"], domain="image")
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.mxfft2d(ksp, w["fmt"], w["k"], op="forward")
+        oracle.mxfft2d(img, w["fmt"], w["k"], op="roundtrip")
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    pts = ns * n0 * n1 * TRANSFORMS_PER_STEP
+    value = pts * len(times) / total / 1e6
+    sample = f"{ns} of {w['nslices'] * w['ncoils']} slices per step, forward + round trip"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Mpts/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(w, ksp, img):
+    import oracle
+    cores = oracle.num_threads()
+    ns = ksp.shape[0]
+    n0, n1 = w["n0"], w["n1"]
+    # bounded sample: about 10-30 s of CPU work
+    per_slice_core_s = 0.3 * (n0 * n1) / 65536 * max(1.0, (n0 * n1) ** 0.5 / 256) ** 0.1
+    ns = int(max(1, min(ns, 25.0 / per_slice_core_s)))
+    t0 = time.perf_counter()
+    oracle.mxfft2d(ksp[:ns], w["fmt"], w["k"], op="forward")
+    oracle.mxfft2d(img[:ns], w["fmt"], w["k"], op="roundtrip")
+    dt = time.perf_counter() - t0
+    return {"value": ns * n0 * n1 * TRANSFORMS_PER_STEP / dt / 1e6, "unit": "Mpts/s",
+            "cores": cores, "kind": "oracle",
+            "sample": f"{ns} of {ksp.shape[0]} slices, forward + round trip, {dt:.2f} s wall"}
+
+
+def accuracy(plan, xk, xi, torch):
+    """NRMSE / PSNR of the forward and round trip against FP64 (cuFFT double)."""
+    y = plan.forward(xk)
+    z = plan.roundtrip(xi)
+    ref = torch.fft.fft2(xk.to(torch.complex128))
+    def nrmse(a, r):
+        return float(torch.linalg.vector_norm((a.to(torch.complex128) - r).flatten()) /
+                     torch.linalg.vector_norm(r.flatten()))
+    def psnr(a, r):
+        err = (a.to(torch.complex128) - r).abs()
+        rms = float(torch.sqrt(torch.mean(err ** 2)))
+        return 20.0 * float(torch.log10(r.abs().max() / rms))
+    xi64 = xi.to(torch.complex128)
+    return {"forward_nrmse": nrmse(y, ref), "forward_psnr_db": psnr(y, ref),
+            "roundtrip_nrmse": nrmse(z, xi64), "roundtrip_psnr_db": psnr(z, xi64)}
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, w, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_04317_gb300 import build as _b
+    from paper_2512_04317_gb300 import mxfft
+    _b.build()
+    mxfft.load()
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n0, n1 = w["n0"], w["n1"]
+    ksp_np, img_np = make_inputs(w, rank)
+    batch = ksp_np.shape[0]
+    pts = batch * n0 * n1
+    xk = torch.from_numpy(ksp_np).to(dev)
+    xi = torch.from_numpy(img_np).to(dev)
+    yk = torch.empty_like(xk)
+    yi = torch.empty_like(xi)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"])
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward(xk, out=yk)
+        plan.roundtrip(xi, out=yi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, L2 flushed between them ----------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_ms = float(t.item())
+    ms_per_step = t_ms / args.steps
+    value = world * pts * TRANSFORMS_PER_STEP * args.steps / (t_ms * 1e-3) / 1e6
+    launches_per_step = 3 + 5
+
+    # ---- per-kernel device time (event pairs on the launch stream) -----------
+    mxfft.mxfft_profile(plan.handle, True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        step()
+    torch.cuda.synchronize()
+    mxfft.mxfft_profile(plan.handle, False)
+    prof = mxfft.mxfft_profile_read(plan.handle)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    avg_ms = dom_ms / max(dom_n, 1)
+    bytes_per_launch = ALG_BYTES_PER_PT * pts if dom == "pass_kernel" else 8 * pts
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    peak, peak_src = load_peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(dom, args.workload,
+                                                                      pts),
+                "kernel": dom, "avg_launch_ms": avg_ms, "peak_source": peak_src,
+                "kernel_share": {k: v[0] / max(sum(x[0] for x in prof.values()), 1e-12)
+                                 for k, v in prof.items()}}
+    whole = pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (ms_per_step * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers ------------------
+    hk = torch.from_numpy(ksp_np).pin_memory()
+    hi = torch.from_numpy(img_np).pin_memory()
+    ok = torch.empty_like(hk).pin_memory()
+    oi = torch.empty_like(hi).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for i in range(2):
+        xk.copy_(hk, non_blocking=True); xi.copy_(hi, non_blocking=True)
+        step()
+        ok.copy_(yk, non_blocking=True); oi.copy_(yi, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for i in range(e2e_steps):
+        xk.copy_(hk, non_blocking=True)
+        xi.copy_(hi, non_blocking=True)
+        step()
+        ok.copy_(yk, non_blocking=True)
+        oi.copy_(yi, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * pts * TRANSFORMS_PER_STEP * e2e_steps / (float(te.item()) * 1e-3) / 1e6
+    bytes_io = 2 * pts * 8
+
+    # ---- accuracy and the FP32 comparator (context) ----------------------------
+    acc = accuracy(plan, xk, xi, torch)
+    st, flags, _ = plan.status()
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    c0.record(stream)
+    for _ in range(reps):
+        for s in range(batch):
+            torch.fft.fft2(xk[s])
+            torch.fft.ifft2(torch.fft.fft2(xi[s]))
+    c1.record(stream)
+    torch.cuda.synchronize()
+    per_slice_fp32 = pts * TRANSFORMS_PER_STEP * reps / (c0.elapsed_time(c1) * 1e-3) / 1e6
+    c0.record(stream)
+    for _ in range(reps):
+        torch.fft.fft2(xk)
+        torch.fft.ifft2(torch.fft.fft2(xi))
+    c1.record(stream)
+    torch.cuda.synchronize()
+    batched_fp32 = pts * TRANSFORMS_PER_STEP * reps / (c0.elapsed_time(c1) * 1e-3) / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, ksp_np, img_np)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": w["desc"], "n0": n0, "n1": n1,
+                       "batch_per_gpu": batch, "format": w["fmt"], "k": w["k"],
+                       "transforms_per_step": TRANSFORMS_PER_STEP,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_roofline_frac_whole_step": whole / peak,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "Mpts/s", "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": launches_per_step * args.steps,
+            "accuracy_vs_fp64": acc,
+            "device_status": st,
+            "fp32_cufft_comparator": {"per_slice_mpts_s": per_slice_fp32,
+                                      "batched_mpts_s": batched_fp32},
+            "clocks": clk,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

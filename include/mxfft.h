@@ -1,0 +1,156 @@
+/*
+ * mxfft.h -- C ABI of the GB300 (sm_103a) MX-scaled low-precision 2D FFT.
+ *
+ * The method is "A mixed precision FFT with applications in MRI"
+ * (arXiv 2512.04317): a single power-of-two global prescale per 2D slice
+ * (Alg. 1, Sec. 2.1), then radix-2 iterative decimation-in-time butterflies
+ * along rows and then columns, where the twiddle multiply of every butterfly
+ * is the MX-scaled complex multiply of Alg. 2 (Sec. 2.2): operands re-encoded
+ * as MX blocks of k real elements sharing a power-of-two scale, quantised to
+ * an OCP element format (FP8 e4m3/e5m2, FP6 e2m3/e3m2, FP4 e2m1), multiplied
+ * in FP32, re-encoded, decoded and accumulated in FP32.  The round trip is
+ * (1/(n0 n1)) F^-1{F{x}} of Eq. (1).
+ *
+ * Conventions shared by every entry point:
+ *   - Data are interleaved complex64 (float re, float im), laid out
+ *     [batch][n0][n1] with n1 contiguous.  "Rows" are the length-n1
+ *     transforms along the contiguous axis; rows are transformed first.
+ *   - Data pointers are DEVICE pointers owned by the caller, 16-byte aligned.
+ *     in == out (in place) is allowed; any other overlap is not.
+ *   - The stream argument is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  Transforms are asynchronous on that stream;
+ *     argument errors are reported synchronously by the return value.
+ *   - Every function returns an mxfft_status (0 = MXFFT_OK).  Nothing aborts,
+ *     prints or throws.  Conditions found on the device (a non-finite
+ *     magnitude in an input) are recorded in the plan and read back with
+ *     mxfft_get_status after the stream has been synchronised.
+ *   - A plan is not safe for concurrent calls from two host threads or on two
+ *     streams at once; use one plan per stream.
+ */
+#ifndef MXFFT_H
+#define MXFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MXFFT_OK = 0,
+    MXFFT_ERR_INVALID = 1,      /* bad argument (size, pointer, alignment, value) */
+    MXFFT_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+    MXFFT_ERR_NOMEM = 3,        /* device or host allocation failed */
+    MXFFT_ERR_CUDA = 4,         /* a CUDA runtime call failed (no device, launch error) */
+    MXFFT_ERR_NONFINITE = 5,    /* an input slice held a non-finite magnitude */
+    MXFFT_ERR_TIMEOUT = 6       /* a bounded device wait gave up */
+} mxfft_status;
+
+/* Element formats of the MX blocks (OCP 8-bit FP and OCP MX v1.0 types). */
+typedef enum {
+    MXFFT_E4M3 = 0,   /* FP8, 3 mantissa bits, largest normal 448 */
+    MXFFT_E5M2 = 1,   /* FP8, 2 mantissa bits, largest normal 57344 */
+    MXFFT_E2M3 = 2,   /* FP6, 3 mantissa bits, largest normal 7.5 */
+    MXFFT_E3M2 = 3,   /* FP6, 2 mantissa bits, largest normal 28 */
+    MXFFT_E2M1 = 4    /* FP4, 1 mantissa bit, largest normal 6 */
+} mxfft_format;
+
+/* Keys of mxfft_set_option. */
+typedef enum {
+    MXFFT_OPT_TAU_MIN = 0,  /* tail floor tau_min of Alg. 1; a power of two.
+                               Default 2^-10 (e4m3, FP6, FP4), 2^-12 (e5m2). */
+    MXFFT_OPT_K_MIN = 1,    /* lower clip k_min of Alg. 1, integer in [-126, 126]; default -126 */
+    MXFFT_OPT_K_MAX = 2     /* upper clip k_max of Alg. 1, integer in [-126, 126]; default 126 */
+} mxfft_option;
+
+typedef struct mxfft_plan_s *mxfft_plan_t;
+
+/*
+ * mxfft_plan -- create a plan for n0 x n1 slices.
+ *   n0, n1  powers of two in [2, 2048].
+ *   format  an mxfft_format.
+ *   k       MX block size in REAL elements (the paper's B, Sec. 2.2: B = 32 is
+ *           "32 real elements", B = 2 one complex value): a power of two in
+ *           [2, 128].  A block holds min(k/2, n/2) complex values: a run of
+ *           consecutive butterflies of one stage of one 1D transform, in the
+ *           order b = g*h + j (g the butterfly group, j the index in it).
+ *   tau     tail percentile of Alg. 1 as a FRACTION in (0, 1) (1e-3 means the
+ *           0.1th percentile); the "lower" order statistic of the nonzero
+ *           magnitudes, rank floor(fl32(tau * fl32(n_nz - 1))).
+ *   target  target peak of Alg. 1; a positive power of two (the paper uses 0.5).
+ *   out     receives the plan (owned by the caller; free with mxfft_destroy).
+ * Allocates the device twiddle tables (prequantised per stage and block at
+ * plan time) and the per-slice statistics; needs a current CUDA device.
+ * Returns MXFFT_ERR_INVALID for out-of-range arguments, MXFFT_ERR_UNSUPPORTED
+ * for a target that is not a power of two, MXFFT_ERR_CUDA / _NOMEM on
+ * device failures.
+ */
+int mxfft_plan(int n0, int n1, int format, int k, float tau, float target,
+               mxfft_plan_t *out);
+
+/* mxfft_set_option -- set an mxfft_option on a plan (see the enum for ranges).
+ * Returns MXFFT_ERR_INVALID for an unknown key or an out-of-range value. */
+int mxfft_set_option(mxfft_plan_t plan, int key, double value);
+
+/*
+ * mxfft_forward -- forward MX-FFT of `batch` slices (Alg. 1, then Alg. 2 in
+ * every butterfly of the row pass and the column pass; Eq. 1 "forward").
+ * Each slice gets its own prescale exponent k (Alg. 1) and its output is
+ * unscaled by 2^-k.  batch >= 0 (0 is a no-op).  The plan's statistics grow
+ * with the largest batch seen (a synchronous device allocation on growth).
+ */
+int mxfft_forward(mxfft_plan_t plan, const void *in, void *out, int batch,
+                  void *stream);
+
+/* mxfft_inverse -- inverse MX-FFT: conjugate twiddles, its own prescale,
+ * unnormalised (Eq. 1 applies 1/N^2 outside the inverse). */
+int mxfft_inverse(mxfft_plan_t plan, const void *in, void *out, int batch,
+                  void *stream);
+
+/*
+ * mxfft_roundtrip -- (1/(n0 n1)) F^-1{F{x}} per slice (Eq. 1 "round-trip"):
+ * the forward output y = 2^-k A is formed, the inverse takes its own prescale
+ * k_inv from y, and one scaling by 2^(-k_inv - log2(n0 n1)) ends it.
+ * `out` also serves as the intermediate buffer.
+ */
+int mxfft_roundtrip(mxfft_plan_t plan, const void *in, void *out, int batch,
+                    void *stream);
+
+/*
+ * mxfft_get_status -- after the stream of the last call has been synchronised
+ * (this function synchronises it), report what the device saw in that call.
+ *   device_flags  nullable; receives bit 0 = some slice had a non-finite
+ *                 magnitude (its k was forced to 0, its output is undefined).
+ *   k_out         nullable; receives the prescale exponents of the last call:
+ *                 [batch] for forward/inverse, [batch][2] (forward k, inverse
+ *                 k) for the round trip.
+ * Returns MXFFT_ERR_NONFINITE when bit 0 is set, else MXFFT_OK (or a CUDA
+ * error).
+ */
+int mxfft_get_status(mxfft_plan_t plan, int *device_flags, int32_t *k_out);
+
+/* mxfft_destroy -- free a plan and its device memory (NULL is a no-op).
+ * Synchronises the device work of the plan first. */
+int mxfft_destroy(mxfft_plan_t plan);
+
+/*
+ * Instrumentation (no counterpart in the paper): per-kernel device time.
+ * mxfft_profile(plan, 1) makes the plan record a CUDA event pair on the
+ * caller's stream around every kernel it launches; mxfft_profile(plan, 0)
+ * stops recording.  mxfft_profile_read synchronises on the recorded events,
+ * writes for each kernel kind i < nkinds the summed device time total_ms[i]
+ * and the launch count launches[i], and clears the records.  Kinds:
+ * 0 = statistics kernel (Alg. 1), 1 = MX butterfly pass kernel (rows and
+ * columns).  Returns MXFFT_ERR_INVALID for a NULL plan or nkinds < 1.
+ */
+int mxfft_profile(mxfft_plan_t plan, int enable);
+int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int nkinds);
+
+/* mxfft_status_string -- static description of a status code. */
+const char *mxfft_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MXFFT_H */

@@ -1,0 +1,75 @@
+// Internal declarations shared by the translation units of libmxfft.
+// Not part of the public C ABI (include/mxfft.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mxfft {
+
+// Element-format constants in the form the device quantiser uses.
+struct FmtParams {
+    int emax;            // unbiased exponent of the largest normal
+    int emin;            // unbiased exponent of the smallest normal
+    int mbits;           // mantissa bits
+    float maxnorm;       // largest finite magnitude
+    uint32_t qmin_bits;  // float bits of 2^emin with a zero mantissa: (emin+127) << 23
+    uint32_t qadd_bits;  // ((23 - mbits) << 23) | 0x400000: turns 2^E into 1.5 * 2^(E+23-mbits)
+};
+
+// Per-slice statistics of Alg. 1 (one record per slice and transform).
+// Zeroed before every transform that accumulates into it.
+struct SliceStats {
+    uint32_t amax_bits;   // bits of max |x| (nonnegative floats order as integers)
+    uint32_t nnz;         // number of nonzero magnitudes
+    uint32_t nonfinite;   // nonzero when some |x| was Inf/NaN
+    uint32_t done;        // CTAs finished (the last one selects k)
+    int32_t k;            // selected prescale exponent
+    uint32_t pad[3];
+    uint32_t hist[280];   // counts of floor(log2 |x|) + 149, bins 0..276
+};
+static_assert(sizeof(SliceStats) % 16 == 0, "SliceStats alignment");
+
+constexpr int kHistBins = 277;   // floor(log2 m) in [-149, 127]
+
+// Integer parameters of the exponent selection (Alg. 1).
+struct KParams {
+    float tau;        // percentile fraction
+    int t_exp;        // target = 2^t_exp
+    int taumin_exp;   // tau_min = 2^taumin_exp
+    int kmin, kmax;   // clip bounds
+};
+
+// Prologue / epilogue modes of a pass.
+enum PassPrologue { PRO_NONE = 0, PRO_PRESCALE = 1 };
+enum PassEpilogue {
+    EPI_RAW = 0,          // store the FP32 stage output
+    EPI_UNSCALE = 1,      // store 2^-k * A
+    EPI_UNSCALE_STATS = 2,// store y = 2^-k * A and accumulate Alg. 1 stats of y
+    EPI_RT_FINAL = 3      // store 2^(-k - lg_total) * A (k of the inverse)
+};
+
+struct PassArgs {
+    const float2* in;
+    float2* out;
+    int n0, n1;           // slice shape
+    int dim;              // 1: transform rows (length n1); 0: columns (length n0)
+    int n, logn;          // transform length and log2
+    int tpc;              // transforms per CTA
+    int m;                // MX block size in butterflies: min(k/2, n/2)
+    const float2* tw;     // twiddle element values, index (h - 1) + j per stage h
+    const int8_t* tws;    // twiddle block scale exponent for the same index
+    SliceStats* st;       // statistics holding k for the prologue / epilogue
+    SliceStats* st_out;   // statistics accumulated by EPI_UNSCALE_STATS
+    int prologue, epilogue;
+    int lg_total;         // log2(n0 * n1) for EPI_RT_FINAL
+    FmtParams fp;
+    KParams kp;           // for the k selection done by EPI_UNSCALE_STATS
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_stats(const float2* x, int batch, int n0, int n1, SliceStats* st,
+                         KParams kp, cudaStream_t s);
+cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s);
+
+}  // namespace mxfft

@@ -1,0 +1,227 @@
+// One pass of the 2D MX-FFT: radix-2 decimation-in-time transforms of length n
+// along rows (dim 1) or columns (dim 0) of each slice, every butterfly being
+// the MX-scaled complex butterfly of Alg. 2.
+//
+// A CTA owns `tpc` whole 1D transforms of one slice, held in shared memory in
+// bit-reversed order.  For every stage a warp takes 64 consecutive butterflies
+// (two per lane: b and b + 32) of one transform; the butterflies of an MX
+// block (m consecutive b, m <= 64) therefore sit in aligned groups of lanes,
+// and the block maxima of Alg. 2 are reduced with xor shuffles.
+#include "mx_device.cuh"
+
+namespace mxfft {
+
+namespace {
+
+constexpr int kPassThreads = 256;
+
+struct Bf {
+    float2 u, v;
+    float xr, xi;   // twiddle element values (block scale removed)
+    int sw;         // twiddle block scale exponent
+    int iu, iv;
+    bool ok;
+};
+
+__device__ __forceinline__ uint32_t abs_max_bits(float a, float b) {
+    return max(__float_as_uint(a) & 0x7fffffffu, __float_as_uint(b) & 0x7fffffffu);
+}
+
+// Reduce a block maximum over the lanes holding one MX block.  For m <= 32 a
+// block is m consecutive lanes of the same half (b or b + 32); for m = 64 it is
+// both halves of all 32 lanes.
+__device__ __forceinline__ void block_max2(uint32_t& a0, uint32_t& a1, int m) {
+    if (m >= 64) { a0 = max(a0, a1); a1 = a0; m = 32; }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        if (o < m) {
+            a0 = max(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+            a1 = max(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+        }
+    }
+}
+
+__device__ __forceinline__ void load_bf(Bf& q, const float2* A, int b, int nb, int h,
+                                        const float2* __restrict__ tw,
+                                        const int8_t* __restrict__ tws) {
+    q.ok = b < nb;
+    if (q.ok) {
+        int j = b & (h - 1);
+        q.iu = 2 * b - j;          // 2h*g + j with g = b / h
+        q.iv = q.iu + h;
+        q.u = A[q.iu];
+        q.v = A[q.iv];
+        float2 w = __ldg(tw + (h - 1) + j);
+        q.xr = w.x;
+        q.xi = w.y;
+        q.sw = __ldg(tws + (h - 1) + j);
+    } else {
+        q.u = q.v = make_float2(0.f, 0.f);
+        q.xr = q.xi = 0.f;
+        q.sw = 0;
+        q.iu = q.iv = 0;
+    }
+}
+
+// Alg. 2 on the pair of butterflies a lane holds, in the element domain:
+//   y = Q(v 2^-s_v)            EncodeBlockMX(v) + MantissasBlock
+//   p = x * y (FP32)           element-space complex multiply
+//   s_out = s_w + s_v; s^ = clamp(s_out + floor(log2 max|p|) - emax)
+//   c = Q(p 2^(s_out - s^))    EncodeFromMantBlock, a fresh MX block
+//   wv = c 2^s^                DecodeBlockMX
+//   (u + wv, u - wv)           FP32
+// The M_max renormalisation of Alg. 2 rescales p and s_out by the same power
+// of two before a fresh re-encode, which leaves c and s^ unchanged, so it is
+// not performed.
+__device__ __forceinline__ void mx_butterfly_pair(float2* A, int b0, int nb, int h, int m,
+                                                  const float2* __restrict__ tw,
+                                                  const int8_t* __restrict__ tws,
+                                                  const FmtParams& fp) {
+    Bf q0, q1;
+    load_bf(q0, A, b0, nb, h, tw, tws);
+    load_bf(q1, A, b0 + 32, nb, h, tw, tws);
+
+    uint32_t a0 = q0.ok ? abs_max_bits(q0.v.x, q0.v.y) : 0u;
+    uint32_t a1 = q1.ok ? abs_max_bits(q1.v.x, q1.v.y) : 0u;
+    block_max2(a0, a1, m);
+    const int sv0 = mx_scale_exp(a0, fp.emax);
+    const int sv1 = mx_scale_exp(a1, fp.emax);
+    const float inv0 = exp2i(-sv0), inv1 = exp2i(-sv1);
+
+    const float y0r = q_elem(__fmul_rn(q0.v.x, inv0), fp);
+    const float y0i = q_elem(__fmul_rn(q0.v.y, inv0), fp);
+    const float y1r = q_elem(__fmul_rn(q1.v.x, inv1), fp);
+    const float y1i = q_elem(__fmul_rn(q1.v.y, inv1), fp);
+
+    const float p0r = __fsub_rn(__fmul_rn(q0.xr, y0r), __fmul_rn(q0.xi, y0i));
+    const float p0i = __fadd_rn(__fmul_rn(q0.xr, y0i), __fmul_rn(q0.xi, y0r));
+    const float p1r = __fsub_rn(__fmul_rn(q1.xr, y1r), __fmul_rn(q1.xi, y1i));
+    const float p1i = __fadd_rn(__fmul_rn(q1.xr, y1i), __fmul_rn(q1.xi, y1r));
+
+    uint32_t P0 = q0.ok ? abs_max_bits(p0r, p0i) : 0u;
+    uint32_t P1 = q1.ok ? abs_max_bits(p1r, p1i) : 0u;
+    block_max2(P0, P1, m);
+
+    const int so0 = q0.sw + sv0, so1 = q1.sw + sv1;
+    const int sh0 = P0 ? min(max(so0 + ilogb_bits(P0) - fp.emax, -127), 127) : so0;
+    const int sh1 = P1 ? min(max(so1 + ilogb_bits(P1) - fp.emax, -127), 127) : so1;
+    const float f0 = exp2i(so0 - sh0), f1 = exp2i(so1 - sh1);
+    const float d0 = exp2i(sh0), d1 = exp2i(sh1);
+
+    if (q0.ok) {
+        const float wr = __fmul_rn(q_elem(__fmul_rn(p0r, f0), fp), d0);
+        const float wi = __fmul_rn(q_elem(__fmul_rn(p0i, f0), fp), d0);
+        A[q0.iu] = make_float2(__fadd_rn(q0.u.x, wr), __fadd_rn(q0.u.y, wi));
+        A[q0.iv] = make_float2(__fsub_rn(q0.u.x, wr), __fsub_rn(q0.u.y, wi));
+    }
+    if (q1.ok) {
+        const float wr = __fmul_rn(q_elem(__fmul_rn(p1r, f1), fp), d1);
+        const float wi = __fmul_rn(q_elem(__fmul_rn(p1i, f1), fp), d1);
+        A[q1.iu] = make_float2(__fadd_rn(q1.u.x, wr), __fadd_rn(q1.u.y, wi));
+        A[q1.iv] = make_float2(__fsub_rn(q1.u.x, wr), __fsub_rn(q1.u.y, wi));
+    }
+}
+
+__global__ void __launch_bounds__(kPassThreads)
+pass_kernel(PassArgs a) {
+    extern __shared__ float2 sm[];
+    __shared__ uint32_t sh_hist[kHistBins];
+    __shared__ uint32_t sh_misc[4];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const int n = a.n, logn = a.logn, tpc = a.tpc;
+    const int per_slice = (a.dim == 1 ? a.n0 : a.n1) / tpc;
+    const int slice = blockIdx.x / per_slice;
+    const int t0 = (blockIdx.x - slice * per_slice) * tpc;
+    const size_t sbase = (size_t)slice * a.n0 * a.n1;
+    const float2* __restrict__ in = a.in + sbase;
+    float2* __restrict__ out = a.out + sbase;
+    const bool stats = a.epilogue == EPI_UNSCALE_STATS;
+    if (stats)
+        for (int b = tid; b < kHistBins; b += nthr) sh_hist[b] = 0;
+
+    // load (with the Alg. 1 prescale on the first pass) in bit-reversed order
+    const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
+    const int total = tpc * n;
+    for (int idx = tid; idx < total; idx += nthr) {
+        int t, i;
+        size_t g;
+        if (a.dim == 1) {
+            t = idx >> logn;
+            i = idx & (n - 1);
+            g = (size_t)(t0 + t) * a.n1 + i;
+        } else {
+            i = idx / tpc;
+            t = idx - i * tpc;
+            g = (size_t)i * a.n1 + t0 + t;
+        }
+        float2 v = in[g];
+        if (a.prologue == PRO_PRESCALE) {
+            v.x = __fmul_rn(v.x, pre);
+            v.y = __fmul_rn(v.y, pre);
+        }
+        sm[t * n + (int)(__brev((unsigned)i) >> (32 - logn))] = v;
+    }
+    __syncthreads();
+
+    const int nb = n >> 1;
+    const int sb_per = (nb + 63) >> 6;
+    const int tasks = tpc * sb_per;
+    for (int s = 0; s < logn; s++) {
+        const int h = 1 << s;
+        for (int task = warp; task < tasks; task += nwarps) {
+            const int t = task / sb_per;
+            const int sb = task - t * sb_per;
+            mx_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.m, a.tw, a.tws, a.fp);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: natural order out
+    float post = 1.0f;
+    if (a.epilogue == EPI_UNSCALE || a.epilogue == EPI_UNSCALE_STATS) post = exp2i(-a.st[slice].k);
+    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
+    StatAcc acc;
+    for (int idx = tid; idx < total; idx += nthr) {
+        int t, i;
+        size_t g;
+        if (a.dim == 1) {
+            t = idx >> logn;
+            i = idx & (n - 1);
+            g = (size_t)(t0 + t) * a.n1 + i;
+        } else {
+            i = idx / tpc;
+            t = idx - i * tpc;
+            g = (size_t)i * a.n1 + t0 + t;
+        }
+        float2 v = sm[t * n + i];
+        if (a.epilogue != EPI_RAW) {
+            v.x = __fmul_rn(v.x, post);
+            v.y = __fmul_rn(v.y, post);
+        }
+        out[g] = v;
+        if (stats) acc.add(v.x, v.y, sh_hist);
+    }
+    if (stats) {
+        __syncthreads();
+        stats_flush_and_select(acc, sh_hist, sh_misc, a.st_out + slice, (uint32_t)per_slice, a.kp);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s) {
+    const int per_slice = (a.dim == 1 ? a.n0 : a.n1) / a.tpc;
+    const size_t smem = (size_t)a.tpc * a.n * sizeof(float2);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             96 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    pass_kernel<<<batch * per_slice, kPassThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mxfft

@@ -1,0 +1,46 @@
+// Alg. 1 statistics pass: per slice, max |x|, the count of nonzero |x| and the
+// histogram of floor(log2 |x|), then (last CTA of the slice) the prescale
+// exponent k.  Reads each complex64 input once with 16-byte loads.
+#include "mx_device.cuh"
+
+namespace mxfft {
+
+namespace {
+
+constexpr int kStatsThreads = 256;
+constexpr int kStatsPtsPerCta = 4096;
+
+__global__ void __launch_bounds__(kStatsThreads)
+stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st,
+             KParams kp, uint32_t ctas_per_slice) {
+    __shared__ uint32_t sh_hist[kHistBins];
+    __shared__ uint32_t sh_misc[4];
+    const int tid = threadIdx.x;
+    const int slice = blockIdx.y;
+    for (int b = tid; b < kHistBins; b += blockDim.x) sh_hist[b] = 0;
+    __syncthreads();
+    const float4* xs = reinterpret_cast<const float4*>(x + (size_t)slice * npts);
+    const int begin = blockIdx.x * kStatsPtsPerCta;
+    const int end = min(begin + kStatsPtsPerCta, npts);
+    StatAcc acc;
+    for (int p = begin + 2 * tid; p < end; p += 2 * blockDim.x) {
+        float4 v = __ldg(xs + (p >> 1));
+        acc.add(v.x, v.y, sh_hist);
+        acc.add(v.z, v.w, sh_hist);
+    }
+    __syncthreads();
+    stats_flush_and_select(acc, sh_hist, sh_misc, st + slice, ctas_per_slice, kp);
+}
+
+}  // namespace
+
+cudaError_t launch_stats(const float2* x, int batch, int n0, int n1, SliceStats* st,
+                         KParams kp, cudaStream_t s) {
+    const int npts = n0 * n1;
+    const uint32_t per = (uint32_t)((npts + kStatsPtsPerCta - 1) / kStatsPtsPerCta);
+    dim3 grid(per, batch);
+    stats_kernel<<<grid, kStatsThreads, 0, s>>>(x, npts, st, kp, per);
+    return cudaGetLastError();
+}
+
+}  // namespace mxfft

@@ -1,0 +1,490 @@
+// Host side of libmxfft: plans, prequantised twiddle tables, the launch
+// sequence of each transform and the C ABI declared in include/mxfft.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mx_internal.h"
+#include "mxfft.h"
+
+using namespace mxfft;
+
+namespace {
+struct ProfRec {
+    int kind;                  // 0 stats, 1 pass
+    cudaEvent_t a, b;
+};
+}  // namespace
+
+struct mxfft_plan_s {
+    int n0, n1, fmt, kblk;
+    float tau;
+    int t_exp;                 // target = 2^t_exp
+    int taumin_exp;            // tau_min = 2^taumin_exp
+    int kmin, kmax;
+    FmtParams fp;
+    int m[2];                  // MX block size in butterflies per axis (0: n0, 1: n1)
+    float2* d_tw[2][2];        // [axis][0 forward, 1 inverse]
+    int8_t* d_tws[2];          // [axis] twiddle block exponents
+    SliceStats* d_st;          // 2 * st_cap records: forward, inverse
+    int st_cap;
+    int last_batch, last_op;   // of the last transform
+    cudaStream_t last_stream;
+    int device;
+    bool prof;                 // record per-kernel event pairs
+    std::vector<ProfRec>* recs;
+};
+
+namespace {
+
+struct FmtHost {
+    int emax, emin, mbits;
+    double maxnorm;
+};
+
+// OCP element formats: unbiased exponents of the largest and smallest normal,
+// mantissa bits and largest finite magnitude.
+bool fmt_host(int code, FmtHost* f) {
+    switch (code) {
+        case MXFFT_E4M3: *f = {8, -6, 3, 448.0}; return true;
+        case MXFFT_E5M2: *f = {15, -14, 2, 57344.0}; return true;
+        case MXFFT_E2M3: *f = {2, 0, 3, 7.5}; return true;
+        case MXFFT_E3M2: *f = {4, -2, 2, 28.0}; return true;
+        case MXFFT_E2M1: *f = {2, 0, 1, 6.0}; return true;
+        default: return false;
+    }
+}
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2(int n) { int l = 0; while ((1 << l) < n) l++; return l; }
+
+// Exponent e if v == 2^e exactly (v > 0), else a sentinel.
+bool exact_pow2_exp(double v, int* e) {
+    if (!(v > 0.0) || !std::isfinite(v)) return false;
+    int ex;
+    double fr = std::frexp(v, &ex);
+    if (fr != 0.5) return false;
+    *e = ex - 1;
+    return true;
+}
+
+// Element rounding of an FP64 value already divided by its block scale:
+// nearest grid value (ties to even), saturating, via the 2^52 add-and-subtract
+// identity: |x| + 1.5 * 2^52 * q lands in a binade whose ulp is the grid
+// spacing q, so the adder rounds half-even onto the grid.
+double q_host(double x, const FmtHost& f) {
+    if (x == 0.0) return x;
+    double a = std::fabs(x);
+    if (a > f.maxnorm) a = f.maxnorm;
+    int ex;
+    std::frexp(a, &ex);
+    int E = ex - 1;
+    if (E < f.emin) E = f.emin;
+    const double c = std::ldexp(1.5, 52 + E - f.mbits);
+    volatile double t = a + c;
+    double r = t - c;
+    return std::copysign(r, x);
+}
+
+// cos and sin of 2 pi j / N for 0 <= j < N/2, reduced to the first octant so
+// that 0, +-1 and +-sqrt(1/2) come out exactly symmetric.
+void unit_root(long j, long N, double* c, double* s) {
+    const double two_pi = 6.283185307179586476925286766559;
+    long j8 = 8 * j;
+    if (j8 <= N) {                       // [0, pi/4]
+        double a = two_pi * (double)j / (double)N;
+        *c = std::cos(a); *s = std::sin(a);
+        if (j8 == N) { *c = *s = std::sqrt(0.5); }
+    } else if (j8 <= 2 * N) {            // (pi/4, pi/2]: angle pi/2 - a
+        double a = two_pi * (double)(N / 4 - j) / (double)N;
+        if (4 * j == N) { *c = 0.0; *s = 1.0; }
+        else { *c = std::sin(a); *s = std::cos(a); }
+    } else if (j8 <= 3 * N) {            // (pi/2, 3pi/4]: angle pi/2 + a
+        double a = two_pi * (double)(j - N / 4) / (double)N;
+        *c = -std::sin(a); *s = std::cos(a);
+        if (j8 == 3 * N) { *c = -std::sqrt(0.5); *s = std::sqrt(0.5); }
+    } else {                             // (3pi/4, pi): angle pi - a
+        double a = two_pi * (double)(N / 2 - j) / (double)N;
+        *c = -std::cos(a); *s = std::sin(a);
+    }
+}
+
+// Prequantised twiddles of one axis of length n with MX blocks of m butterflies:
+// stage h (h = 1, 2, ..., n/2) holds w_j = exp(-2 pi i j / (2h)), j < h, at
+// index (h - 1) + j.  The MX blocks of a stage are the runs of m consecutive
+// butterflies b = g*h + j; for h >= m a block covers j in [j0, j0 + m), for
+// h < m it covers every j of the stage.  Each block gets its shared exponent
+// s_w = floor(log2 max|w component|) - emax and element values Q(w 2^-s_w).
+void build_twiddles(int n, int m, const FmtHost& f, std::vector<float2>& fwd,
+                    std::vector<float2>& inv, std::vector<int8_t>& sw) {
+    fwd.assign(n, make_float2(0.f, 0.f));
+    inv.assign(n, make_float2(0.f, 0.f));
+    sw.assign(n, 0);
+    for (int h = 1; h < n; h <<= 1) {
+        const int bl = h >= m ? m : h;   // j-run per block
+        for (int j0 = 0; j0 < h; j0 += bl) {
+            std::vector<double> cs(bl), sn(bl);
+            double amax = 0.0;
+            for (int jj = 0; jj < bl; jj++) {
+                unit_root(j0 + jj, 2L * h, &cs[jj], &sn[jj]);
+                amax = std::fmax(amax, std::fmax(std::fabs(cs[jj]), std::fabs(sn[jj])));
+            }
+            int ex;
+            std::frexp(amax, &ex);
+            int s = (ex - 1) - f.emax;
+            if (s < -127) s = -127;
+            if (s > 127) s = 127;
+            for (int jj = 0; jj < bl; jj++) {
+                const double xr = q_host(std::ldexp(cs[jj], -s), f);
+                const double xi = q_host(std::ldexp(-sn[jj], -s), f);
+                const int idx = (h - 1) + j0 + jj;
+                fwd[idx] = make_float2((float)xr, (float)xi);
+                inv[idx] = make_float2((float)xr, (float)-xi);
+                sw[idx] = (int8_t)s;
+            }
+        }
+    }
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MXFFT_OK;
+    if (e == cudaErrorMemoryAllocation) return MXFFT_ERR_NOMEM;
+    return MXFFT_ERR_CUDA;
+}
+
+void free_plan_device(mxfft_plan_s* p) {
+    for (int a = 0; a < 2; a++) {
+        for (int d = 0; d < 2; d++) if (p->d_tw[a][d]) cudaFree(p->d_tw[a][d]);
+        if (p->d_tws[a]) cudaFree(p->d_tws[a]);
+    }
+    if (p->d_st) cudaFree(p->d_st);
+}
+
+int ensure_stats(mxfft_plan_s* p, int batch) {
+    if (batch <= p->st_cap) return MXFFT_OK;
+    int cap = p->st_cap ? p->st_cap : 1;
+    while (cap < batch) cap *= 2;
+    if (p->d_st) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(p->d_st);
+        p->d_st = nullptr;
+        p->st_cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&p->d_st, sizeof(SliceStats) * 2 * (size_t)cap);
+    if (e != cudaSuccess) { p->d_st = nullptr; return cuda_status(e); }
+    p->st_cap = cap;
+    return MXFFT_OK;
+}
+
+KParams kparams(const mxfft_plan_s* p) {
+    KParams kp;
+    kp.tau = p->tau;
+    kp.t_exp = p->t_exp;
+    kp.taumin_exp = p->taumin_exp;
+    kp.kmin = p->kmin;
+    kp.kmax = p->kmax;
+    return kp;
+}
+
+PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.n0 = p->n0;
+    a.n1 = p->n1;
+    a.dim = dim;
+    a.n = dim == 1 ? p->n1 : p->n0;
+    a.logn = ilog2(a.n);
+    const int other = dim == 1 ? p->n0 : p->n1;
+    int tpc = 8192 / a.n;
+    if (tpc < 1) tpc = 1;
+    if (tpc > other) tpc = other;
+    a.tpc = tpc;
+    a.m = p->m[dim];
+    a.tw = p->d_tw[dim][dir];
+    a.tws = p->d_tws[dim];
+    a.fp = p->fp;
+    a.kp = kparams(p);
+    a.lg_total = ilog2(p->n0) + ilog2(p->n1);
+    return a;
+}
+
+bool aligned16(const void* q) { return ((uintptr_t)q & 15u) == 0; }
+
+// Event pair around one launch when profiling is on (nullptr otherwise).
+ProfRec* prof_begin(mxfft_plan_s* p, int kind, cudaStream_t s) {
+    if (!p->prof) return nullptr;
+    ProfRec rec{kind, nullptr, nullptr};
+    if (cudaEventCreate(&rec.a) != cudaSuccess) return nullptr;
+    if (cudaEventCreate(&rec.b) != cudaSuccess) { cudaEventDestroy(rec.a); return nullptr; }
+    cudaEventRecord(rec.a, s);
+    p->recs->push_back(rec);
+    return &p->recs->back();
+}
+
+void prof_end(ProfRec* r, cudaStream_t s) {
+    if (r) cudaEventRecord(r->b, s);
+}
+
+cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
+    ProfRec* r = prof_begin(p, 1, s);
+    cudaError_t e = launch_pass(a, batch, s);
+    prof_end(r, s);
+    return e;
+}
+
+void prof_clear(mxfft_plan_s* p) {
+    if (!p->recs) return;
+    for (ProfRec& r : *p->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    p->recs->clear();
+}
+
+// op: 0 forward, 1 inverse, 2 round trip
+int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int op) {
+    if (!p || batch < 0) return MXFFT_ERR_INVALID;
+    if (batch == 0) return MXFFT_OK;
+    if (!in || !out || !aligned16(in) || !aligned16(out)) return MXFFT_ERR_INVALID;
+    const size_t bytes = (size_t)batch * p->n0 * p->n1 * sizeof(float2);
+    const char* ci = (const char*)in;
+    const char* co = (const char*)out;
+    if (ci != co && ci < co + bytes && co < ci + bytes) return MXFFT_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return MXFFT_ERR_CUDA;
+    int rc = ensure_stats(p, batch);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    SliceStats* st_f = p->d_st;
+    SliceStats* st_i = p->d_st + p->st_cap;
+    cudaError_t e = cudaMemsetAsync(st_f, 0, sizeof(SliceStats) * (size_t)batch, s);
+    if (e == cudaSuccess && op == 2) e = cudaMemsetAsync(st_i, 0, sizeof(SliceStats) * (size_t)batch, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const float2* x = (const float2*)in;
+    float2* y = (float2*)out;
+    const int dir0 = op == 1 ? 1 : 0;
+    ProfRec* r = prof_begin(p, 0, s);
+    e = launch_stats(x, batch, p->n0, p->n1, st_f, kparams(p), s);
+    prof_end(r, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    PassArgs rows = pass_args(p, 1, dir0, x, y);
+    rows.st = st_f;
+    rows.prologue = PRO_PRESCALE;
+    rows.epilogue = EPI_RAW;
+    if ((e = timed_pass(p, rows, batch, s)) != cudaSuccess) return cuda_status(e);
+    PassArgs cols = pass_args(p, 0, dir0, y, y);
+    cols.st = st_f;
+    cols.prologue = PRO_NONE;
+    cols.epilogue = op == 2 ? EPI_UNSCALE_STATS : EPI_UNSCALE;
+    cols.st_out = st_i;
+    if ((e = timed_pass(p, cols, batch, s)) != cudaSuccess) return cuda_status(e);
+    if (op == 2) {
+        PassArgs r2 = pass_args(p, 1, 1, y, y);
+        r2.st = st_i;
+        r2.prologue = PRO_PRESCALE;
+        r2.epilogue = EPI_RAW;
+        if ((e = timed_pass(p, r2, batch, s)) != cudaSuccess) return cuda_status(e);
+        PassArgs c2 = pass_args(p, 0, 1, y, y);
+        c2.st = st_i;
+        c2.prologue = PRO_NONE;
+        c2.epilogue = EPI_RT_FINAL;
+        if ((e = timed_pass(p, c2, batch, s)) != cudaSuccess) return cuda_status(e);
+    }
+    p->last_batch = batch;
+    p->last_op = op;
+    p->last_stream = s;
+    return MXFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft_plan_t* out) {
+    if (!out) return MXFFT_ERR_INVALID;
+    *out = nullptr;
+    FmtHost f;
+    if (!is_pow2(n0) || !is_pow2(n1) || n0 < 2 || n1 < 2 || n0 > 2048 || n1 > 2048)
+        return MXFFT_ERR_INVALID;
+    if (!fmt_host(format, &f)) return MXFFT_ERR_INVALID;
+    if (!is_pow2(k) || k < 2 || k > 128) return MXFFT_ERR_INVALID;
+    if (!(tau > 0.0f && tau < 1.0f)) return MXFFT_ERR_INVALID;
+    if (!(target > 0.0f) || !std::isfinite(target)) return MXFFT_ERR_INVALID;
+    int t_exp;
+    if (!exact_pow2_exp((double)target, &t_exp)) return MXFFT_ERR_UNSUPPORTED;
+
+    mxfft_plan_s* p = new (std::nothrow) mxfft_plan_s;
+    if (!p) return MXFFT_ERR_NOMEM;
+    std::memset(p, 0, sizeof(*p));
+    p->n0 = n0;
+    p->n1 = n1;
+    p->fmt = format;
+    p->kblk = k;
+    p->tau = tau;
+    p->t_exp = t_exp;
+    p->taumin_exp = format == MXFFT_E5M2 ? -12 : -10;
+    p->kmin = -126;
+    p->kmax = 126;
+    p->fp.emax = f.emax;
+    p->fp.emin = f.emin;
+    p->fp.mbits = f.mbits;
+    p->fp.maxnorm = (float)f.maxnorm;
+    p->fp.qmin_bits = (uint32_t)(f.emin + 127) << 23;
+    p->fp.qadd_bits = ((uint32_t)(23 - f.mbits) << 23) | 0x400000u;
+    p->recs = new (std::nothrow) std::vector<ProfRec>();
+    if (!p->recs) { delete p; return MXFFT_ERR_NOMEM; }
+    p->recs->reserve(1024);
+    p->m[0] = std::min(k / 2, n0 / 2);
+    p->m[1] = std::min(k / 2, n1 / 2);
+
+    int rc = MXFFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return MXFFT_ERR_CUDA; }
+    for (int axis = 0; axis < 2 && rc == MXFFT_OK; axis++) {
+        const int n = axis == 0 ? n0 : n1;
+        std::vector<float2> fw, iv;
+        std::vector<int8_t> sw;
+        build_twiddles(n, p->m[axis], f, fw, iv, sw);
+        for (int d = 0; d < 2 && rc == MXFFT_OK; d++) {
+            const std::vector<float2>& t = d == 0 ? fw : iv;
+            rc = cuda_status(cudaMalloc(&p->d_tw[axis][d], sizeof(float2) * t.size()));
+            if (rc == MXFFT_OK)
+                rc = cuda_status(cudaMemcpy(p->d_tw[axis][d], t.data(), sizeof(float2) * t.size(),
+                                            cudaMemcpyHostToDevice));
+        }
+        if (rc == MXFFT_OK) rc = cuda_status(cudaMalloc(&p->d_tws[axis], sw.size()));
+        if (rc == MXFFT_OK)
+            rc = cuda_status(cudaMemcpy(p->d_tws[axis], sw.data(), sw.size(), cudaMemcpyHostToDevice));
+    }
+    if (rc == MXFFT_OK) rc = ensure_stats(p, 1);
+    if (rc != MXFFT_OK) {
+        free_plan_device(p);
+        delete p->recs;
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return MXFFT_OK;
+}
+
+int mxfft_set_option(mxfft_plan_t p, int key, double value) {
+    if (!p) return MXFFT_ERR_INVALID;
+    switch (key) {
+        case MXFFT_OPT_TAU_MIN: {
+            int e;
+            if (!exact_pow2_exp(value, &e) || e < -149 || e > 127) return MXFFT_ERR_INVALID;
+            p->taumin_exp = e;
+            return MXFFT_OK;
+        }
+        case MXFFT_OPT_K_MIN:
+        case MXFFT_OPT_K_MAX: {
+            if (value != std::floor(value) || value < -126 || value > 126) return MXFFT_ERR_INVALID;
+            const int v = (int)value;
+            if (key == MXFFT_OPT_K_MIN) p->kmin = v; else p->kmax = v;
+            return MXFFT_OK;
+        }
+        default:
+            return MXFFT_ERR_INVALID;
+    }
+}
+
+int mxfft_forward(mxfft_plan_t p, const void* in, void* out, int batch, void* stream) {
+    return run(p, in, out, batch, stream, 0);
+}
+
+int mxfft_inverse(mxfft_plan_t p, const void* in, void* out, int batch, void* stream) {
+    return run(p, in, out, batch, stream, 1);
+}
+
+int mxfft_roundtrip(mxfft_plan_t p, const void* in, void* out, int batch, void* stream) {
+    return run(p, in, out, batch, stream, 2);
+}
+
+int mxfft_get_status(mxfft_plan_t p, int* device_flags, int32_t* k_out) {
+    if (!p) return MXFFT_ERR_INVALID;
+    if (device_flags) *device_flags = 0;
+    if (p->last_batch == 0) return MXFFT_OK;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int b = p->last_batch;
+    std::vector<SliceStats> hf(b), hi;
+    e = cudaMemcpy(hf.data(), p->d_st, sizeof(SliceStats) * b, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (p->last_op == 2) {
+        hi.resize(b);
+        e = cudaMemcpy(hi.data(), p->d_st + p->st_cap, sizeof(SliceStats) * b, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    int flags = 0;
+    for (int i = 0; i < b; i++) {
+        if (hf[i].nonfinite || (p->last_op == 2 && hi[i].nonfinite)) flags |= 1;
+        if (k_out) {
+            if (p->last_op == 2) {
+                k_out[2 * i] = hf[i].k;
+                k_out[2 * i + 1] = hi[i].k;
+            } else {
+                k_out[i] = hf[i].k;
+            }
+        }
+    }
+    if (device_flags) *device_flags = flags;
+    return (flags & 1) ? MXFFT_ERR_NONFINITE : MXFFT_OK;
+}
+
+int mxfft_destroy(mxfft_plan_t p) {
+    if (!p) return MXFFT_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev == p->device) cudaDeviceSynchronize();
+    prof_clear(p);
+    delete p->recs;
+    free_plan_device(p);
+    delete p;
+    return MXFFT_OK;
+}
+
+int mxfft_profile(mxfft_plan_t p, int enable) {
+    if (!p) return MXFFT_ERR_INVALID;
+    p->prof = enable != 0;
+    return MXFFT_OK;
+}
+
+int mxfft_profile_read(mxfft_plan_t p, double* total_ms, int* launches, int nkinds) {
+    if (!p || nkinds < 1) return MXFFT_ERR_INVALID;
+    for (int i = 0; i < nkinds; i++) {
+        if (total_ms) total_ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    int rc = MXFFT_OK;
+    for (ProfRec& r : *p->recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) { rc = cuda_status(e); break; }
+        if (r.kind < nkinds) {
+            if (total_ms) total_ms[r.kind] += ms;
+            if (launches) launches[r.kind] += 1;
+        }
+    }
+    prof_clear(p);
+    return rc;
+}
+
+const char* mxfft_status_string(int status) {
+    switch (status) {
+        case MXFFT_OK: return "ok";
+        case MXFFT_ERR_INVALID: return "invalid argument";
+        case MXFFT_ERR_UNSUPPORTED: return "unsupported request";
+        case MXFFT_ERR_NOMEM: return "out of memory";
+        case MXFFT_ERR_CUDA: return "CUDA runtime error";
+        case MXFFT_ERR_NONFINITE: return "non-finite input magnitude";
+        case MXFFT_ERR_TIMEOUT: return "bounded device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+"""Python binding of libmxfft (include/mxfft.h): argument marshalling only.
+
+Every step of the transform runs in the CUDA library; this module passes
+pointers, sizes and the current torch stream through ctypes.  PyTorch is used
+for device memory and streams only.  If the library has not been built the
+first call raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+MXFFT_OK = 0
+MXFFT_ERR_INVALID = 1
+MXFFT_ERR_UNSUPPORTED = 2
+MXFFT_ERR_NOMEM = 3
+MXFFT_ERR_CUDA = 4
+MXFFT_ERR_NONFINITE = 5
+MXFFT_ERR_TIMEOUT = 6
+
+FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4}
+OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX = 0, 1, 2
+
+# every symbol include/mxfft.h declares
+EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
+           "mxfft_roundtrip", "mxfft_get_status", "mxfft_destroy", "mxfft_profile",
+           "mxfft_profile_read", "mxfft_status_string")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MxfftError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load libmxfft.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmxfft.so is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, I, F, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+        lib.mxfft_plan.argtypes = [I, I, I, I, F, F, ctypes.POINTER(P)]
+        lib.mxfft_set_option.argtypes = [P, I, D]
+        for name in ("mxfft_forward", "mxfft_inverse", "mxfft_roundtrip"):
+            getattr(lib, name).argtypes = [P, P, P, I, P]
+        lib.mxfft_get_status.argtypes = [P, P, P]
+        lib.mxfft_destroy.argtypes = [P]
+        lib.mxfft_profile.argtypes = [P, I]
+        lib.mxfft_profile_read.argtypes = [P, P, P, I]
+        lib.mxfft_status_string.argtypes = [I]
+        lib.mxfft_status_string.restype = ctypes.c_char_p
+        for name in EXPORTS[:-1]:
+            getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().mxfft_status_string(int(status)).decode()
+    except Exception:
+        return f"status {status}"
+
+
+# ---- thin C-ABI wrappers with the header's names -------------------------------
+
+def mxfft_plan(n0: int, n1: int, fmt, k: int, tau: float, target: float) -> int:
+    h = ctypes.c_void_p()
+    st = load().mxfft_plan(int(n0), int(n1), _fmt(fmt), int(k), float(tau), float(target),
+                           ctypes.byref(h))
+    if st:
+        raise MxfftError(st, "mxfft_plan")
+    return h.value
+
+
+def mxfft_set_option(plan: int, key: int, value: float) -> None:
+    st = load().mxfft_set_option(plan, int(key), float(value))
+    if st:
+        raise MxfftError(st, "mxfft_set_option")
+
+
+def _call(name, plan, x_ptr, y_ptr, batch, stream_ptr):
+    st = getattr(load(), name)(plan, x_ptr, y_ptr, int(batch), stream_ptr)
+    if st:
+        raise MxfftError(st, name)
+
+
+def mxfft_forward(plan, in_ptr, out_ptr, batch, stream=None):
+    _call("mxfft_forward", plan, in_ptr, out_ptr, batch, stream)
+
+
+def mxfft_inverse(plan, in_ptr, out_ptr, batch, stream=None):
+    _call("mxfft_inverse", plan, in_ptr, out_ptr, batch, stream)
+
+
+def mxfft_roundtrip(plan, in_ptr, out_ptr, batch, stream=None):
+    _call("mxfft_roundtrip", plan, in_ptr, out_ptr, batch, stream)
+
+
+def mxfft_get_status(plan, k_count: int = 0):
+    """Returns (status, device_flags, k list of length k_count)."""
+    flags = ctypes.c_int(0)
+    karr = (ctypes.c_int32 * max(k_count, 1))()
+    st = load().mxfft_get_status(plan, ctypes.byref(flags), karr if k_count else None)
+    return st, flags.value, list(karr)[:k_count]
+
+
+def mxfft_destroy(plan) -> None:
+    if plan:
+        load().mxfft_destroy(plan)
+
+
+def mxfft_profile(plan, enable: bool) -> None:
+    st = load().mxfft_profile(plan, int(bool(enable)))
+    if st:
+        raise MxfftError(st, "mxfft_profile")
+
+
+PROFILE_KINDS = ("stats_kernel", "pass_kernel")
+
+
+def mxfft_profile_read(plan):
+    """{kernel name: (total_ms, launches)} recorded since the last read."""
+    n = len(PROFILE_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    st = load().mxfft_profile_read(plan, ms, cnt, n)
+    if st:
+        raise MxfftError(st, "mxfft_profile_read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def _fmt(fmt) -> int:
+    return FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+
+
+# ---- torch convenience ---------------------------------------------------------
+
+class Plan:
+    """A plan for n0 x n1 complex64 slices; transforms torch CUDA tensors of
+    shape [..., n0, n1] (contiguous complex64) on the current torch stream."""
+
+    def __init__(self, n0: int, n1: int, fmt="e4m3", k: int = 32, tau: float = 1e-3,
+                 target: float = 0.5, tau_min: float | None = None,
+                 kmin: int | None = None, kmax: int | None = None):
+        self.n0, self.n1, self.fmt, self.k = int(n0), int(n1), fmt, int(k)
+        self.handle = mxfft_plan(n0, n1, fmt, k, tau, target)
+        self._last = (0, 0)   # (batch, op)
+        if tau_min is not None:
+            mxfft_set_option(self.handle, OPT_TAU_MIN, tau_min)
+        if kmin is not None:
+            mxfft_set_option(self.handle, OPT_K_MIN, kmin)
+        if kmax is not None:
+            mxfft_set_option(self.handle, OPT_K_MAX, kmax)
+
+    def _run(self, name, x, out):
+        import torch
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous complex64 CUDA tensor")
+        if tuple(x.shape[-2:]) != (self.n0, self.n1):
+            raise ValueError(f"expected [..., {self.n0}, {self.n1}], got {tuple(x.shape)}")
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise ValueError("out must match x")
+        batch = x.numel() // (self.n0 * self.n1)
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        _call(name, self.handle, x.data_ptr(), out.data_ptr(), batch, stream)
+        self._last = (batch, 2 if name == "mxfft_roundtrip" else 1)
+        return out
+
+    def forward(self, x, out=None):
+        return self._run("mxfft_forward", x, out)
+
+    def inverse(self, x, out=None):
+        return self._run("mxfft_inverse", x, out)
+
+    def roundtrip(self, x, out=None):
+        return self._run("mxfft_roundtrip", x, out)
+
+    def status(self):
+        """(status, device_flags, k) of the last call; k is [batch] or [batch][2]."""
+        batch, per = self._last
+        st, flags, k = mxfft_get_status(self.handle, batch * per)
+        if per == 2:
+            k = [k[2 * i:2 * i + 2] for i in range(batch)]
+        return st, flags, k
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mxfft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

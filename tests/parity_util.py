@@ -1,0 +1,60 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the oracle on the same seeded inputs and compare bit for bit."""
+import numpy as np
+
+import oracle
+
+
+def run_gpu(x: np.ndarray, fmt="e4m3", k=32, op="forward", tau=1e-3, target=0.5,
+            tau_min=None, kmin=None, kmax=None, inplace=False):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    n0, n1 = x.shape[-2:]
+    dev = torch.device("cuda:0")
+    xt = torch.from_numpy(np.ascontiguousarray(x, np.complex64)).to(dev)
+    with mxfft.Plan(n0, n1, fmt, k, tau, target, tau_min=tau_min, kmin=kmin, kmax=kmax) as p:
+        out = xt if inplace else None
+        y = getattr(p, op)(xt, out=out)
+        torch.cuda.synchronize()
+        st, flags, kk = p.status()
+    return y.cpu().numpy(), np.array(kk), flags, st
+
+
+def run_oracle(x, fmt="e4m3", k=32, op="forward", tau=1e-3, target=0.5, tau_min=None,
+               kmin=None, kmax=None):
+    kw = {}
+    if tau_min is not None:
+        kw["tau_min"] = tau_min
+    if kmin is not None:
+        kw["kmin"] = kmin
+    if kmax is not None:
+        kw["kmax"] = kmax
+    return oracle.mxfft2d(x, fmt, k, tau=tau, target=target, op=op, **kw)
+
+
+def assert_bitwise(got: np.ndarray, want: np.ndarray, what=""):
+    g = np.ascontiguousarray(got).view(np.uint32)
+    w = np.ascontiguousarray(want).view(np.uint32)
+    if not np.array_equal(g, w):
+        bad = np.argwhere(g.reshape(got.shape + (2,)) != w.reshape(want.shape + (2,)))
+        first = tuple(bad[0][:-1])
+        raise AssertionError(
+            f"{what}: {len(bad)} of {g.size} words differ; first at {first}: "
+            f"got {got[first]!r} want {want[first]!r}")
+
+
+def check(x, fmt="e4m3", k=32, op="forward", **kw):
+    """Bitwise output parity and exact prescale exponents."""
+    inplace = kw.pop("inplace", False)
+    got, kg, flags, st = run_gpu(x, fmt, k, op, inplace=inplace, **kw)
+    want, kw_, wflags = run_oracle(x, fmt, k, op, **kw)
+    assert st == (5 if wflags.any() else 0), (st, wflags)
+    assert bool(flags) == bool(wflags.any())
+    ok = ~wflags.astype(bool)
+    shape = x.shape
+    got = got.reshape((-1,) + shape[-2:])
+    want = want.reshape((-1,) + shape[-2:])
+    assert_bitwise(got[ok], want[ok], f"{fmt} k={k} {op} {shape}")
+    assert np.array_equal(np.asarray(kg).reshape(np.asarray(kw_).shape), kw_), (kg, kw_)
+    return got, want

@@ -30,7 +30,9 @@
  *      canonical order b = g*h + j of one stage of one 1D transform.
  *   C5 EncodeFromMantBlock recomputes the shared scale (a fresh MX block).
  *   C6 M_max is the element format's largest normal.
- *   C8 non-finite magnitudes give k = 0 and a flag; a_max = 0 gives k = 0.
+ *   C8 non-finite magnitudes give k = 0 and a flag; a_max = 0 gives k = 0;
+ *      an MX block holding Inf/NaN gets the NaN shared scale of OCP MX v1.0,
+ *      so each of its elements decodes to NaN.
  *   C9 the output is unscaled by 2^-k.
  *   C10 twiddles are exact FP64 values exp(-+ 2 pi i j / (2h)), quantised
  *       directly from FP64.
@@ -154,11 +156,24 @@ static void mx_butterfly_block(int nb, const float *u, const float *v,
         xi[b] = (float)q_elem(ldexp(wim[b], -sw), f);
     }
 
-    /* EncodeBlockMX(v) + MantissasBlock: shared scale s_v, element values y */
+    /* EncodeBlockMX(v) + MantissasBlock: shared scale s_v, element values y.
+     * A block holding an Inf or NaN gets the NaN shared scale of OCP MX, so
+     * every element of it decodes to NaN (reading C8). */
     float av = 0.0f;
+    int nonfinite = 0;
     for (int b = 0; b < nb; b++) {
+        if (!isfinite(v[2 * b]) || !isfinite(v[2 * b + 1])) nonfinite = 1;
         av = fmaxf(av, fabsf(v[2 * b]));
         av = fmaxf(av, fabsf(v[2 * b + 1]));
+    }
+    if (nonfinite) {
+        for (int b = 0; b < nb; b++) {
+            y0[2 * b] = u[2 * b] + NAN;
+            y0[2 * b + 1] = u[2 * b + 1] + NAN;
+            y1[2 * b] = u[2 * b] - NAN;
+            y1[2 * b + 1] = u[2 * b + 1] - NAN;
+        }
+        return;
     }
     int sv = mx_scale_exp((double)av, f);
     for (int b = 0; b < nb; b++) {

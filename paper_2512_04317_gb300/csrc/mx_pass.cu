@@ -108,15 +108,18 @@ __device__ __forceinline__ void mx_butterfly_pair(float2* A, int b0, int nb, int
     const float f0 = exp2i(so0 - sh0), f1 = exp2i(so1 - sh1);
     const float d0 = exp2i(sh0), d1 = exp2i(sh1);
 
+    // a block holding Inf/NaN has the NaN shared scale of OCP MX: all NaN
+    const float nan0 = a0 >= 0x7f800000u ? __int_as_float(0x7fffffff) : 1.0f;
+    const float nan1 = a1 >= 0x7f800000u ? __int_as_float(0x7fffffff) : 1.0f;
     if (q0.ok) {
-        const float wr = __fmul_rn(q_elem(__fmul_rn(p0r, f0), fp), d0);
-        const float wi = __fmul_rn(q_elem(__fmul_rn(p0i, f0), fp), d0);
+        const float wr = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p0r, f0), fp), d0), nan0);
+        const float wi = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p0i, f0), fp), d0), nan0);
         A[q0.iu] = make_float2(__fadd_rn(q0.u.x, wr), __fadd_rn(q0.u.y, wi));
         A[q0.iv] = make_float2(__fsub_rn(q0.u.x, wr), __fsub_rn(q0.u.y, wi));
     }
     if (q1.ok) {
-        const float wr = __fmul_rn(q_elem(__fmul_rn(p1r, f1), fp), d1);
-        const float wi = __fmul_rn(q_elem(__fmul_rn(p1i, f1), fp), d1);
+        const float wr = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p1r, f1), fp), d1), nan1);
+        const float wi = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p1i, f1), fp), d1), nan1);
         A[q1.iu] = make_float2(__fadd_rn(q1.u.x, wr), __fadd_rn(q1.u.y, wi));
         A[q1.iv] = make_float2(__fsub_rn(q1.u.x, wr), __fsub_rn(q1.u.y, wi));
     }

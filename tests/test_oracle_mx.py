@@ -202,3 +202,22 @@ def test_nonfinite_flag_and_k_zero():
     _, k, flags = oracle.mxfft2d(x, "e4m3", 8)
     assert flags.tolist() == [0, 1, 1]
     assert k[1] == 0 and k[2] == 0 and k[0] != 0
+
+
+def test_nonfinite_block_decodes_to_nan():
+    # OCP MX: a block holding Inf/NaN has a NaN shared scale; every element of
+    # the block decodes to NaN, so both butterfly outputs are NaN for that block
+    u = np.array([1 + 1j, 2 - 1j], np.complex64)
+    v = np.array([np.inf + 0j, 0.5 + 0.25j], np.complex64)
+    w = np.array([1.0, np.exp(-0.25j * np.pi)])
+    y0, y1 = oracle.butterfly_block(u, v, w, "e4m3")
+    assert np.isnan(y0.real).all() and np.isnan(y1.imag).all()
+    # a finite block next to it is untouched
+    y0f, _ = oracle.butterfly_block(u, np.array([1 + 0j, 0.5 + 0.25j], np.complex64), w, "e4m3")
+    assert np.isfinite(y0f).all()
+    # a prescale that overflows the peak (k2 ruled by a 1e-45 tail) yields
+    # non-finite outputs without the non-finite input flag
+    x = np.full((1, 8, 8), 1e-45, np.complex64)
+    x[0, 0, 0] = 1e36
+    out, k, flags = oracle.mxfft2d(x, "e4m3", 8)
+    assert k[0] == 90 and flags[0] == 0 and not np.isfinite(out).all()

@@ -60,7 +60,9 @@ typedef enum {
     MXFFT_OPT_TAU_MIN = 0,  /* tail floor tau_min of Alg. 1; a power of two.
                                Default 2^-10 (e4m3, FP6, FP4), 2^-12 (e5m2). */
     MXFFT_OPT_K_MIN = 1,    /* lower clip k_min of Alg. 1, integer in [-126, 126]; default -126 */
-    MXFFT_OPT_K_MAX = 2     /* upper clip k_max of Alg. 1, integer in [-126, 126]; default 126 */
+    MXFFT_OPT_K_MAX = 2,    /* upper clip k_max of Alg. 1, integer in [-126, 126]; default 126 */
+    MXFFT_OPT_GENERIC = 3   /* 1: run every pass on the generic shared-memory kernel instead of
+                               the register-resident one (same results; for testing); default 0 */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;
@@ -140,8 +142,10 @@ int mxfft_destroy(mxfft_plan_t plan);
  * stops recording.  mxfft_profile_read synchronises on the recorded events,
  * writes for each kernel kind i < nkinds the summed device time total_ms[i]
  * and the launch count launches[i], and clears the records.  Kinds:
- * 0 = statistics kernel (Alg. 1), 1 = MX butterfly pass kernel (rows and
- * columns).  Returns MXFFT_ERR_INVALID for a NULL plan or nkinds < 1.
+ * 0 = statistics kernel (Alg. 1), 1 = generic MX butterfly pass kernel,
+ * 2 = register-resident MX butterfly pass kernel (rows and columns of
+ * length 64..2048 with k <= 32).  Returns MXFFT_ERR_INVALID for a NULL plan
+ * or nkinds < 1.
  */
 int mxfft_profile(mxfft_plan_t plan, int enable);
 int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int nkinds);

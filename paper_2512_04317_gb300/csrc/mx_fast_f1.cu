@@ -1,0 +1,8 @@
+// Register-resident MX pass instantiated for the E5M2 element format.
+#include "mx_fast_kernel.cuh"
+
+namespace mxfft {
+namespace fast {
+template cudaError_t launch_fast_fmt<1>(const FastArgs&, int, int, cudaStream_t);
+}  // namespace fast
+}  // namespace mxfft

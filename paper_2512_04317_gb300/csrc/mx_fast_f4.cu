@@ -1,0 +1,8 @@
+// Register-resident MX pass instantiated for the E2M1 element format.
+#include "mx_fast_kernel.cuh"
+
+namespace mxfft {
+namespace fast {
+template cudaError_t launch_fast_fmt<4>(const FastArgs&, int, int, cudaStream_t);
+}  // namespace fast
+}  // namespace mxfft

@@ -1,0 +1,218 @@
+// Register-resident MX radix-2 pass for transform lengths n = 64..2048 and
+// MX blocks of m <= 16 butterflies (k <= 32 real elements).
+//
+// Data layout and work split:
+//   * A CTA owns NG groups of TG transforms (rows or columns) of one slice.
+//     A group's data live in shared memory as [element e][transform tau]
+//     (row stride S complex), so the TG lanes that share an element index
+//     touch consecutive 8-byte words and 64-bit accesses are conflict-free.
+//   * Lanes of a warp are transforms (lane % TG) and the rest of the thread
+//     index is a "slot" sigma in [0, n/32): every thread holds 32 elements of
+//     one transform in registers.
+//   * Phase A (stages h = 1..16, all inside a 32-element chunk of the
+//     bit-reversed order): slot sigma holds chunk sigma, i.e. the inputs
+//     x[rev(sigma) + j n/32], j = 0..31.  Every MX block of these stages lies
+//     inside one chunk for m <= 16, so the block maxima are register-local.
+//   * Phase B (stages h >= 32): stage pairs (h, 2h); slot sigma = G*(h/8) + r
+//     holds the 8-element runs P + 8r + q h, q = 0..3, P = 4hG, which carry
+//     whole butterfly groups of both stages.  An MX block of m = 16 spans the
+//     runs r and r^1, held by the lanes sigma and sigma^1 (lane ^ TG): one
+//     xor shuffle.  An odd last stage h = n/2 pairs runs sigma and sigma+n/32.
+//   * Element quantisation uses the sm_100-family conversions
+//     cvt.rn.satfinite.<fmt>x2.f32 and cvt.rn.f16x2.<fmt>x2 (round to nearest
+//     even, saturating, signed zeros and subnormals kept), the element-space
+//     product uses fma.rn.f32.f16 on the exact f16 element values (a product
+//     of two element values is exact, so the only rounding is the add, as in
+//     Alg. 2), and u +- c 2^s^ is one FFMA each because c 2^s^ is always an
+//     exact FP32 value (s^ >= -127 and the element grid step is >= 2^-16).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "mx_device.cuh"
+
+namespace mxfft {
+namespace fast {
+
+// ---- element conversions: f16x2 bits {lo: Q(a), hi: Q(b)} -----------------
+template <int FMT> struct Cvt;
+template <> struct Cvt<0> {  // E4M3
+    static __device__ __forceinline__ uint32_t q2(float a, float b) {
+        unsigned short p; uint32_t h;
+        asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(p) : "f"(b), "f"(a));
+        asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h) : "h"(p));
+        return h;
+    }
+};
+template <> struct Cvt<1> {  // E5M2
+    static __device__ __forceinline__ uint32_t q2(float a, float b) {
+        unsigned short p; uint32_t h;
+        asm("cvt.rn.satfinite.e5m2x2.f32 %0, %1, %2;" : "=h"(p) : "f"(b), "f"(a));
+        asm("cvt.rn.f16x2.e5m2x2 %0, %1;" : "=r"(h) : "h"(p));
+        return h;
+    }
+};
+template <> struct Cvt<2> {  // E2M3
+    static __device__ __forceinline__ uint32_t q2(float a, float b) {
+        unsigned short p; uint32_t h;
+        asm("cvt.rn.satfinite.e2m3x2.f32 %0, %1, %2;" : "=h"(p) : "f"(b), "f"(a));
+        asm("cvt.rn.f16x2.e2m3x2 %0, %1;" : "=r"(h) : "h"(p));
+        return h;
+    }
+};
+template <> struct Cvt<3> {  // E3M2
+    static __device__ __forceinline__ uint32_t q2(float a, float b) {
+        unsigned short p; uint32_t h;
+        asm("cvt.rn.satfinite.e3m2x2.f32 %0, %1, %2;" : "=h"(p) : "f"(b), "f"(a));
+        asm("cvt.rn.f16x2.e3m2x2 %0, %1;" : "=r"(h) : "h"(p));
+        return h;
+    }
+};
+template <> struct Cvt<4> {  // E2M1
+    static __device__ __forceinline__ uint32_t q2(float a, float b) {
+        unsigned short p; uint32_t h;
+        asm("{.reg .b8 t; cvt.rn.satfinite.e2m1x2.f32 t, %1, %2; cvt.u16.u8 %0, t;}"
+            : "=h"(p) : "f"(b), "f"(a));
+        asm("{.reg .b8 t; cvt.u8.u16 t, %1; cvt.rn.f16x2.e2m1x2 %0, t;}" : "=r"(h) : "h"(p));
+        return h;
+    }
+};
+
+// a.x * b.y + c with f16 halves (x, y in {lo, hi}) and FP32 c, d
+#define MX_FMA_H(NAME, AH, BH)                                                              \
+    __device__ __forceinline__ float NAME(uint32_t a, uint32_t b, float c) {                \
+        float d;                                                                            \
+        asm("{.reg .b16 a0, a1, b0, b1; mov.b32 {a0, a1}, %1; mov.b32 {b0, b1}, %2;"      \
+            " fma.rn.f32.f16 %0, " AH ", " BH ", %3;}"                                      \
+            : "=f"(d) : "r"(a), "r"(b), "f"(c));                                            \
+        return d;                                                                           \
+    }
+MX_FMA_H(fma_ll, "a0", "b0")
+MX_FMA_H(fma_lh, "a0", "b1")
+MX_FMA_H(fma_hl, "a1", "b0")
+MX_FMA_H(fma_hh, "a1", "b1")
+#undef MX_FMA_H
+
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+__device__ __forceinline__ float cabs_max(float2 v) {
+    return fmax_nan(fabsf(v.x), fabsf(v.y));
+}
+
+// Shared exponent from a nonnegative block maximum (NaN/Inf handled by caller).
+__device__ __forceinline__ int scale_of(float amax, int emax) {
+    return mx_scale_exp(__float_as_uint(amax), emax);
+}
+
+
+// Alg. 2 on one MX block of NB butterflies whose u/v live in registers.
+// Steps: block max of v -> s_v; y = Q(v 2^-s_v); p = x y (exact products, one
+// rounding each); block max of p -> s^; c = Q(p 2^(s_w + s_v - s^));
+// u +- c 2^s^.  A block holding Inf/NaN decodes to NaN (OCP MX NaN scale).
+// `red` != 0 reduces the two block maxima with the lane `red` apart too.
+template <int FMT, int NB>
+__device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (&V)[NB],
+                                         const uint32_t (&W)[NB], int sw, unsigned red,
+                                         const FmtParams& fp) {
+    float A = 0.f;
+#pragma unroll
+    for (int t = 0; t < NB; t++) A = fmax_nan(A, cabs_max(*V[t]));
+    if (red) A = fmax_nan(A, __shfl_xor_sync(0xffffffffu, A, red));
+    const bool bad = !(A <= 3.402823466e38f);
+    const int sv = scale_of(A, fp.emax);
+    const float inv = exp2i(-sv);
+    float pr[NB], pi[NB];
+    float P = 0.f;
+#pragma unroll
+    for (int t = 0; t < NB; t++) {
+        const float2 v = *V[t];
+        const uint32_t y = Cvt<FMT>::q2(__fmul_rn(v.x, inv), __fmul_rn(v.y, inv));
+        const uint32_t w = W[t];
+        pr[t] = fma_ll(w, y, -fma_hh(w, y, -0.0f));
+        pi[t] = fma_hl(w, y, fma_lh(w, y, -0.0f));
+        P = fmaxf(P, fmaxf(fabsf(pr[t]), fabsf(pi[t])));
+    }
+    if (red) P = fmaxf(P, __shfl_xor_sync(0xffffffffu, P, red));
+    const int so = sw + sv;
+    const uint32_t Pb = __float_as_uint(P);
+    const int sh = Pb ? min(max(so + ilogb_bits(Pb) - fp.emax, -127), 127) : so;
+    const float f = exp2i(so - sh);
+    const float d = bad ? __int_as_float(0x7fffffff) : exp2i(sh);
+#pragma unroll
+    for (int t = 0; t < NB; t++) {
+        const uint32_t c = Cvt<FMT>::q2(__fmul_rn(pr[t], f), __fmul_rn(pi[t], f));
+        const __half2 ch = *reinterpret_cast<const __half2*>(&c);
+        const float cr = __low2float(ch), ci = __high2float(ch);
+        const float2 u = *U[t];
+        *U[t] = make_float2(__fmaf_rn(cr, d, u.x), __fmaf_rn(ci, d, u.y));
+        *V[t] = make_float2(__fmaf_rn(-cr, d, u.x), __fmaf_rn(-ci, d, u.y));
+    }
+}
+
+// Phase A stage H on a 32-element chunk r[] (chunk-local butterfly t = 0..15:
+// group t / H, index j = t % H).
+template <int FMT, int LOGM, int H>
+__device__ __forceinline__ void stage_a(float2 (&r)[32], const TwA& tw, const FmtParams& fp) {
+    constexpr int M = 1 << LOGM;
+#pragma unroll
+    for (int b0 = 0; b0 < 16; b0 += M) {
+        float2* U[M];
+        float2* V[M];
+        uint32_t W[M];
+#pragma unroll
+        for (int q = 0; q < M; q++) {
+            const int t = b0 + q;
+            const int iu = 2 * H * (t / H) + (t % H);
+            U[q] = &r[iu];
+            V[q] = &r[iu + H];
+            W[q] = tw.h2[H - 1 + (t % H)];
+        }
+        mx_block<FMT, M>(U, V, W, tw.sw[H - 1 + (b0 % H)], 0u, fp);
+    }
+}
+
+// Phase B: one stage on 8 butterflies u = Ru[i], v = Rv[i], j = jb + i, with
+// twiddles at twh[j] / tws[j] (already offset to stage h: index h - 1 + j).
+template <int FMT, int LOGM>
+__device__ __forceinline__ void stage_b8(float2 (&Ru)[8], float2 (&Rv)[8],
+                                         const uint32_t* __restrict__ twh,
+                                         const int8_t* __restrict__ tws, int jb, unsigned red,
+                                         const FmtParams& fp) {
+    constexpr int M = 1 << LOGM;
+    constexpr int ML = M < 8 ? M : 8;  // butterflies of a block held by this thread
+#pragma unroll
+    for (int b0 = 0; b0 < 8; b0 += ML) {
+        float2* U[ML];
+        float2* V[ML];
+        uint32_t W[ML];
+#pragma unroll
+        for (int q = 0; q < ML; q++) {
+            U[q] = &Ru[b0 + q];
+            V[q] = &Rv[b0 + q];
+            W[q] = __ldg(twh + jb + b0 + q);
+        }
+        mx_block<FMT, ML>(U, V, W, __ldg(tws + jb + b0), M > 8 ? red : 0u, fp);
+    }
+}
+
+// Compile-time 5-bit reversal of the chunk position.
+__host__ __device__ constexpr int rev5(int t) {
+    return ((t & 1) << 4) | ((t & 2) << 2) | (t & 4) | ((t & 8) >> 2) | ((t & 16) >> 4);
+}
+
+struct FastArgs {
+    PassArgs a;
+    TwA twa;
+    const uint32_t* twh;   // f16x2 twiddle element values, index h - 1 + j
+    int TG;                // transforms per group (16, or 8 for n = 2048)
+    int S;                 // shared row stride (complex) of a group: TG or TG + 1
+    int NG;                // groups per CTA
+};
+
+}  // namespace fast
+}  // namespace mxfft

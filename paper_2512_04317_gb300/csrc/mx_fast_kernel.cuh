@@ -1,0 +1,220 @@
+// The register-resident MX pass kernel (see mx_fast_impl.cuh for the layout)
+// and its launcher, instantiated once per element format in mx_fast_f*.cu.
+#pragma once
+
+#include "mx_fast_impl.cuh"
+
+namespace mxfft {
+namespace fast {
+
+constexpr int kMaxThreads = 512;
+
+__device__ __forceinline__ float2 epi_value(float2 v, int mode, float post) {
+    if (mode != EPI_RAW) {
+        v.x = __fmul_rn(v.x, post);
+        v.y = __fmul_rn(v.y, post);
+    }
+    return v;
+}
+
+template <int FMT, int LOGM>
+__global__ void __launch_bounds__(kMaxThreads)
+fast_pass_kernel(const FastArgs fa) {
+    extern __shared__ float2 sm[];
+    __shared__ uint32_t sh_hist[kHistBins];
+    __shared__ uint32_t sh_misc[4];
+    const PassArgs& a = fa.a;
+    const int n = a.n, L = a.logn, TG = fa.TG, S = fa.S;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int per_group = TG * (n >> 5);
+    const int grp = tid / per_group;
+    const int w = tid - grp * per_group;
+    const int tau = w % TG;
+    const int sigma = w / TG;
+    const int other = a.dim == 1 ? a.n0 : a.n1;
+    const int tpc = TG * fa.NG;
+    const int per_slice = other / tpc;
+    const int slice = blockIdx.x / per_slice;
+    const int t0 = (blockIdx.x - slice * per_slice) * tpc;
+    const int tr = t0 + grp * TG + tau;          // row (dim 1) or column (dim 0)
+    float2* __restrict__ Gs = sm + (size_t)grp * n * S;
+    const size_t sbase = (size_t)slice * a.n0 * a.n1;
+    const float2* __restrict__ in = a.in + sbase;
+    float2* __restrict__ out = a.out + sbase;
+    const FmtParams fp = a.fp;
+    const bool stats = a.epilogue == EPI_UNSCALE_STATS;
+    if (stats)
+        for (int b = tid; b < kHistBins; b += nthr) sh_hist[b] = 0;
+
+    const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
+    const int s = n >> 5;                        // chunk stride of the bit-reversed gather
+    const int rc = L > 5 ? (int)(__brev((unsigned)sigma) >> (37 - L)) : 0;
+
+    // ---- phase A input: x[rc + j s] -> r[rev5(j)] ---------------------------
+    float2 r[32];
+    if (a.dim == 0) {
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            float2 v = in[(size_t)(rc + j * s) * a.n1 + tr];
+            if (a.prologue == PRO_PRESCALE) { v.x = __fmul_rn(v.x, pre); v.y = __fmul_rn(v.y, pre); }
+            r[rev5(j)] = v;
+        }
+    } else {
+        // stage the CTA's rows as [e][tau]: lanes run over rows, two lanes per
+        // 16-byte pair, so each row contributes a full 32-byte sector per load
+        const int half = n >> 1;
+        const int total = fa.NG * TG * half;
+        for (int u = tid; u < total; u += nthr) {
+            const int tc = u % TG;
+            const int rest = u / TG;
+            const int p = rest % half;
+            const int g = rest / half;
+            const float4 v = __ldg(reinterpret_cast<const float4*>(
+                in + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p));
+            float2* Gg = sm + (size_t)g * n * S;
+            Gg[(2 * p) * S + tc] = make_float2(__fmul_rn(v.x, pre), __fmul_rn(v.y, pre));
+            Gg[(2 * p + 1) * S + tc] = make_float2(__fmul_rn(v.z, pre), __fmul_rn(v.w, pre));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 32; j++) r[rev5(j)] = Gs[(rc + j * s) * S + tau];
+        __syncthreads();
+    }
+
+    // ---- phase A: stages h = 1..16 inside the chunk -------------------------
+    stage_a<FMT, LOGM, 1>(r, fa.twa, fp);
+    stage_a<FMT, LOGM, 2>(r, fa.twa, fp);
+    stage_a<FMT, LOGM, 4>(r, fa.twa, fp);
+    stage_a<FMT, LOGM, 8>(r, fa.twa, fp);
+    stage_a<FMT, LOGM, 16>(r, fa.twa, fp);
+#pragma unroll
+    for (int t = 0; t < 32; t++) Gs[(32 * sigma + t) * S + tau] = r[t];
+    __syncthreads();
+
+    // ---- phase B: stage pairs (h, 2h), an odd last stage alone ---------------
+    const unsigned red = (unsigned)TG;           // lane of the partner run (slot ^ 1)
+    float2 R[4][8];
+    int e0[4];
+    int ast = 5;
+    while (true) {
+        const int h = 1 << ast;
+        const bool two = ast + 1 < L;
+        int jA, jB, jC, jD;
+        if (two) {
+            const int runs = h >> 3;
+            const int Gi = sigma / runs, rr = sigma - Gi * runs;
+            const int base = 4 * h * Gi + 8 * rr;
+#pragma unroll
+            for (int q = 0; q < 4; q++) e0[q] = base + q * h;
+            jA = jB = 8 * rr;
+            jC = 8 * rr;
+            jD = h + 8 * rr;
+        } else {
+            e0[0] = 8 * sigma;
+            e0[1] = 8 * sigma + h;
+            e0[2] = 8 * (sigma + s);
+            e0[3] = 8 * (sigma + s) + h;
+            jA = 8 * sigma;
+            jB = 8 * (sigma + s);
+            jC = jD = 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) R[q][i] = Gs[(e0[q] + i) * S + tau];
+        stage_b8<FMT, LOGM>(R[0], R[1], fa.twh + h - 1, a.tws + h - 1, jA, red, fp);
+        stage_b8<FMT, LOGM>(R[2], R[3], fa.twh + h - 1, a.tws + h - 1, jB, red, fp);
+        if (two) {
+            stage_b8<FMT, LOGM>(R[0], R[2], fa.twh + 2 * h - 1, a.tws + 2 * h - 1, jC, red, fp);
+            stage_b8<FMT, LOGM>(R[1], R[3], fa.twh + 2 * h - 1, a.tws + 2 * h - 1, jD, red, fp);
+        }
+        ast += two ? 2 : 1;
+        if (ast >= L) break;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
+        __syncthreads();
+    }
+
+    // ---- output in natural order ---------------------------------------------
+    float post = 1.0f;
+    if (a.epilogue == EPI_UNSCALE || a.epilogue == EPI_UNSCALE_STATS) post = exp2i(-a.st[slice].k);
+    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
+    StatAcc acc;
+    if (a.dim == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const float2 v = epi_value(R[q][i], a.epilogue, post);
+                out[(size_t)(e0[q] + i) * a.n1 + tr] = v;
+                if (stats) acc.add(v.x, v.y, sh_hist);
+            }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
+        __syncthreads();
+        const int half = n >> 1;
+        const int total = fa.NG * TG * half;
+        for (int u = tid; u < total; u += nthr) {
+            const int tc = u % TG;
+            const int rest = u / TG;
+            const int p = rest % half;
+            const int g = rest / half;
+            const float2* Gg = sm + (size_t)g * n * S;
+            const float2 v0 = epi_value(Gg[(2 * p) * S + tc], a.epilogue, post);
+            const float2 v1 = epi_value(Gg[(2 * p + 1) * S + tc], a.epilogue, post);
+            *reinterpret_cast<float4*>(out + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p) =
+                make_float4(v0.x, v0.y, v1.x, v1.y);
+            if (stats) { acc.add(v0.x, v0.y, sh_hist); acc.add(v1.x, v1.y, sh_hist); }
+        }
+    }
+    if (stats) {
+        __syncthreads();
+        stats_flush_and_select(acc, sh_hist, sh_misc, a.st_out + slice, (uint32_t)per_slice, a.kp);
+    }
+}
+
+// Launch geometry: TG transforms per group (8 for n = 2048 so a group fits in
+// shared memory, with a padded stride), NG groups per CTA so that a CTA has
+// about 256 threads (512 for n >= 1024).
+inline bool fast_geometry(int n, int other, int* TG, int* S, int* NG, int* threads) {
+    if (n < 64 || n > 2048) return false;
+    *TG = n == 2048 ? 8 : 16;
+    *S = n == 2048 ? 9 : 16;
+    const int per_group = *TG * (n / 32);
+    int ng = per_group >= 256 ? 1 : 256 / per_group;
+    while (ng > 1 && (*TG * ng > other || other % (*TG * ng) != 0)) ng >>= 1;
+    if (*TG > other || other % *TG != 0) return false;
+    *NG = ng;
+    *threads = per_group * ng;
+    return *threads <= kMaxThreads;
+}
+
+template <int FMT>
+cudaError_t launch_fast_fmt(const FastArgs& fa, int logm, int batch, cudaStream_t s) {
+    const PassArgs& a = fa.a;
+    const int other = a.dim == 1 ? a.n0 : a.n1;
+    const int threads = fa.TG * (a.n / 32) * fa.NG;
+    const int blocks = batch * (other / (fa.TG * fa.NG));
+    const size_t smem = (size_t)fa.NG * a.n * fa.S * sizeof(float2);
+    void (*k)(const FastArgs) = nullptr;
+    switch (logm) {
+        case 0: k = fast_pass_kernel<FMT, 0>; break;
+        case 1: k = fast_pass_kernel<FMT, 1>; break;
+        case 2: k = fast_pass_kernel<FMT, 2>; break;
+        case 3: k = fast_pass_kernel<FMT, 3>; break;
+        case 4: k = fast_pass_kernel<FMT, 4>; break;
+        default: return cudaErrorNotSupported;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, threads, smem, s>>>(fa);
+    return cudaGetLastError();
+}
+
+}  // namespace fast
+}  // namespace mxfft

@@ -63,13 +63,26 @@ struct PassArgs {
     SliceStats* st_out;   // statistics accumulated by EPI_UNSCALE_STATS
     int prologue, epilogue;
     int lg_total;         // log2(n0 * n1) for EPI_RT_FINAL
+    int fmt;              // element format code (mxfft_format)
     FmtParams fp;
     KParams kp;           // for the k selection done by EPI_UNSCALE_STATS
+};
+
+// Twiddles of stages h = 1..16 (index h - 1 + j) for the register-resident
+// pass: identical for every 32-element chunk, passed as kernel parameters.
+struct TwA {
+    uint32_t h2[32];   // f16x2 {re, im} twiddle element values
+    int8_t sw[32];     // twiddle block scale exponents
 };
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_stats(const float2* x, int batch, int n0, int n1, SliceStats* st,
                          KParams kp, cudaStream_t s);
 cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s);
+// Register-resident pass for n in [64, 2048] and m <= 16; returns
+// cudaErrorNotSupported (launching nothing) outside that range.
+bool fast_pass_supported(const PassArgs& a);
+cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
+                             cudaStream_t s);
 
 }  // namespace mxfft

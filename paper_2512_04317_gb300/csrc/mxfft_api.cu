@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "mx_internal.h"
 #include "mxfft.h"
 
@@ -29,6 +31,9 @@ struct mxfft_plan_s {
     int m[2];                  // MX block size in butterflies per axis (0: n0, 1: n1)
     float2* d_tw[2][2];        // [axis][0 forward, 1 inverse]
     int8_t* d_tws[2];          // [axis] twiddle block exponents
+    uint32_t* d_twh[2][2];     // [axis][dir] f16x2 twiddle element values
+    TwA twa[2][2];             // [axis][dir] stages h <= 16 for the register pass
+    int force_generic;         // 1: always use the generic pass kernel
     SliceStats* d_st;          // 2 * st_cap records: forward, inverse
     int st_cap;
     int last_batch, last_op;   // of the last transform
@@ -157,7 +162,10 @@ int cuda_status(cudaError_t e) {
 
 void free_plan_device(mxfft_plan_s* p) {
     for (int a = 0; a < 2; a++) {
-        for (int d = 0; d < 2; d++) if (p->d_tw[a][d]) cudaFree(p->d_tw[a][d]);
+        for (int d = 0; d < 2; d++) {
+            if (p->d_tw[a][d]) cudaFree(p->d_tw[a][d]);
+            if (p->d_twh[a][d]) cudaFree(p->d_twh[a][d]);
+        }
         if (p->d_tws[a]) cudaFree(p->d_tws[a]);
     }
     if (p->d_st) cudaFree(p->d_st);
@@ -208,6 +216,7 @@ PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, fl
     a.m = p->m[dim];
     a.tw = p->d_tw[dim][dir];
     a.tws = p->d_tws[dim];
+    a.fmt = p->fmt;
     a.fp = p->fp;
     a.kp = kparams(p);
     a.lg_total = ilog2(p->n0) + ilog2(p->n1);
@@ -231,9 +240,14 @@ void prof_end(ProfRec* r, cudaStream_t s) {
     if (r) cudaEventRecord(r->b, s);
 }
 
+// The register-resident kernel where it applies (n in [64, 2048], m <= 16),
+// else the generic shared-memory kernel.
 cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
-    ProfRec* r = prof_begin(p, 1, s);
-    cudaError_t e = launch_pass(a, batch, s);
+    const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
+    const bool fast = !p->force_generic && fast_pass_supported(a);
+    ProfRec* r = prof_begin(p, fast ? 2 : 1, s);
+    cudaError_t e = fast ? launch_fast_pass(a, p->d_twh[a.dim][dir], p->twa[a.dim][dir], batch, s)
+                         : launch_pass(a, batch, s);
     prof_end(r, s);
     return e;
 }
@@ -357,6 +371,22 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
                 rc = cuda_status(cudaMemcpy(p->d_tw[axis][d], t.data(), sizeof(float2) * t.size(),
                                             cudaMemcpyHostToDevice));
         }
+        for (int d = 0; d < 2 && rc == MXFFT_OK; d++) {
+            const std::vector<float2>& t = d == 0 ? fw : iv;
+            std::vector<uint32_t> h2(t.size());
+            for (size_t i = 0; i < t.size(); i++) {
+                const __half2 hh = __floats2half2_rn(t[i].x, t[i].y);   // exact: element values
+                std::memcpy(&h2[i], &hh, sizeof(uint32_t));
+            }
+            for (int i = 0; i < 32; i++) {
+                p->twa[axis][d].h2[i] = i < (int)h2.size() ? h2[i] : 0u;
+                p->twa[axis][d].sw[i] = i < (int)sw.size() ? sw[i] : (int8_t)0;
+            }
+            rc = cuda_status(cudaMalloc(&p->d_twh[axis][d], sizeof(uint32_t) * h2.size()));
+            if (rc == MXFFT_OK)
+                rc = cuda_status(cudaMemcpy(p->d_twh[axis][d], h2.data(), sizeof(uint32_t) * h2.size(),
+                                            cudaMemcpyHostToDevice));
+        }
         if (rc == MXFFT_OK) rc = cuda_status(cudaMalloc(&p->d_tws[axis], sw.size()));
         if (rc == MXFFT_OK)
             rc = cuda_status(cudaMemcpy(p->d_tws[axis], sw.data(), sw.size(), cudaMemcpyHostToDevice));
@@ -388,6 +418,10 @@ int mxfft_set_option(mxfft_plan_t p, int key, double value) {
             if (key == MXFFT_OPT_K_MIN) p->kmin = v; else p->kmax = v;
             return MXFFT_OK;
         }
+        case MXFFT_OPT_GENERIC:
+            if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
+            p->force_generic = value != 0.0;
+            return MXFFT_OK;
         default:
             return MXFFT_ERR_INVALID;
     }

@@ -6,14 +6,15 @@ import oracle
 
 
 def run_gpu(x: np.ndarray, fmt="e4m3", k=32, op="forward", tau=1e-3, target=0.5,
-            tau_min=None, kmin=None, kmax=None, inplace=False):
+            tau_min=None, kmin=None, kmax=None, inplace=False, generic=False):
     import torch
 
     from paper_2512_04317_gb300 import mxfft
     n0, n1 = x.shape[-2:]
     dev = torch.device("cuda:0")
     xt = torch.from_numpy(np.ascontiguousarray(x, np.complex64)).to(dev)
-    with mxfft.Plan(n0, n1, fmt, k, tau, target, tau_min=tau_min, kmin=kmin, kmax=kmax) as p:
+    with mxfft.Plan(n0, n1, fmt, k, tau, target, tau_min=tau_min, kmin=kmin, kmax=kmax,
+                    generic=generic) as p:
         out = xt if inplace else None
         y = getattr(p, op)(xt, out=out)
         torch.cuda.synchronize()
@@ -53,7 +54,8 @@ def assert_bitwise(got: np.ndarray, want: np.ndarray, what=""):
 def check(x, fmt="e4m3", k=32, op="forward", **kw):
     """Bitwise output parity and exact prescale exponents."""
     inplace = kw.pop("inplace", False)
-    got, kg, flags, st = run_gpu(x, fmt, k, op, inplace=inplace, **kw)
+    generic = kw.pop("generic", False)
+    got, kg, flags, st = run_gpu(x, fmt, k, op, inplace=inplace, generic=generic, **kw)
     want, kw_, wflags = run_oracle(x, fmt, k, op, **kw)
     assert st == (5 if wflags.any() else 0), (st, wflags)
     assert bool(flags) == bool(wflags.any())

@@ -86,6 +86,16 @@ def test_large_2048_sampled(cuda_device):
         assert int(np.asarray(kg)[0]) == int(kw[0])
 
 
+@pytest.mark.parametrize("n0,n1", [(64, 64), (256, 128), (128, 512), (2048, 16)])
+def test_generic_kernel_matches_oracle(n0, n1, cuda_device):
+    # the shared-memory kernel also covers sizes the register-resident one
+    # serves; pin it there too
+    x = phantom.random_complex((2, n0, n1), seed=n0 + 5 * n1)
+    for fmt, k in (("e4m3", 32), ("e5m2", 8), ("e2m1", 2)):
+        for op in OPS:
+            check(x, fmt, k, op, generic=True)
+
+
 def test_ragged_batches_and_in_place(cuda_device):
     for batch in (1, 5, 17):
         x = phantom.random_complex((batch, 32, 64), seed=batch)

@@ -80,6 +80,21 @@ __device__ __forceinline__ bool is_finite_bits(uint32_t b) {
     return (b & 0x7f800000u) != 0x7f800000u;
 }
 
+// The same |x| for finite inputs, with a short path: when each component is
+// zero or has magnitude in [2^-62, 2^62], the unscaled sqrt(re^2 + im^2)
+// performs the scaled computation of mag_c3 times exact powers of two (every
+// intermediate stays normal, or the smaller square is below half an ulp of the
+// larger in both forms), so the rounded results are identical.
+__device__ __forceinline__ float mag_c3_fast(float re, float im) {
+    const uint32_t br = __float_as_uint(re) & 0x7fffffffu;
+    const uint32_t bi = __float_as_uint(im) & 0x7fffffffu;
+    const uint32_t lo = (uint32_t)(127 - 62) << 23, hi = (uint32_t)(127 + 63) << 23;
+    const bool okr = br == 0 || (br >= lo && br < hi);
+    const bool oki = bi == 0 || (bi >= lo && bi < hi);
+    if (okr && oki) return __fsqrt_rn(__fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im)));
+    return mag_c3(re, im);
+}
+
 // Alg. 1 exponent selection from a slice's statistics, exact integer form.
 //   k1 = round(log2(2^t / max(a_max, 1e-30))) = t - (e_a + [M_a^2 >= 2^47])
 //        (a_max = M_a 2^(e_a - 23), 24-bit significand; ties cannot occur);
@@ -143,21 +158,36 @@ __device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams
 }
 
 // Accumulates one value's contribution to Alg. 1's statistics in per-thread
-// registers and the CTA's shared histogram.
+// registers and the CTA's shared histogram.  When the whole warp executes the
+// call, lanes that hit the same bin are merged first (__match_any_sync), so a
+// bin shared by many lanes costs one shared atomic instead of one per lane.
 struct StatAcc {
     uint32_t amax_bits = 0;
     uint32_t nnz = 0;
     uint32_t nonfinite = 0;
     __device__ __forceinline__ void add(float re, float im, uint32_t* sh_hist) {
-        uint32_t br = __float_as_uint(re), bi = __float_as_uint(im);
-        if (!is_finite_bits(br) || !is_finite_bits(bi)) { nonfinite = 1; return; }
-        float m = mag_c3(re, im);
-        uint32_t mb = __float_as_uint(m);
-        if (!is_finite_bits(mb)) { nonfinite = 1; return; }
-        if (mb == 0) return;
-        amax_bits = max(amax_bits, mb);
-        nnz++;
-        atomicAdd(&sh_hist[ilogb_bits(mb) + 149], 1u);
+        const uint32_t br = __float_as_uint(re), bi = __float_as_uint(im);
+        int bin = -1;
+        if (!is_finite_bits(br) || !is_finite_bits(bi)) {
+            nonfinite = 1;
+        } else {
+            const uint32_t mb = __float_as_uint(mag_c3_fast(re, im));
+            if (!is_finite_bits(mb)) {
+                nonfinite = 1;
+            } else if (mb != 0) {
+                amax_bits = max(amax_bits, mb);
+                nnz++;
+                bin = ilogb_bits(mb) + 149;
+            }
+        }
+        const unsigned act = __activemask();
+        if (act == 0xffffffffu) {
+            const unsigned same = __match_any_sync(0xffffffffu, bin);
+            if (bin >= 0 && (threadIdx.x & 31) == __ffs(same) - 1)
+                atomicAdd(&sh_hist[bin], (uint32_t)__popc(same));
+        } else if (bin >= 0) {
+            atomicAdd(&sh_hist[bin], 1u);
+        }
     }
 };
 

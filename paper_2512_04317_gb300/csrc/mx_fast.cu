@@ -38,6 +38,7 @@ cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& 
     int threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
     fast::fast_geometry(a.n, other, &fa.TG, &fa.S, &fa.NG, &threads);
+    fa.lgTG = fa.TG == 16 ? 4 : 3;
     const int logm = log2_exact(a.m);
     switch (a.fmt) {
         case 0: return fast::launch_fast_fmt<0>(fa, logm, batch, s);

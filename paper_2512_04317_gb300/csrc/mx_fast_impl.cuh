@@ -115,28 +115,44 @@ __device__ __forceinline__ int scale_of(float amax, int emax) {
 // rounding each); block max of p -> s^; c = Q(p 2^(s_w + s_v - s^));
 // u +- c 2^s^.  A block holding Inf/NaN decodes to NaN (OCP MX NaN scale).
 // `red` != 0 reduces the two block maxima with the lane `red` apart too.
+template <int NB>
+__device__ __forceinline__ float tree_max_nan(float (&a)[NB]) {
+#pragma unroll
+    for (int w = 1; w < NB; w <<= 1)
+#pragma unroll
+        for (int t = 0; t + w < NB; t += 2 * w) a[t] = fmax_nan(a[t], a[t + w]);
+    return a[0];
+}
+
+// Alg. 2 on one MX block of NB butterflies whose u/v live in registers.
+// Steps: block max of v -> s_v; y = Q(v 2^-s_v); p = x y (exact products, one
+// rounding each), written over v, which is dead by then; block max of p -> s^;
+// c = Q(p 2^(s_w + s_v - s^)); u +- c 2^s^.  A block holding Inf/NaN decodes
+// to NaN (OCP MX NaN scale).  `red` != 0 also reduces the two block maxima
+// with the lane `red` apart.
 template <int FMT, int NB>
 __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (&V)[NB],
                                          const uint32_t (&W)[NB], int sw, unsigned red,
                                          const FmtParams& fp) {
-    float A = 0.f;
+    float m[NB];
 #pragma unroll
-    for (int t = 0; t < NB; t++) A = fmax_nan(A, cabs_max(*V[t]));
+    for (int t = 0; t < NB; t++) m[t] = cabs_max(*V[t]);
+    float A = tree_max_nan(m);
     if (red) A = fmax_nan(A, __shfl_xor_sync(0xffffffffu, A, red));
     const bool bad = !(A <= 3.402823466e38f);
     const int sv = scale_of(A, fp.emax);
     const float inv = exp2i(-sv);
-    float pr[NB], pi[NB];
-    float P = 0.f;
 #pragma unroll
     for (int t = 0; t < NB; t++) {
         const float2 v = *V[t];
         const uint32_t y = Cvt<FMT>::q2(__fmul_rn(v.x, inv), __fmul_rn(v.y, inv));
         const uint32_t w = W[t];
-        pr[t] = fma_ll(w, y, -fma_hh(w, y, -0.0f));
-        pi[t] = fma_hl(w, y, fma_lh(w, y, -0.0f));
-        P = fmaxf(P, fmaxf(fabsf(pr[t]), fabsf(pi[t])));
+        const float pr = fma_ll(w, y, -fma_hh(w, y, -0.0f));
+        const float pi = fma_hl(w, y, fma_lh(w, y, -0.0f));
+        *V[t] = make_float2(pr, pi);
+        m[t] = fmaxf(fabsf(pr), fabsf(pi));
     }
+    float P = tree_max_nan(m);
     if (red) P = fmaxf(P, __shfl_xor_sync(0xffffffffu, P, red));
     const int so = sw + sv;
     const uint32_t Pb = __float_as_uint(P);
@@ -145,7 +161,8 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
     const float d = bad ? __int_as_float(0x7fffffff) : exp2i(sh);
 #pragma unroll
     for (int t = 0; t < NB; t++) {
-        const uint32_t c = Cvt<FMT>::q2(__fmul_rn(pr[t], f), __fmul_rn(pi[t], f));
+        const float2 p = *V[t];
+        const uint32_t c = Cvt<FMT>::q2(__fmul_rn(p.x, f), __fmul_rn(p.y, f));
         const __half2 ch = *reinterpret_cast<const __half2*>(&c);
         const float cr = __low2float(ch), ci = __high2float(ch);
         const float2 u = *U[t];
@@ -210,6 +227,7 @@ struct FastArgs {
     TwA twa;
     const uint32_t* twh;   // f16x2 twiddle element values, index h - 1 + j
     int TG;                // transforms per group (16, or 8 for n = 2048)
+    int lgTG;              // log2(TG)
     int S;                 // shared row stride (complex) of a group: TG or TG + 1
     int NG;                // groups per CTA
 };

@@ -17,7 +17,7 @@ __device__ __forceinline__ float2 epi_value(float2 v, int mode, float post) {
     return v;
 }
 
-template <int FMT, int LOGM>
+template <int FMT, int LOGM, int DIM>
 __global__ void __launch_bounds__(kMaxThreads)
 fast_pass_kernel(const FastArgs fa) {
     extern __shared__ float2 sm[];
@@ -26,17 +26,18 @@ fast_pass_kernel(const FastArgs fa) {
     const PassArgs& a = fa.a;
     const int n = a.n, L = a.logn, TG = fa.TG, S = fa.S;
     const int nthr = blockDim.x, tid = threadIdx.x;
-    const int per_group = TG * (n >> 5);
-    const int grp = tid / per_group;
-    const int w = tid - grp * per_group;
-    const int tau = w % TG;
-    const int sigma = w / TG;
-    const int other = a.dim == 1 ? a.n0 : a.n1;
+    const int lgTG = fa.lgTG;
+    const int lg_pg = lgTG + L - 5;              // log2 of threads per group
+    const int grp = tid >> lg_pg;
+    const int w = tid & ((1 << lg_pg) - 1);
+    const int tau = w & (TG - 1);
+    const int sigma = w >> lgTG;
+    const int other = DIM == 1 ? a.n0 : a.n1;
     const int tpc = TG * fa.NG;
     const int per_slice = other / tpc;
     const int slice = blockIdx.x / per_slice;
     const int t0 = (blockIdx.x - slice * per_slice) * tpc;
-    const int tr = t0 + grp * TG + tau;          // row (dim 1) or column (dim 0)
+    const int tr = t0 + (grp << lgTG) + tau;     // row (dim 1) or column (dim 0)
     float2* __restrict__ Gs = sm + (size_t)grp * n * S;
     const size_t sbase = (size_t)slice * a.n0 * a.n1;
     const float2* __restrict__ in = a.in + sbase;
@@ -52,7 +53,7 @@ fast_pass_kernel(const FastArgs fa) {
 
     // ---- phase A input: x[rc + j s] -> r[rev5(j)] ---------------------------
     float2 r[32];
-    if (a.dim == 0) {
+    if (DIM == 0) {
 #pragma unroll
         for (int j = 0; j < 32; j++) {
             float2 v = in[(size_t)(rc + j * s) * a.n1 + tr];
@@ -62,18 +63,31 @@ fast_pass_kernel(const FastArgs fa) {
     } else {
         // stage the CTA's rows as [e][tau]: lanes run over rows, two lanes per
         // 16-byte pair, so each row contributes a full 32-byte sector per load
-        const int half = n >> 1;
-        const int total = fa.NG * TG * half;
-        for (int u = tid; u < total; u += nthr) {
-            const int tc = u % TG;
-            const int rest = u / TG;
-            const int p = rest % half;
-            const int g = rest / half;
-            const float4 v = __ldg(reinterpret_cast<const float4*>(
-                in + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p));
-            float2* Gg = sm + (size_t)g * n * S;
-            Gg[(2 * p) * S + tc] = make_float2(__fmul_rn(v.x, pre), __fmul_rn(v.y, pre));
-            Gg[(2 * p + 1) * S + tc] = make_float2(__fmul_rn(v.z, pre), __fmul_rn(v.w, pre));
+        // total is a multiple of 8 * nthr (NG * TG * n / 2 = 16 * threads)
+        const int total = fa.NG << (lgTG + L - 1);
+        for (int u0 = tid; u0 < total; u0 += 8 * nthr) {
+            float4 v[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int u = u0 + b * nthr;
+                const int tc = u & (TG - 1);
+                const int rest = u >> lgTG;
+                const int p = rest & ((n >> 1) - 1);
+                const int g = rest >> (L - 1);
+                v[b] = __ldg(reinterpret_cast<const float4*>(
+                    in + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p));
+            }
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int u = u0 + b * nthr;
+                const int tc = u & (TG - 1);
+                const int rest = u >> lgTG;
+                const int p = rest & ((n >> 1) - 1);
+                const int g = rest >> (L - 1);
+                float2* Gg = sm + (size_t)g * n * S;
+                Gg[(2 * p) * S + tc] = make_float2(__fmul_rn(v[b].x, pre), __fmul_rn(v[b].y, pre));
+                Gg[(2 * p + 1) * S + tc] = make_float2(__fmul_rn(v[b].z, pre), __fmul_rn(v[b].w, pre));
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -101,8 +115,7 @@ fast_pass_kernel(const FastArgs fa) {
         const bool two = ast + 1 < L;
         int jA, jB, jC, jD;
         if (two) {
-            const int runs = h >> 3;
-            const int Gi = sigma / runs, rr = sigma - Gi * runs;
+            const int Gi = sigma >> (ast - 3), rr = sigma & ((h >> 3) - 1);
             const int base = 4 * h * Gi + 8 * rr;
 #pragma unroll
             for (int q = 0; q < 4; q++) e0[q] = base + q * h;
@@ -142,28 +155,40 @@ fast_pass_kernel(const FastArgs fa) {
     if (a.epilogue == EPI_UNSCALE || a.epilogue == EPI_UNSCALE_STATS) post = exp2i(-a.st[slice].k);
     else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
     StatAcc acc;
-    if (a.dim == 0) {
+    if (DIM == 0) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i++) {
                 const float2 v = epi_value(R[q][i], a.epilogue, post);
                 out[(size_t)(e0[q] + i) * a.n1 + tr] = v;
-                if (stats) acc.add(v.x, v.y, sh_hist);
+                R[q][i] = v;
             }
+        if (stats) {
+            // one copy of the statistics code: the values go through this
+            // thread's own shared slots and a rolled loop
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+#pragma unroll
+                for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
+#pragma unroll 1
+            for (int t = 0; t < 32; t++) {
+                const float2 v = Gs[(e0[t >> 3] + (t & 7)) * S + tau];
+                acc.add(v.x, v.y, sh_hist);
+            }
+        }
     } else {
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
         __syncthreads();
-        const int half = n >> 1;
-        const int total = fa.NG * TG * half;
+        const int total = fa.NG << (lgTG + L - 1);
         for (int u = tid; u < total; u += nthr) {
-            const int tc = u % TG;
-            const int rest = u / TG;
-            const int p = rest % half;
-            const int g = rest / half;
+            const int tc = u & (TG - 1);
+            const int rest = u >> lgTG;
+            const int p = rest & ((n >> 1) - 1);
+            const int g = rest >> (L - 1);
             const float2* Gg = sm + (size_t)g * n * S;
             const float2 v0 = epi_value(Gg[(2 * p) * S + tc], a.epilogue, post);
             const float2 v1 = epi_value(Gg[(2 * p + 1) * S + tc], a.epilogue, post);
@@ -180,18 +205,38 @@ fast_pass_kernel(const FastArgs fa) {
 
 // Launch geometry: TG transforms per group (8 for n = 2048 so a group fits in
 // shared memory, with a padded stride), NG groups per CTA so that a CTA has
-// about 256 threads (512 for n >= 1024).
+// at least 128 threads (a group of n = 512 has 256, of n >= 1024 has 512).
+// Small CTAs let four of them share an SM and drift apart, so one CTA's loads
+// overlap another's arithmetic.
 inline bool fast_geometry(int n, int other, int* TG, int* S, int* NG, int* threads) {
     if (n < 64 || n > 2048) return false;
     *TG = n == 2048 ? 8 : 16;
     *S = n == 2048 ? 9 : 16;
     const int per_group = *TG * (n / 32);
-    int ng = per_group >= 256 ? 1 : 256 / per_group;
+    int ng = per_group >= 128 ? 1 : 128 / per_group;
     while (ng > 1 && (*TG * ng > other || other % (*TG * ng) != 0)) ng >>= 1;
     if (*TG > other || other % *TG != 0) return false;
     *NG = ng;
     *threads = per_group * ng;
     return *threads <= kMaxThreads;
+}
+
+template <int FMT, int DIM>
+cudaError_t launch_fast_dim(const FastArgs& fa, int logm, int blocks, int threads, size_t smem,
+                            cudaStream_t s) {
+    void (*k)(const FastArgs) = nullptr;
+    switch (logm) {
+        case 0: k = fast_pass_kernel<FMT, 0, DIM>; break;
+        case 1: k = fast_pass_kernel<FMT, 1, DIM>; break;
+        case 2: k = fast_pass_kernel<FMT, 2, DIM>; break;
+        case 3: k = fast_pass_kernel<FMT, 3, DIM>; break;
+        case 4: k = fast_pass_kernel<FMT, 4, DIM>; break;
+        default: return cudaErrorNotSupported;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, threads, smem, s>>>(fa);
+    return cudaGetLastError();
 }
 
 template <int FMT>
@@ -201,19 +246,8 @@ cudaError_t launch_fast_fmt(const FastArgs& fa, int logm, int batch, cudaStream_
     const int threads = fa.TG * (a.n / 32) * fa.NG;
     const int blocks = batch * (other / (fa.TG * fa.NG));
     const size_t smem = (size_t)fa.NG * a.n * fa.S * sizeof(float2);
-    void (*k)(const FastArgs) = nullptr;
-    switch (logm) {
-        case 0: k = fast_pass_kernel<FMT, 0>; break;
-        case 1: k = fast_pass_kernel<FMT, 1>; break;
-        case 2: k = fast_pass_kernel<FMT, 2>; break;
-        case 3: k = fast_pass_kernel<FMT, 3>; break;
-        case 4: k = fast_pass_kernel<FMT, 4>; break;
-        default: return cudaErrorNotSupported;
-    }
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<blocks, threads, smem, s>>>(fa);
-    return cudaGetLastError();
+    return a.dim == 1 ? launch_fast_dim<FMT, 1>(fa, logm, blocks, threads, smem, s)
+                      : launch_fast_dim<FMT, 0>(fa, logm, blocks, threads, smem, s);
 }
 
 }  // namespace fast

@@ -23,8 +23,10 @@ stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st
     const int begin = blockIdx.x * kStatsPtsPerCta;
     const int end = min(begin + kStatsPtsPerCta, npts);
     StatAcc acc;
-    for (int p = begin + 2 * tid; p < end; p += 2 * blockDim.x) {
-        float4 v = __ldg(xs + (p >> 1));
+    for (int base = begin; base < end; base += 2 * blockDim.x) {
+        const int p = base + 2 * tid;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);   // zeros do not count
+        if (p < end) v = __ldg(xs + (p >> 1));
         acc.add(v.x, v.y, sh_hist);
         acc.add(v.z, v.w, sh_hist);
     }

@@ -150,6 +150,40 @@ int mxfft_destroy(mxfft_plan_t plan);
 int mxfft_profile(mxfft_plan_t plan, int enable);
 int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int nkinds);
 
+/*
+ * mxfft_prescale_exponents_noalloc -- allocation-free entry point; the paper
+ * has no counterpart (it is a deployment facility).
+ *
+ * For callers that cannot allocate device memory when they call in: a thread
+ * that runs inside another framework's fixed memory pool, a real-time
+ * acquisition and reconstruction loop that must not reach the CUDA allocator,
+ * or code that has already committed all free device memory.  It computes the
+ * Alg. 1 prescale exponent k of each of `batch` slices (the statistics kernel
+ * of the transforms) without a plan and without any cudaMalloc, cudaFree or
+ * allocating library call.
+ *   in      device pointer to [batch][n0][n1] complex64, 16-byte aligned.
+ *   batch   0 .. MXFFT_NOALLOC_MAX_SLICES; a larger batch returns
+ *           MXFFT_ERR_INVALID because the scratch is a fixed static array
+ *           (split the batch into several calls).
+ *   n0, n1, format, tau, target  as for mxfft_plan, with the plan defaults for
+ *           tau_min and (k_min, k_max).
+ *   k_out   device pointer to `batch` int32 exponents (4-byte aligned),
+ *           written asynchronously on `stream`; a slice holding a non-finite
+ *           magnitude gets 0, like the transforms.
+ * Scratch: one file-scope device array of MXFFT_NOALLOC_MAX_SLICES per-slice
+ * records (about 1.2 MB), which every GPU that loads this library keeps until
+ * the process exits.  Every call uses it and it keeps the last call's
+ * contents; each call clears the records it needs first.  Calls that overlap
+ * on the GPU (two streams, or two host threads without ordering) race on it:
+ * serialise them.
+ * Set-up: the first call on a device, made with that device current, looks up
+ * the array's device address once (cudaGetSymbolAddress); make that first call
+ * before any stream capture.
+ */
+#define MXFFT_NOALLOC_MAX_SLICES 1024
+int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, int format,
+                                     float tau, float target, int32_t *k_out, void *stream);
+
 /* mxfft_status_string -- static description of a status code. */
 const char *mxfft_status_string(int status);
 

@@ -27,7 +27,7 @@ OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC = 0, 1, 2, 3
 # every symbol include/mxfft.h declares
 EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
            "mxfft_roundtrip", "mxfft_get_status", "mxfft_destroy", "mxfft_profile",
-           "mxfft_profile_read", "mxfft_status_string")
+           "mxfft_profile_read", "mxfft_prescale_exponents_noalloc", "mxfft_status_string")
 
 _lock = threading.Lock()
 _lib = None
@@ -62,6 +62,7 @@ def load(path: str | None = None):
         lib.mxfft_destroy.argtypes = [P]
         lib.mxfft_profile.argtypes = [P, I]
         lib.mxfft_profile_read.argtypes = [P, P, P, I]
+        lib.mxfft_prescale_exponents_noalloc.argtypes = [P, I, I, I, I, F, F, P, P]
         lib.mxfft_status_string.argtypes = [I]
         lib.mxfft_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -143,6 +144,18 @@ def mxfft_profile_read(plan):
     if st:
         raise MxfftError(st, "mxfft_profile_read")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+NOALLOC_MAX_SLICES = 1024
+
+
+def mxfft_prescale_exponents_noalloc(in_ptr, batch, n0, n1, fmt, tau, target, k_out_ptr,
+                                     stream=None) -> int:
+    """Alg. 1 exponents of `batch` slices without any device allocation
+    (for callers that cannot allocate at call time); returns the status."""
+    return load().mxfft_prescale_exponents_noalloc(in_ptr, int(batch), int(n0), int(n1),
+                                                   _fmt(fmt), float(tau), float(target),
+                                                   k_out_ptr, stream)
 
 
 def _fmt(fmt) -> int:

@@ -70,14 +70,33 @@ def dist_env():
     return world, rank, local
 
 
+def rank_config_id(w, rank):
+    """Seed key of a rank's slices: every rank transforms its own full batch
+    (weak scaling, independent slices, nothing exchanged on the data path)."""
+    return w["config_id"] * 1000 + rank
+
+
 def make_inputs(w, rank):
     from paper_2512_04317_gb300 import phantom
-    # each rank gets its own slices (weak scaling): distinct config seeds
-    cid = w["config_id"] * 1000 + rank
+    cid = rank_config_id(w, rank)
     ksp = phantom.mri_batch(w["n0"], w["n1"], w["nslices"], w["ncoils"], config_id=cid)
     img = phantom.mri_batch(w["n0"], w["n1"], w["nslices"], w["ncoils"], config_id=cid,
                             domain="image")
     return ksp, img
+
+
+def job_time_ms(local_ms, world, dist=None, device=None):
+    """Job time = the slowest rank's time (max over ranks, one all_reduce)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput_mpts(world, pts_per_rank, transforms, steps, job_ms):
+    """Whole-job points x transforms per second, in millions."""
+    return world * pts_per_rank * transforms * steps / (job_ms * 1e-3) / 1e6
 
 
 def load_peaks():
@@ -301,13 +320,9 @@ def main():
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_ms = float(t.item())
+    t_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evs), world, dist, dev)
     ms_per_step = t_ms / args.steps
-    value = world * pts * TRANSFORMS_PER_STEP * args.steps / (t_ms * 1e-3) / 1e6
+    value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, t_ms)
     launches_per_step = 3 + 5
 
     # ---- per-kernel device time (event pairs on the launch stream) -----------
@@ -354,10 +369,8 @@ def main():
         oi.copy_(yi, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * pts * TRANSFORMS_PER_STEP * e2e_steps / (float(te.item()) * 1e-3) / 1e6
+    te_ms = job_time_ms(e0.elapsed_time(e1), world, dist, dev)
+    e2e_value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, e2e_steps, te_ms)
     bytes_io = 2 * pts * 8
 
     # ---- accuracy and the FP32 comparator (context) ----------------------------

@@ -181,3 +181,22 @@ def test_invalid_arguments_on_device(cuda_device):
     with pytest.raises(mxfft.MxfftError):
         mxfft.mxfft_set_option(p.handle, mxfft.OPT_K_MAX, 127)
     p.close()
+
+
+def test_accuracy_equals_stated_tolerance(cuda_device):
+    # the radix-2 path reproduces the oracle bit for bit, so its accuracy
+    # against FP64 is the stated figure in tests/golden/nrmse_oracle.json
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "nrmse_oracle.json")
+    tol = json.load(open(path))
+    ksp = phantom.mri_batch(128, 128, 1, 1, config_id=1)
+    img = phantom.mri_batch(128, 128, 1, 1, config_id=1, domain="image")
+    got_f, _, _, _ = run_gpu(ksp, "e4m3", 32, "forward")
+    got_r, _, _, _ = run_gpu(img, "e4m3", 32, "roundtrip")
+    ref = np.fft.fft2(ksp.astype(np.complex128))
+    nf = np.linalg.norm(got_f - ref) / np.linalg.norm(ref)
+    nr = np.linalg.norm(got_r - img.astype(np.complex128)) / np.linalg.norm(img)
+    want = tol["single_128x128"]["results"][0]
+    assert abs(nf - want["forward"]["nrmse"]) <= 5e-6
+    assert abs(nr - want["roundtrip"]["nrmse"]) <= 5e-6

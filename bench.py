@@ -323,7 +323,7 @@ def main():
     t_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evs), world, dist, dev)
     ms_per_step = t_ms / args.steps
     value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, t_ms)
-    launches_per_step = 3 + 5
+    launches_per_step = 3 + 6   # forward: stats, rows, cols; round trip: twice that
 
     # ---- per-kernel device time (event pairs on the launch stream) -----------
     mxfft.mxfft_profile(plan.handle, True)

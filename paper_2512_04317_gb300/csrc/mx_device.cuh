@@ -166,12 +166,25 @@ struct StatAcc {
     uint32_t nnz = 0;
     uint32_t nonfinite = 0;
     __device__ __forceinline__ void add(float re, float im, uint32_t* sh_hist) {
-        const uint32_t br = __float_as_uint(re), bi = __float_as_uint(im);
+        const uint32_t br = __float_as_uint(re) & 0x7fffffffu;
+        const uint32_t bi = __float_as_uint(im) & 0x7fffffffu;
+        const uint32_t lo = (uint32_t)(127 - 62) << 23, hi = (uint32_t)(127 + 63) << 23;
         int bin = -1;
-        if (!is_finite_bits(br) || !is_finite_bits(bi)) {
+        if ((br == 0 || (br >= lo && br < hi)) && (bi == 0 || (bi >= lo && bi < hi))) {
+            // |x| = sqrt(re^2 + im^2) exactly as mag_c3 computes it (see
+            // mag_c3_fast); the result is zero or normal, so its bin is its
+            // exponent field shifted by 149 - 127
+            const uint32_t mb = __float_as_uint(
+                __fsqrt_rn(__fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im))));
+            if (mb) {
+                amax_bits = max(amax_bits, mb);
+                nnz++;
+                bin = (int)(mb >> 23) + 22;
+            }
+        } else if (br >= 0x7f800000u || bi >= 0x7f800000u) {
             nonfinite = 1;
         } else {
-            const uint32_t mb = __float_as_uint(mag_c3_fast(re, im));
+            const uint32_t mb = __float_as_uint(mag_c3(re, im));
             if (!is_finite_bits(mb)) {
                 nonfinite = 1;
             } else if (mb != 0) {
@@ -180,10 +193,9 @@ struct StatAcc {
                 bin = ilogb_bits(mb) + 149;
             }
         }
-        const unsigned act = __activemask();
-        if (act == 0xffffffffu) {
+        if (__activemask() == 0xffffffffu) {
             const unsigned same = __match_any_sync(0xffffffffu, bin);
-            if (bin >= 0 && (threadIdx.x & 31) == __ffs(same) - 1)
+            if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1)
                 atomicAdd(&sh_hist[bin], (uint32_t)__popc(same));
         } else if (bin >= 0) {
             atomicAdd(&sh_hist[bin], 1u);

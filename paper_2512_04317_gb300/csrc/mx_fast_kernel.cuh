@@ -21,8 +21,6 @@ template <int FMT, int LOGM, int DIM>
 __global__ void __launch_bounds__(kMaxThreads)
 fast_pass_kernel(const FastArgs fa) {
     extern __shared__ float2 sm[];
-    __shared__ uint32_t sh_hist[kHistBins];
-    __shared__ uint32_t sh_misc[4];
     const PassArgs& a = fa.a;
     const int n = a.n, L = a.logn, TG = fa.TG, S = fa.S;
     const int nthr = blockDim.x, tid = threadIdx.x;
@@ -43,9 +41,6 @@ fast_pass_kernel(const FastArgs fa) {
     const float2* __restrict__ in = a.in + sbase;
     float2* __restrict__ out = a.out + sbase;
     const FmtParams fp = a.fp;
-    const bool stats = a.epilogue == EPI_UNSCALE_STATS;
-    if (stats)
-        for (int b = tid; b < kHistBins; b += nthr) sh_hist[b] = 0;
 
     const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
     const int s = n >> 5;                        // chunk stride of the bit-reversed gather
@@ -152,31 +147,14 @@ fast_pass_kernel(const FastArgs fa) {
 
     // ---- output in natural order ---------------------------------------------
     float post = 1.0f;
-    if (a.epilogue == EPI_UNSCALE || a.epilogue == EPI_UNSCALE_STATS) post = exp2i(-a.st[slice].k);
+    if (a.epilogue == EPI_UNSCALE) post = exp2i(-a.st[slice].k);
     else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
-    StatAcc acc;
     if (DIM == 0) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const float2 v = epi_value(R[q][i], a.epilogue, post);
-                out[(size_t)(e0[q] + i) * a.n1 + tr] = v;
-                R[q][i] = v;
-            }
-        if (stats) {
-            // one copy of the statistics code: the values go through this
-            // thread's own shared slots and a rolled loop
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-#pragma unroll
-                for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
-#pragma unroll 1
-            for (int t = 0; t < 32; t++) {
-                const float2 v = Gs[(e0[t >> 3] + (t & 7)) * S + tau];
-                acc.add(v.x, v.y, sh_hist);
-            }
-        }
+            for (int i = 0; i < 8; i++)
+                out[(size_t)(e0[q] + i) * a.n1 + tr] = epi_value(R[q][i], a.epilogue, post);
     } else {
 #pragma unroll
         for (int q = 0; q < 4; q++)
@@ -194,12 +172,7 @@ fast_pass_kernel(const FastArgs fa) {
             const float2 v1 = epi_value(Gg[(2 * p + 1) * S + tc], a.epilogue, post);
             *reinterpret_cast<float4*>(out + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p) =
                 make_float4(v0.x, v0.y, v1.x, v1.y);
-            if (stats) { acc.add(v0.x, v0.y, sh_hist); acc.add(v1.x, v1.y, sh_hist); }
         }
-    }
-    if (stats) {
-        __syncthreads();
-        stats_flush_and_select(acc, sh_hist, sh_misc, a.st_out + slice, (uint32_t)per_slice, a.kp);
     }
 }
 

@@ -45,7 +45,6 @@ enum PassPrologue { PRO_NONE = 0, PRO_PRESCALE = 1 };
 enum PassEpilogue {
     EPI_RAW = 0,          // store the FP32 stage output
     EPI_UNSCALE = 1,      // store 2^-k * A
-    EPI_UNSCALE_STATS = 2,// store y = 2^-k * A and accumulate Alg. 1 stats of y
     EPI_RT_FINAL = 3      // store 2^(-k - lg_total) * A (k of the inverse)
 };
 
@@ -60,12 +59,11 @@ struct PassArgs {
     const float2* tw;     // twiddle element values, index (h - 1) + j per stage h
     const int8_t* tws;    // twiddle block scale exponent for the same index
     SliceStats* st;       // statistics holding k for the prologue / epilogue
-    SliceStats* st_out;   // statistics accumulated by EPI_UNSCALE_STATS
     int prologue, epilogue;
     int lg_total;         // log2(n0 * n1) for EPI_RT_FINAL
     int fmt;              // element format code (mxfft_format)
     FmtParams fp;
-    KParams kp;           // for the k selection done by EPI_UNSCALE_STATS
+    KParams kp;           // exponent selection parameters of the plan
 };
 
 // Twiddles of stages h = 1..16 (index h - 1 + j) for the register-resident

@@ -128,8 +128,6 @@ __device__ __forceinline__ void mx_butterfly_pair(float2* A, int b0, int nb, int
 __global__ void __launch_bounds__(kPassThreads)
 pass_kernel(PassArgs a) {
     extern __shared__ float2 sm[];
-    __shared__ uint32_t sh_hist[kHistBins];
-    __shared__ uint32_t sh_misc[4];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
     const int n = a.n, logn = a.logn, tpc = a.tpc;
@@ -139,9 +137,6 @@ pass_kernel(PassArgs a) {
     const size_t sbase = (size_t)slice * a.n0 * a.n1;
     const float2* __restrict__ in = a.in + sbase;
     float2* __restrict__ out = a.out + sbase;
-    const bool stats = a.epilogue == EPI_UNSCALE_STATS;
-    if (stats)
-        for (int b = tid; b < kHistBins; b += nthr) sh_hist[b] = 0;
 
     // load (with the Alg. 1 prescale on the first pass) in bit-reversed order
     const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
@@ -182,9 +177,8 @@ pass_kernel(PassArgs a) {
 
     // epilogue: natural order out
     float post = 1.0f;
-    if (a.epilogue == EPI_UNSCALE || a.epilogue == EPI_UNSCALE_STATS) post = exp2i(-a.st[slice].k);
+    if (a.epilogue == EPI_UNSCALE) post = exp2i(-a.st[slice].k);
     else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
-    StatAcc acc;
     for (int idx = tid; idx < total; idx += nthr) {
         int t, i;
         size_t g;
@@ -203,11 +197,6 @@ pass_kernel(PassArgs a) {
             v.y = __fmul_rn(v.y, post);
         }
         out[g] = v;
-        if (stats) acc.add(v.x, v.y, sh_hist);
-    }
-    if (stats) {
-        __syncthreads();
-        stats_flush_and_select(acc, sh_hist, sh_misc, a.st_out + slice, (uint32_t)per_slice, a.kp);
     }
 }
 

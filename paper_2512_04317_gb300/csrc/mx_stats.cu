@@ -23,12 +23,16 @@ stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st
     const int begin = blockIdx.x * kStatsPtsPerCta;
     const int end = min(begin + kStatsPtsPerCta, npts);
     StatAcc acc;
-    for (int base = begin; base < end; base += 2 * blockDim.x) {
-        const int p = base + 2 * tid;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);   // zeros do not count
-        if (p < end) v = __ldg(xs + (p >> 1));
-        acc.add(v.x, v.y, sh_hist);
-        acc.add(v.z, v.w, sh_hist);
+    // two 16-byte loads in flight per thread before their arithmetic
+    for (int base = begin; base < end; base += 4 * blockDim.x) {
+        const int p0 = base + 2 * tid, p1 = p0 + 2 * blockDim.x;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);   // zeros do not count
+        const float4 v0 = p0 < end ? __ldg(xs + (p0 >> 1)) : zero;
+        const float4 v1 = p1 < end ? __ldg(xs + (p1 >> 1)) : zero;
+        acc.add(v0.x, v0.y, sh_hist);
+        acc.add(v0.z, v0.w, sh_hist);
+        acc.add(v1.x, v1.y, sh_hist);
+        acc.add(v1.z, v1.w, sh_hist);
     }
     __syncthreads();
     stats_flush_and_select(acc, sh_hist, sh_misc, st + slice, ctas_per_slice, kp);

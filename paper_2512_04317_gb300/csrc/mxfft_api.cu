@@ -295,10 +295,14 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
     PassArgs cols = pass_args(p, 0, dir0, y, y);
     cols.st = st_f;
     cols.prologue = PRO_NONE;
-    cols.epilogue = op == 2 ? EPI_UNSCALE_STATS : EPI_UNSCALE;
-    cols.st_out = st_i;
+    cols.epilogue = EPI_UNSCALE;
     if ((e = timed_pass(p, cols, batch, s)) != cudaSuccess) return cuda_status(e);
     if (op == 2) {
+        // the inverse's own prescale statistics, on the forward output y
+        ProfRec* rs = prof_begin(p, 0, s);
+        e = launch_stats(y, batch, p->n0, p->n1, st_i, kparams(p), s);
+        prof_end(rs, s);
+        if (e != cudaSuccess) return cuda_status(e);
         PassArgs r2 = pass_args(p, 1, 1, y, y);
         r2.st = st_i;
         r2.prologue = PRO_PRESCALE;

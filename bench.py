@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--path", choices=["radix2", "tc16"], default="radix2",
+                    help="radix2: bit-exact radix-2 MX path; tc16: radix-16 tcgen05 variant")
     return ap.parse_args()
 
 
@@ -293,7 +295,7 @@ def main():
     yk = torch.empty_like(xk)
     yi = torch.empty_like(xi)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"])
+    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"], path=args.path)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -336,7 +338,7 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
     avg_ms = dom_ms / max(dom_n, 1)
-    bytes_per_launch = ALG_BYTES_PER_PT * pts if dom == "pass_kernel" else 8 * pts
+    bytes_per_launch = 8 * pts if dom == "stats_kernel" else ALG_BYTES_PER_PT * pts
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     peak, peak_src = load_peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -405,7 +407,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "n0": n0, "n1": n1,
+            "config": {"workload": args.workload, "desc": w["desc"], "path": args.path,
+                       "n0": n0, "n1": n1,
                        "batch_per_gpu": batch, "format": w["fmt"], "k": w["k"],
                        "transforms_per_step": TRANSFORMS_PER_STEP,
                        "l2": "flushed between steps (256 MiB write)",

@@ -61,8 +61,15 @@ typedef enum {
                                Default 2^-10 (e4m3, FP6, FP4), 2^-12 (e5m2). */
     MXFFT_OPT_K_MIN = 1,    /* lower clip k_min of Alg. 1, integer in [-126, 126]; default -126 */
     MXFFT_OPT_K_MAX = 2,    /* upper clip k_max of Alg. 1, integer in [-126, 126]; default 126 */
-    MXFFT_OPT_GENERIC = 3   /* 1: run every pass on the generic shared-memory kernel instead of
+    MXFFT_OPT_GENERIC = 3,  /* 1: run every pass on the generic shared-memory kernel instead of
                                the register-resident one (same results; for testing); default 0 */
+    MXFFT_OPT_PATH = 4      /* 0: radix-2 MX path (Alg. 2 in every butterfly, bit-exact with the
+                               oracle), the default.  1: tensor-core variant: radix-16 sub-DFTs
+                               as MXFP8 matrix products on tcgen05 (FP32 accumulation), each
+                               16-point input vector one MX block (k must be 32), MX-quantised
+                               twiddles between the radix-16 stages; approximate, not bit-exact.
+                               Needs n0, n1 in {256, 512} and format E4M3 or E5M2, else
+                               MXFFT_ERR_UNSUPPORTED. */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;
@@ -126,8 +133,10 @@ int mxfft_roundtrip(mxfft_plan_t plan, const void *in, void *out, int batch,
  *   k_out         nullable; receives the prescale exponents of the last call:
  *                 [batch] for forward/inverse, [batch][2] (forward k, inverse
  *                 k) for the round trip.
- * Returns MXFFT_ERR_NONFINITE when bit 0 is set, else MXFFT_OK (or a CUDA
- * error).
+ *                 bit 1 = a bounded wait of the tensor-core path gave up (its
+ *                 output is undefined).
+ * Returns MXFFT_ERR_NONFINITE when bit 0 is set, MXFFT_ERR_TIMEOUT when bit 1
+ * is set, else MXFFT_OK (or a CUDA error).
  */
 int mxfft_get_status(mxfft_plan_t plan, int *device_flags, int32_t *k_out);
 
@@ -144,7 +153,7 @@ int mxfft_destroy(mxfft_plan_t plan);
  * and the launch count launches[i], and clears the records.  Kinds:
  * 0 = statistics kernel (Alg. 1), 1 = generic MX butterfly pass kernel,
  * 2 = register-resident MX butterfly pass kernel (rows and columns of
- * length 64..2048 with k <= 32).  Returns MXFFT_ERR_INVALID for a NULL plan
+ * length 64..2048 with k <= 32), 3 = tensor-core radix-16 pass kernel.  Returns MXFFT_ERR_INVALID for a NULL plan
  * or nkinds < 1.
  */
 int mxfft_profile(mxfft_plan_t plan, int enable);

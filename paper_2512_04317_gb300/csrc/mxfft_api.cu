@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "mx_internal.h"
 #include "mxfft.h"
@@ -34,6 +35,11 @@ struct mxfft_plan_s {
     uint32_t* d_twh[2][2];     // [axis][dir] f16x2 twiddle element values
     TwA twa[2][2];             // [axis][dir] stages h <= 16 for the register pass
     int force_generic;         // 1: always use the generic pass kernel
+    int path;                  // 0 radix-2 MX, 1 tensor-core radix-16
+    uint8_t* d_bmat[2];        // [dir] tensor-core DFT matrix codes (core-matrix layout)
+    float2* d_twA[2][2];       // [axis][dir] radix-16 stage twiddles
+    float2* d_twC[2][2];       // [axis][dir] twiddles before the radix-2 stage (n = 512)
+    int* d_err;                // device flag: a bounded wait gave up
     SliceStats* d_st;          // 2 * st_cap records: forward, inverse
     int st_cap;
     int last_batch, last_op;   // of the last transform
@@ -154,6 +160,31 @@ void build_twiddles(int n, int m, const FmtHost& f, std::vector<float2>& fwd,
     }
 }
 
+// cos and sin of 2 pi j / N for any 0 <= j < N.
+void unit_root_full(long j, long N, double* c, double* s) {
+    if (2 * j < N) { unit_root(j, N, c, s); return; }
+    unit_root(j - N / 2, N, c, s);
+    *c = -*c;
+    *s = -*s;
+}
+
+// MX block of 16 twiddles exp(sgn i 2 pi (m idx) / N), idx = 0..15: shared
+// exponent from the block maximum, element values back-scaled (exact).
+void twiddle_block16(long m, long N, int sgn, const FmtHost& f, float2* out) {
+    double c[16], sn[16], amax = 0.0;
+    for (int i = 0; i < 16; i++) {
+        unit_root_full((m * i) % N, N, &c[i], &sn[i]);
+        sn[i] *= sgn;
+        amax = std::fmax(amax, std::fmax(std::fabs(c[i]), std::fabs(sn[i])));
+    }
+    int ex;
+    std::frexp(amax, &ex);
+    const int sc = (ex - 1) - f.emax;
+    for (int i = 0; i < 16; i++)
+        out[i] = make_float2((float)std::ldexp(q_host(std::ldexp(c[i], -sc), f), sc),
+                             (float)std::ldexp(q_host(std::ldexp(sn[i], -sc), f), sc));
+}
+
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return MXFFT_OK;
     if (e == cudaErrorMemoryAllocation) return MXFFT_ERR_NOMEM;
@@ -161,6 +192,14 @@ int cuda_status(cudaError_t e) {
 }
 
 void free_plan_device(mxfft_plan_s* p) {
+    for (int d = 0; d < 2; d++) {
+        if (p->d_bmat[d]) cudaFree(p->d_bmat[d]);
+        for (int a = 0; a < 2; a++) {
+            if (p->d_twA[a][d]) cudaFree(p->d_twA[a][d]);
+            if (p->d_twC[a][d]) cudaFree(p->d_twC[a][d]);
+        }
+    }
+    if (p->d_err) cudaFree(p->d_err);
     for (int a = 0; a < 2; a++) {
         for (int d = 0; d < 2; d++) {
             if (p->d_tw[a][d]) cudaFree(p->d_tw[a][d]);
@@ -186,6 +225,82 @@ int ensure_stats(mxfft_plan_s* p, int batch) {
     if (e != cudaSuccess) { p->d_st = nullptr; return cuda_status(e); }
     p->st_cap = cap;
     return MXFFT_OK;
+}
+
+// Real 32 x 32 matrix of the 16-point DFT (sign sgn) for interleaved re/im
+// vectors, each output row an MX block: element codes in the K-major
+// core-matrix layout of the tensor-core B operand, and the row scales.
+void build_dft16_matrix(int sgn, int fmt, const FmtHost& f, std::vector<uint8_t>& codes,
+                        std::vector<float>& scales) {
+    codes.assign(1024, 0);
+    scales.assign(32, 0.f);
+    for (int m = 0; m < 16; m++) {
+        double row[2][32];
+        for (int j = 0; j < 16; j++) {
+            double c, s;
+            unit_root_full((long)(j * m) % 16, 16, &c, &s);
+            s *= sgn;                                  // W = c + i s
+            row[0][2 * j] = c;  row[0][2 * j + 1] = -s;    // Re y: a c - b s
+            row[1][2 * j] = s;  row[1][2 * j + 1] = c;     // Im y: a s + b c
+        }
+        for (int part = 0; part < 2; part++) {
+            const int nrow = 2 * m + part;
+            double amax = 0.0;
+            for (int k = 0; k < 32; k++) amax = std::fmax(amax, std::fabs(row[part][k]));
+            int ex;
+            std::frexp(amax, &ex);
+            const int sc = (ex - 1) - f.emax;
+            scales[nrow] = (float)std::ldexp(1.0, sc);
+            for (int k = 0; k < 32; k++) {
+                const float q = (float)q_host(std::ldexp(row[part][k], -sc), f);
+                uint8_t code;
+                if (fmt == MXFFT_E4M3) { __nv_fp8_e4m3 v(q); std::memcpy(&code, &v, 1); }
+                else { __nv_fp8_e5m2 v(q); std::memcpy(&code, &v, 1); }
+                codes[(nrow >> 3) * 256 + (k >> 4) * 128 + (nrow & 7) * 16 + (k & 15)] = code;
+            }
+        }
+    }
+}
+
+template <class T>
+int upload(T** dst, const std::vector<T>& v) {
+    int rc = cuda_status(cudaMalloc(dst, sizeof(T) * v.size()));
+    if (rc == MXFFT_OK)
+        rc = cuda_status(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return rc;
+}
+
+// Tables of the tensor-core path (built when the path is selected).
+int build_tc16_tables(mxfft_plan_s* p) {
+    FmtHost f;
+    fmt_host(p->fmt, &f);
+    int rc = MXFFT_OK;
+    for (int d = 0; d < 2 && rc == MXFFT_OK; d++) {
+        if (p->d_bmat[d]) continue;
+        const int sgn = d == 0 ? -1 : 1;
+        std::vector<uint8_t> codes;
+        std::vector<float> scales;
+        build_dft16_matrix(sgn, p->fmt, f, codes, scales);
+        // the kernel folds the row scales into one constant: every row of the
+        // matrix holds an entry of magnitude 1, so each row scale is 2^-emax
+        for (float sc : scales)
+            if (sc != (float)std::ldexp(1.0, -f.emax)) return MXFFT_ERR_UNSUPPORTED;
+        rc = upload(&p->d_bmat[d], codes);
+        for (int axis = 0; axis < 2 && rc == MXFFT_OK; axis++) {
+            const int n = axis == 0 ? p->n0 : p->n1;
+            const int r = n / 256, M = 16 * r;
+            std::vector<float2> twa((size_t)M * 16), twc((size_t)std::max(r, 1) * 16);
+            for (int j2 = 0; j2 < M; j2++) twiddle_block16(j2, n, sgn, f, &twa[(size_t)j2 * 16]);
+            for (int j22 = 0; j22 < r; j22++) twiddle_block16(j22, M, sgn, f, &twc[(size_t)j22 * 16]);
+            rc = upload(&p->d_twA[axis][d], twa);
+            if (rc == MXFFT_OK) rc = upload(&p->d_twC[axis][d], twc);
+        }
+    }
+    if (rc == MXFFT_OK && !p->d_err) {
+        rc = cuda_status(cudaMalloc(&p->d_err, sizeof(int)));
+        if (rc == MXFFT_OK) rc = cuda_status(cudaMemset(p->d_err, 0, sizeof(int)));
+    }
+    return rc;
 }
 
 KParams kparams(const mxfft_plan_s* p) {
@@ -240,10 +355,35 @@ void prof_end(ProfRec* r, cudaStream_t s) {
     if (r) cudaEventRecord(r->b, s);
 }
 
-// The register-resident kernel where it applies (n in [64, 2048], m <= 16),
-// else the generic shared-memory kernel.
+// The tensor-core pass when that path is selected, else the register-resident
+// kernel where it applies (n in [64, 2048], m <= 16), else the generic
+// shared-memory kernel.
 cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
     const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
+    if (p->path == 1) {
+        Tc16Args t;
+        t.in = a.in;
+        t.out = a.out;
+        t.n0 = a.n0;
+        t.n1 = a.n1;
+        t.dim = a.dim;
+        t.n = a.n;
+        t.r = a.n / 256;
+        t.bmat = p->d_bmat[dir];
+        t.twA = p->d_twA[a.dim][dir];
+        t.twC = p->d_twC[a.dim][dir];
+        t.st = a.st;
+        t.prologue = a.prologue;
+        t.epilogue = a.epilogue;
+        t.lg_total = a.lg_total;
+        const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
+        t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+        t.err = p->d_err;
+        ProfRec* r = prof_begin(p, 3, s);
+        cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
+        prof_end(r, s);
+        return e;
+    }
     const bool fast = !p->force_generic && fast_pass_supported(a);
     ProfRec* r = prof_begin(p, fast ? 2 : 1, s);
     cudaError_t e = fast ? launch_fast_pass(a, p->d_twh[a.dim][dir], p->twa[a.dim][dir], batch, s)
@@ -422,6 +562,17 @@ int mxfft_set_option(mxfft_plan_t p, int key, double value) {
             if (key == MXFFT_OPT_K_MIN) p->kmin = v; else p->kmax = v;
             return MXFFT_OK;
         }
+        case MXFFT_OPT_PATH: {
+            if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
+            if (value == 0.0) { p->path = 0; return MXFFT_OK; }
+            if (p->kblk != 32 || !tc16_supported(p->n1, p->n0, p->fmt) ||
+                !tc16_supported(p->n0, p->n1, p->fmt))
+                return MXFFT_ERR_UNSUPPORTED;
+            const int rc = build_tc16_tables(p);
+            if (rc) return rc;
+            p->path = 1;
+            return MXFFT_OK;
+        }
         case MXFFT_OPT_GENERIC:
             if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
             p->force_generic = value != 0.0;
@@ -470,7 +621,14 @@ int mxfft_get_status(mxfft_plan_t p, int* device_flags, int32_t* k_out) {
             }
         }
     }
+    if (p->d_err) {
+        int herr = 0;
+        e = cudaMemcpy(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (herr) flags |= 2;
+    }
     if (device_flags) *device_flags = flags;
+    if (flags & 2) return MXFFT_ERR_TIMEOUT;
     return (flags & 1) ? MXFFT_ERR_NONFINITE : MXFFT_OK;
 }
 

@@ -22,7 +22,7 @@ MXFFT_ERR_NONFINITE = 5
 MXFFT_ERR_TIMEOUT = 6
 
 FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4}
-OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC = 0, 1, 2, 3
+OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH = 0, 1, 2, 3, 4
 
 # every symbol include/mxfft.h declares
 EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
@@ -132,7 +132,7 @@ def mxfft_profile(plan, enable: bool) -> None:
         raise MxfftError(st, "mxfft_profile")
 
 
-PROFILE_KINDS = ("stats_kernel", "pass_kernel", "fast_pass_kernel")
+PROFILE_KINDS = ("stats_kernel", "pass_kernel", "fast_pass_kernel", "tc16_pass_kernel")
 
 
 def mxfft_profile_read(plan):
@@ -170,7 +170,8 @@ class Plan:
 
     def __init__(self, n0: int, n1: int, fmt="e4m3", k: int = 32, tau: float = 1e-3,
                  target: float = 0.5, tau_min: float | None = None,
-                 kmin: int | None = None, kmax: int | None = None, generic: bool = False):
+                 kmin: int | None = None, kmax: int | None = None, generic: bool = False,
+                 path: str = "radix2"):
         self.n0, self.n1, self.fmt, self.k = int(n0), int(n1), fmt, int(k)
         self.handle = mxfft_plan(n0, n1, fmt, k, tau, target)
         self._last = (0, 0)   # (batch, op)
@@ -182,6 +183,11 @@ class Plan:
             mxfft_set_option(self.handle, OPT_K_MAX, kmax)
         if generic:
             mxfft_set_option(self.handle, OPT_GENERIC, 1)
+        if path not in ("radix2", "tc16"):
+            raise ValueError(path)
+        if path == "tc16":
+            mxfft_set_option(self.handle, OPT_PATH, 1)
+        self.path = path
 
     def _run(self, name, x, out):
         import torch

@@ -1,0 +1,124 @@
+"""numpy emulation of the tensor-core radix-16 variant (MXFFT_OPT_PATH = 1),
+written from its description: four-step n = 16 x 16 r, each 16-point input
+vector one MX block, the real 32 x 32 DFT matrix quantised with one shared
+scale per output row, products exact and accumulated in FP64 (the hardware
+accumulates 32 exact products in FP32, so results agree to ~1e-7 relative),
+MX-quantised twiddles multiplied in FP32.  Uses the oracle's element rounding
+and Alg. 1 (test infrastructure only)."""
+import numpy as np
+
+import oracle
+
+EMAX = {"e4m3": 8, "e5m2": 15}
+
+
+def _scale_exp(amax, emax):
+    s = np.zeros(amax.shape, np.int64)
+    nz = amax > 0
+    s[nz] = np.floor(np.log2(amax[nz].astype(np.float64))).astype(np.int64) - emax
+    return np.clip(s, -127, 127)
+
+
+def _q(x, fmt):
+    return oracle.quantize(np.ascontiguousarray(x, np.float32), fmt).astype(np.float64)
+
+
+def twiddle_block(m, N, sgn, fmt):
+    """16 MX-quantised twiddles exp(sgn 2 pi i m idx / N), back-scaled."""
+    idx = np.arange(16)
+    ang = 2 * np.pi * ((m * idx) % N) / N
+    c, s = np.cos(ang), sgn * np.sin(ang)
+    c[np.abs(c) < 1e-12] = 0.0
+    s[np.abs(s) < 1e-12] = 0.0
+    amax = max(np.abs(c).max(), np.abs(s).max())
+    sc = int(np.floor(np.log2(amax))) - EMAX[fmt]
+    qc = oracle.quantize(np.ldexp(c, -sc), fmt) * 2.0 ** sc
+    qs = oracle.quantize(np.ldexp(s, -sc), fmt) * 2.0 ** sc
+    return qc.astype(np.float32) + 1j * qs.astype(np.float32)
+
+
+def dft16_matrix(sgn, fmt):
+    """(element values [32, 32], row scale exponents [32])."""
+    F = np.zeros((32, 32))
+    for m in range(16):
+        for j in range(16):
+            ang = 2 * np.pi * ((j * m) % 16) / 16
+            c, s = np.cos(ang), sgn * np.sin(ang)
+            c = 0.0 if abs(c) < 1e-12 else c
+            s = 0.0 if abs(s) < 1e-12 else s
+            F[2 * m, 2 * j], F[2 * m, 2 * j + 1] = c, -s
+            F[2 * m + 1, 2 * j], F[2 * m + 1, 2 * j + 1] = s, c
+    sF = _scale_exp(np.abs(F).max(axis=1), EMAX[fmt])
+    Fq = oracle.quantize(np.ldexp(F, -sF[:, None]), fmt)
+    return Fq, sF
+
+
+def dft16_mx(V, fmt, sgn):
+    """V: complex64 [..., 16] -> complex64 [..., 16]."""
+    r = np.stack([V.real, V.imag], -1).reshape(V.shape[:-1] + (32,)).astype(np.float32)
+    sv = _scale_exp(np.abs(r).max(-1), EMAX[fmt])
+    q = _q(r * np.exp2(-sv)[..., None].astype(np.float32), fmt)
+    Fq, sF = dft16_matrix(sgn, fmt)
+    D = (q @ Fq.T).astype(np.float32)                    # exact products, FP32 result
+    y = (D * np.exp2(sF).astype(np.float32)) * np.exp2(sv)[..., None].astype(np.float32)
+    return (y[..., 0::2] + 1j * y[..., 1::2]).astype(np.complex64)
+
+
+def cmul32(w, y):
+    w = w.astype(np.complex64)
+    y = y.astype(np.complex64)
+    wr, wi, yr, yi = (np.float32(0) + a for a in (w.real, w.imag, y.real, y.imag))
+    return ((wr * yr - wi * yi) + 1j * (wr * yi + wi * yr)).astype(np.complex64)
+
+
+def fft1d(x, fmt, sgn):
+    """x: complex64 [..., n], n in {256, 512}; transforms the last axis."""
+    n = x.shape[-1]
+    r = n // 256
+    M = 16 * r
+    X = x.reshape(x.shape[:-1] + (16, M))                # [j1][j2]
+    V = np.swapaxes(X, -1, -2)                          # [j2][j1]
+    Y = dft16_mx(V, fmt, sgn)                           # [j2][k1]
+    TA = np.stack([twiddle_block(j2, n, sgn, fmt) for j2 in range(M)])  # [j2][k1]
+    Y = cmul32(TA, Y)
+    Y = np.swapaxes(Y, -1, -2)                          # [k1][j2]
+    if r == 1:
+        Z = dft16_mx(Y, fmt, sgn)                       # [k1][k2]
+        return np.swapaxes(Z, -1, -2).reshape(x.shape)  # X[k1 + 16 k2]
+    Yr = Y.reshape(Y.shape[:-1] + (16, r))              # [k1][j21][j22]
+    U = dft16_mx(np.swapaxes(Yr, -1, -2), fmt, sgn)     # [k1][j22][k21]
+    TC = np.stack([twiddle_block(j22, M, sgn, fmt) for j22 in range(r)])   # [j22][k21]
+    U = cmul32(TC, U)
+    a, b = U[..., 0, :], U[..., 1, :]                   # [k1][k21]
+    s0 = (a + b).astype(np.complex64)
+    s1 = (a - b).astype(np.complex64)
+    out = np.stack([s0, s1], -1)                        # [k1][k21][k22]
+    return np.swapaxes(out, -1, -3).reshape(x.shape)    # [k22][k21][k1]: k = k1 + 16 (k21 + 16 k22)
+
+
+def mxfft2d(x, fmt="e4m3", op="forward"):
+    """Batch [..., n0, n1] complex64; same prescale (Alg. 1) as the library."""
+    x = np.asarray(x, np.complex64)
+    out = np.empty_like(x)
+    flat = x.reshape((-1,) + x.shape[-2:])
+    res = out.reshape(flat.shape)
+    for i, s in enumerate(flat):
+        def transform(z, sgn):
+            k, _ = oracle.prescale_k(z, fmt)
+            zs = (z * np.float32(2.0 ** k)).astype(np.complex64)
+            zs = fft1d(zs, fmt, sgn)                                         # rows
+            zs = np.swapaxes(fft1d(np.swapaxes(zs, 0, 1).copy(), fmt, sgn), 0, 1)   # columns
+            return zs, k
+        if op == "forward":
+            y, k = transform(s, -1)
+            res[i] = y * np.float32(2.0 ** -k)
+        elif op == "inverse":
+            y, k = transform(s, +1)
+            res[i] = y * np.float32(2.0 ** -k)
+        else:
+            y, k = transform(s, -1)
+            y = (y * np.float32(2.0 ** -k)).astype(np.complex64)
+            z, ki = transform(y, +1)
+            lg = int(np.log2(s.shape[0] * s.shape[1]))
+            res[i] = z * np.float32(2.0 ** (-ki - lg))
+    return out

@@ -1,0 +1,75 @@
+"""Tensor-core radix-16 variant (MXFFT_OPT_PATH = 1): radix-16 sub-DFTs as
+MXFP8 tcgen05 matrix products.  Not bit-exact with the radix-2 oracle by
+design; checked (1) against a numpy emulation of the same algorithm to FP32
+accumulation-order level, and (2) against FP64 with the stated tolerance:
+NRMSE <= 1.10 x the radix-2 oracle's NRMSE on the same input."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_04317_gb300 import phantom
+from parity_util import run_gpu
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+import tc16_ref  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def run_tc16(x, fmt, op):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    xt = torch.from_numpy(np.ascontiguousarray(x, np.complex64)).cuda()
+    with mxfft.Plan(x.shape[-2], x.shape[-1], fmt, 32, path="tc16") as p:
+        y = getattr(p, op)(xt)
+        torch.cuda.synchronize()
+        st, flags, _ = p.status()
+    assert st == 0 and flags == 0, (st, flags)
+    return y.cpu().numpy()
+
+
+def nrmse(a, ref):
+    return float(np.linalg.norm(a.astype(np.complex128) - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (512, 256)])
+@pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
+@pytest.mark.parametrize("op", ["forward", "inverse", "roundtrip"])
+def test_tc16_matches_emulation(n0, n1, fmt, op, cuda_device):
+    x = phantom.mri_batch(n0, n1, 2, 1, config_id=31, domain="image" if op == "roundtrip" else "kspace")
+    got = run_tc16(x, fmt, op)
+    want = tc16_ref.mxfft2d(x, fmt, op)
+    assert np.isfinite(got).all()
+    # FP32 accumulation order differs from the emulation; a 1-ulp difference can
+    # flip a later rounding, so agreement is ~1e-5, while an index error gives ~1
+    assert nrmse(got, want.astype(np.complex128)) < 1e-4
+
+
+@pytest.mark.parametrize("n", [256, 512])
+@pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
+def test_tc16_within_stated_tolerance(n, fmt, cuda_device):
+    ksp = phantom.mri_batch(n, n, 4, 1, config_id=32)
+    img = phantom.mri_batch(n, n, 4, 1, config_id=32, domain="image")
+    ref = np.fft.fft2(ksp.astype(np.complex128))
+    r2f = nrmse(oracle.mxfft2d(ksp, fmt, 32)[0], ref)
+    r2r = nrmse(oracle.mxfft2d(img, fmt, 32, op="roundtrip")[0], img.astype(np.complex128))
+    tcf = nrmse(run_tc16(ksp, fmt, "forward"), ref)
+    tcr = nrmse(run_tc16(img, fmt, "roundtrip"), img.astype(np.complex128))
+    assert tcf <= 1.10 * r2f, (tcf, r2f)
+    assert tcr <= 1.10 * r2r, (tcr, r2r)
+
+
+def test_tc16_option_validation(cuda_device):
+    from paper_2512_04317_gb300 import mxfft
+    for args in [(128, 256, "e4m3", 32), (256, 256, "e2m3", 32), (256, 256, "e4m3", 16)]:
+        with pytest.raises(mxfft.MxfftError) as ei:
+            mxfft.Plan(*args, path="tc16")
+        assert ei.value.status == mxfft.MXFFT_ERR_UNSUPPORTED
+    # same plan can switch back to the bit-exact path
+    p = mxfft.Plan(256, 256, "e4m3", 32, path="tc16")
+    mxfft.mxfft_set_option(p.handle, mxfft.OPT_PATH, 0)
+    p.close()

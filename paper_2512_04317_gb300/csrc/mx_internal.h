@@ -78,6 +78,7 @@ struct Tc16Args {
     const float2* in;
     float2* out;
     int n0, n1, dim, n, r;            // n = 256 r
+    int batch;                        // slices (set by launch_tc16_pass)
     const uint8_t* bmat;              // B operand: 32 x 32 element codes, core-matrix layout (1 KB)
     const float2* twA;                // [j2 < 16 r][k1 < 16] twiddle element values x 2^s
     const float2* twC;                // [j22 < r][k21 < 16] (r > 1)
@@ -96,7 +97,8 @@ cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s);
 bool fast_pass_supported(const PassArgs& a);
 cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                              cudaStream_t s);
-// Tensor-core radix-16 pass: n in {256, 512}, 8-bit formats, other % 8 == 0.
+// Tensor-core radix-16 pass: n in {256, 512}, 8-bit formats, other a multiple
+// of 4096 / n.
 bool tc16_supported(int n, int other, int fmt);
 cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s);
 

@@ -18,11 +18,19 @@
 // to the FP32 result when it is read back (tcgen05.ld).  Twiddles are MX
 // element values (one block per 16 twiddles) multiplied in FP32.
 //
-// A CTA (128 threads) owns T = 8 transforms in shared memory; thread i owns
-// row i of the MMA (one vector) in every round.  The only wait is on the MMA
-// completion mbarrier, with an iteration limit: on time-out the kernel sets
-// the plan's error flag, waits once more (bounded) for its own MMA, frees its
-// tensor memory and finishes without using the result.
+// Work unit: a tile of 4096 points (T = 4096 / n whole transforms of one
+// slice), which is exactly 256 vectors per radix-16 stage, so a CTA of 256
+// threads runs each stage as one round of two MMAs (rows 0-127 and 128-255,
+// accumulators in tensor-memory columns 0-31 and 32-63); thread i owns
+// vector i.  CTAs are persistent: each walks tiles blockIdx.x, + gridDim.x,
+// ... and copies the next tile into its second shared buffer (cp.async, 16 B
+// per thread and copy) while it transforms the current one, so that HBM
+// reads overlap the MMA rounds.  The shared layouts are padded so that every
+// access pattern below is free of bank conflicts (see slot_row / slot_col).
+//
+// The only spin wait is on the MMA completion mbarrier, with an iteration
+// limit: on time-out the kernel sets the plan's error flag, waits once more
+// (bounded) for its own MMA, frees its tensor memory and finishes.
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -31,12 +39,61 @@
 namespace mxfft {
 namespace tc16 {
 
-constexpr int kThreads = 128;
-constexpr int kT = 8;                 // transforms per CTA
-constexpr uint32_t kTmemCols = 32;
+constexpr int kThreads = 256;
+constexpr int kTilePts = 4096;        // points per tile = 256 vectors x 16
+constexpr uint32_t kTmemCols = 64;    // two 128 x 32 FP32 accumulators
 constexpr int kWaitLimit = 1 << 22;
+// Dynamic shared memory: A operand (2 x 128 rows x 32 B), B operand (32 x 32
+// B), twiddles (rows of 16 padded to 18 values so that a quarter-warp's 16-byte
+// reads of 8 consecutive rows hit distinct banks), then the two tile buffers.
+constexpr int kTwRow = 18;
+constexpr int kOffB = 8192;
+constexpr int kOffTwA = kOffB + 1024;                  // up to 32 rows
+constexpr int kOffTwC = kOffTwA + 32 * kTwRow * 8;     // up to 2 rows
+constexpr int kOffBuf = kOffTwC + 2 * kTwRow * 8;
+static_assert(kOffBuf % 16 == 0, "16-byte aligned cp.async destinations");
 
 using Args = Tc16Args;
+
+// Geometry of one transform length n = 2^LOGN.
+template <int LOGN>
+struct Geo {
+    static constexpr int n = 1 << LOGN;
+    static constexpr int r = n / 256;
+    static constexpr int M = 16 * r;
+    static constexpr int LGM = r == 1 ? 4 : 5;
+    static constexpr int T = kTilePts / n;          // transforms per tile (16 or 8)
+    static constexpr int LGT = T == 16 ? 4 : 3;
+    // rows pass: [t][e], 2 pad slots after every M elements
+    static constexpr int TS = n + 2 * (n / M);
+    static constexpr int ROW_SLOTS = T * TS;
+    // columns pass: [e][t]; with T = 8, 8 pad slots after every 16 elements
+    static constexpr int COL_SLOTS = n * T + (T == 8 ? 8 * (n / 16) : 0);
+    static constexpr int BUF_SLOTS = ROW_SLOTS > COL_SLOTS ? ROW_SLOTS : COL_SLOTS;
+    static_assert(T * M == kThreads, "one vector per thread per stage");
+};
+
+// Slot (8 bytes) of element e of transform t.  Rows pass: round A reads 16
+// consecutive elements per half-warp; round C1 reads each thread's own group
+// of M elements as 16-byte pairs (r = 1: chunks 9 k1 + c, distinct mod 8 over
+// a quarter-warp) or 8-byte elements (r = 2: slots 34 k1 + 2 j + j22, distinct
+// mod 16 over a half-warp).  Columns pass: a half-warp spans 16 transforms
+// (T = 16) or 8 transforms x two elements 16 apart (T = 8, the pad puts them
+// in opposite bank halves).
+template <int LOGN>
+__device__ __forceinline__ int slot_row(int t, int e) {
+    using G = Geo<LOGN>;
+    return t * G::TS + e + 2 * (e >> G::LGM);
+}
+template <int LOGN>
+__device__ __forceinline__ int slot_col(int t, int e) {
+    using G = Geo<LOGN>;
+    return e * G::T + (G::T == 8 ? 8 * (e >> 4) : 0) + t;
+}
+template <int LOGN, int DIM>
+__device__ __forceinline__ int slot(int t, int e) {
+    return DIM == 1 ? slot_row<LOGN>(t, e) : slot_col<LOGN>(t, e);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -68,15 +125,6 @@ __device__ __forceinline__ float fmax_nan(float a, float b) {
     return d;
 }
 
-// Padded shared index of element e: 16-element groups are 17 slots apart and
-// transforms TS = n + n/16 + 2 slots apart (TS = 2 mod 16).  With 8-byte slots
-// and 32 four-byte banks, every access pattern of the kernel (16 lanes on
-// consecutive elements; 16 lanes on one element of 16 consecutive groups;
-// 8 transforms x 2 groups; 4 transforms x 4 consecutive elements) then touches
-// 16 distinct slots modulo 16, i.e. no bank conflicts.
-__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
-__host__ __device__ constexpr int tstride(int n) { return n + n / 16 + 2; }
-
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase) {
     uint32_t done = 0;
     for (int it = 0; it < kWaitLimit && !done; it++) {
@@ -104,14 +152,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&d)[32]) {
     for (int c = 0; c < 32; c++) d[c] = __uint_as_float(v[c]);
 }
 
-// One MMA round: every thread MX-encodes its 16-element vector into row tid of
-// the A operand, one thread issues the product, all read back their row.
-// Returns the 16 complex DFT outputs (scales applied) in y.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {   // all but the newest group
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Shared state of one CTA's MMA rounds.
+struct Mma {
+    uint8_t* sA;
+    uint32_t sa, sb, mbar, tbase, phase;
+    bool ok;
+};
+
+// One MMA round: every thread MX-encodes its 16-element vector into its row
+// of the A operand (thread i: operand half i / 128, row i % 128), one thread
+// issues both products, all read back their row.  Returns the 16 complex
+// DFT outputs (scales applied) in y.  Ends with a CTA barrier, after which the
+// A operand, the accumulators and the caller's shared-memory writes made
+// before the call may be reused / are visible.
 template <int FMT>
-__device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], uint8_t* sA,
-                                            uint32_t sa_u32, uint32_t sb_u32, uint32_t mbar,
-                                            uint32_t tbase, uint32_t& phase, bool& ok,
-                                            const Args& a, const FmtParams& fp) {
+__device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
+                                            uint32_t idesc, int emax) {
     const int tid = threadIdx.x, warp = tid >> 5;
     float m[16];
 #pragma unroll
@@ -122,7 +191,7 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
         for (int j = 0; j + w < 16; j += 2 * w) m[j] = fmax_nan(m[j], m[j + w]);
     const float A = m[0];
     const bool bad = !(A <= 3.402823466e38f);
-    const int sv = mx_scale_exp(__float_as_uint(A), fp.emax);
+    const int sv = mx_scale_exp(__float_as_uint(A), emax);
     const float inv = exp2i(-sv);
     uint32_t w32[8];
 #pragma unroll
@@ -131,47 +200,50 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
         const uint32_t hi = enc2<FMT>(__fmul_rn(x[2 * j + 1].x, inv), __fmul_rn(x[2 * j + 1].y, inv));
         w32[j] = lo | (hi << 16);
     }
-    // row tid: K bytes 0..15 in core matrix (tid / 8, 0), 16..31 in (tid / 8, 1)
-    uint4* r0 = reinterpret_cast<uint4*>(sA + (tid >> 3) * 256 + (tid & 7) * 16);
-    uint4* r1 = reinterpret_cast<uint4*>(sA + (tid >> 3) * 256 + 128 + (tid & 7) * 16);
-    *r0 = make_uint4(w32[0], w32[1], w32[2], w32[3]);
-    *r1 = make_uint4(w32[4], w32[5], w32[6], w32[7]);
+    // row rr of half h: K bytes 0..15 in core matrix (rr / 8, 0), 16..31 in (rr / 8, 1)
+    const int h = tid >> 7, rr = tid & 127;
+    uint8_t* row = mm.sA + h * 4096 + (rr >> 3) * 256 + (rr & 7) * 16;
+    *reinterpret_cast<uint4*>(row) = make_uint4(w32[0], w32[1], w32[2], w32[3]);
+    *reinterpret_cast<uint4*>(row + 128) = make_uint4(w32[4], w32[5], w32[6], w32[7]);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
-        const uint64_t ad = smem_desc(sa_u32, 128, 256);
-        const uint64_t bd = smem_desc(sb_u32, 128, 256);
+        const uint64_t bd = smem_desc(mm.sb, 128, 256);
+        const uint64_t a0 = smem_desc(mm.sa, 128, 256);
+        const uint64_t a1 = smem_desc(mm.sa + 4096, 128, 256);
         asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
                      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
-                     :: "r"(tbase), "l"(ad), "l"(bd), "r"(a.idesc), "r"(0));
+                     :: "r"(mm.tbase), "l"(a0), "l"(bd), "r"(idesc), "r"(0));
+        asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
+                     " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
+                     :: "r"(mm.tbase + 32u), "l"(a1), "l"(bd), "r"(idesc), "r"(0));
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(mbar));
+                     :: "r"(mm.mbar));
     }
     // tcgen05.ld below is warp-collective: the warp reads only if every lane saw
-    // the product complete
-    const bool done = __all_sync(0xffffffffu, wait_phase(mbar, phase));
-    phase ^= 1u;
+    // the products complete
+    const bool done = __all_sync(0xffffffffu, wait_phase(mm.mbar, mm.phase));
+    mm.phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     float d[32];
     if (done) {
-        tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16), d);
+        // warp w reads lanes 32 (w % 4) .. of accumulator w / 4
+        tmem_ld32(mm.tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 32), d);
     } else {
 #pragma unroll
         for (int c = 0; c < 32; c++) d[c] = 0.f;
-        ok = false;
+        mm.ok = false;
     }
     // D is exact-scaled by the vector's scale and the matrix rows' scale, which
     // is 2^-emax for every row (each row holds an entry of magnitude 1)
-    const float sc = bad ? __int_as_float(0x7fffffff) : exp2i(sv - fp.emax);
+    const float sc = bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         y[k].x = __fmul_rn(d[2 * k], sc);
         y[k].y = __fmul_rn(d[2 * k + 1], sc);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();   // A and D may be reused once every row has been read
 }
 
 __device__ __forceinline__ float2 cmul(float2 w, float2 y) {
@@ -183,27 +255,51 @@ __device__ __forceinline__ float2 scale2(float2 v, float s) {
     return make_float2(__fmul_rn(v.x, s), __fmul_rn(v.y, s));
 }
 
+// Issue the cp.async copies of one tile into buffer buf (8 x 16 B per thread).
+template <int LOGN, int DIM>
+__device__ __forceinline__ void load_tile(const Args& a, int tile, uint32_t buf) {
+    using G = Geo<LOGN>;
+    const int other = DIM == 1 ? a.n0 : a.n1;
+    const int per_slice = other / G::T;
+    const int slice = tile / per_slice;
+    const int t0 = (tile - slice * per_slice) * G::T;
+    const float2* in = a.in + (size_t)slice * a.n0 * a.n1;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int q = threadIdx.x + i * kThreads;      // 16-byte chunk of the tile
+        const float2* src;
+        int t, e;
+        if (DIM == 1) {
+            t = q >> (LOGN - 1);
+            e = 2 * (q & ((G::n >> 1) - 1));
+            src = in + (size_t)(t0 + t) * a.n1 + e;
+        } else {
+            e = q >> (G::LGT - 1);
+            t = 2 * (q & ((G::T >> 1) - 1));
+            src = in + (size_t)e * a.n1 + t0 + t;
+        }
+        cp_async16(buf + 8u * (uint32_t)slot<LOGN, DIM>(t, e), src);
+    }
+}
+
 template <int FMT, int DIM, int LOGN>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 tc16_pass_kernel(const Args a) {
+    using G = Geo<LOGN>;
+    constexpr int r = G::r, M = G::M, T = G::T;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    uint8_t* sA = smem;                                   // 4 KB A operand
-    uint8_t* sB = smem + 4096;                            // 1 KB B operand
-    float2* data = reinterpret_cast<float2*>(smem + 5120);
-    constexpr int n = 1 << LOGN, r = n / 256, M = 16 * r;
-    constexpr int TS = tstride(n);                        // padded transform stride (slots)
+    uint8_t* sB = smem + kOffB;
+    float2* sTwA = reinterpret_cast<float2*>(smem + kOffTwA);
+    float2* sTwC = reinterpret_cast<float2*>(smem + kOffTwC);
+    float2* bufs = reinterpret_cast<float2*>(smem + kOffBuf);
+    const uint32_t buf_u32 = smem_u32(bufs);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int other = DIM == 1 ? a.n0 : a.n1;
-    const int per_slice = other / kT;
-    const int slice = blockIdx.x / per_slice;
-    const int t0 = (blockIdx.x - slice * per_slice) * kT;
-    const size_t sbase = (size_t)slice * a.n0 * a.n1;
-    const float2* __restrict__ in = a.in + sbase;
-    float2* __restrict__ out = a.out + sbase;
-    FmtParams fp;
-    fp.emax = FMT == 0 ? 8 : 15;
+    const int per_slice = other / T;
+    const int ntiles = a.batch * per_slice;
+    const int emax = FMT == 0 ? 8 : 15;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -215,175 +311,225 @@ tc16_pass_kernel(const Args a) {
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (tid < 64) reinterpret_cast<uint4*>(sB)[tid] = __ldg(reinterpret_cast<const uint4*>(a.bmat) + tid);
-
-    // ---- tile in: kT transforms, padded [t][e] layout, prescale on the first pass
-    const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
-    // (kT n / 2 = 1024 n / 256 float4 per CTA: a multiple of 8 x 128 threads)
-    const int quads = kT * (n >> 1);
-    for (int u0 = tid; u0 < quads; u0 += 8 * kThreads) {
-        float4 v[8];
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            const int u = u0 + b * kThreads;
-            const float4* src;
-            if (DIM == 1) {
-                const int t = u / (n >> 1), e = 2 * (u - t * (n >> 1));
-                src = reinterpret_cast<const float4*>(in + (size_t)(t0 + t) * a.n1 + e);
-            } else {
-                const int e = u / (kT >> 1), t = 2 * (u - e * (kT >> 1));
-                src = reinterpret_cast<const float4*>(in + (size_t)e * a.n1 + t0 + t);
-            }
-            v[b] = __ldg(src);
-        }
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            const int u = u0 + b * kThreads;
-            const float2 lo = make_float2(__fmul_rn(v[b].x, pre), __fmul_rn(v[b].y, pre));
-            const float2 hi = make_float2(__fmul_rn(v[b].z, pre), __fmul_rn(v[b].w, pre));
-            if (DIM == 1) {
-                const int t = u / (n >> 1), e = 2 * (u - t * (n >> 1));
-                data[t * TS + pidx(e)] = lo;
-                data[t * TS + pidx(e + 1)] = hi;
-            } else {
-                const int e = u / (kT >> 1), t = 2 * (u - e * (kT >> 1));
-                data[t * TS + pidx(e)] = lo;
-                data[(t + 1) * TS + pidx(e)] = hi;
-            }
-        }
-    }
+    for (int i = tid; i < M * 16; i += kThreads) sTwA[(i >> 4) * kTwRow + (i & 15)] = __ldg(a.twA + i);
+    if (r > 1 && tid < r * 16) sTwC[(tid >> 4) * kTwRow + (tid & 15)] = __ldg(a.twC + tid);
+    if ((int)blockIdx.x < ntiles) load_tile<LOGN, DIM>(a, blockIdx.x, buf_u32);
+    cp_async_commit();
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tbase = tmem_base;
-    const uint32_t sa_u32 = smem_u32(sA), sb_u32 = smem_u32(sB), mb = smem_u32(&mbar);
-    uint32_t phase = 0;
-    bool ok = true;
+    Mma mm;
+    mm.sA = smem;
+    mm.sa = smem_u32(smem);
+    mm.sb = smem_u32(sB);
+    mm.mbar = smem_u32(&mbar);
+    mm.tbase = tmem_base;
+    mm.phase = 0;
+    mm.ok = true;
 
-    // ---- round A: vectors (t, j2), 16 elements x[M j1 + j2] ------------------
-    const int nvec = kT * M;
-    for (int v0 = 0; v0 < nvec; v0 += kThreads) {
-        const int v = v0 + tid;
-        int t, j2;
-        if (DIM == 1) { t = v / M; j2 = v - t * M; } else { j2 = v / kT; t = v - j2 * kT; }
-        float2* d = data + t * TS;
-        float2 x[16], y[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++) x[j] = d[pidx(M * j + j2)];
-        dft16_round<FMT>(x, y, sA, sa_u32, sb_u32, mb, tbase, phase, ok, a, fp);
-        const float4* tw = reinterpret_cast<const float4*>(a.twA + j2 * 16);
-#pragma unroll
-        for (int k = 0; k < 16; k += 2) {
-            const float4 w = __ldg(tw + (k >> 1));
-            d[pidx(M * k + j2)] = cmul(make_float2(w.x, w.y), y[k]);
-            d[pidx(M * (k + 1) + j2)] = cmul(make_float2(w.z, w.w), y[k + 1]);
-        }
-    }
-    __syncthreads();
+    int cur = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, cur ^= 1) {
+        // prefetch the next tile into the other buffer (free since the last
+        // barrier of the previous iteration), then wait for this one
+        const int next = tile + gridDim.x;
+        if (next < ntiles)
+            load_tile<LOGN, DIM>(a, next, buf_u32 + (uint32_t)((cur ^ 1) * G::BUF_SLOTS * 8));
+        cp_async_commit();
+        const int slice = tile / per_slice;
+        const int t0 = (tile - slice * per_slice) * T;
+        // the slice's exponent is fetched while the tile's copies land
+        const int kslice = (a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW) ? a.st[slice].k : 0;
+        cp_async_wait_prev();
+        __syncthreads();
 
-    // ---- round C1: vectors (t, k1, j22), 16 elements Y[M k1 + r j21 + j22] ---
-    float post = 1.0f;
-    if (a.epilogue == EPI_UNSCALE) post = exp2i(-a.st[slice].k);
-    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
-    const bool scale_out = a.epilogue != EPI_RAW;
-    for (int v0 = 0; v0 < nvec; v0 += kThreads) {
-        const int v = v0 + tid;
-        int t, k1, j22;
-        if (DIM == 1) {
-            t = v / M;
-            const int rem = v - t * M;
-            k1 = rem / r;
-            j22 = rem - k1 * r;
-        } else {
-            t = v % kT;
-            const int rem = v / kT;
-            k1 = rem / r;
-            j22 = rem - k1 * r;
-        }
-        float2* d = data + t * TS;
-        float2 x[16], y[16];
+        float2* d = bufs + cur * G::BUF_SLOTS;
+        const size_t sbase = (size_t)slice * a.n0 * a.n1;
+        float2* __restrict__ out = a.out + sbase;
+
+        // ---- round A: vector (t, j2), elements x[M j1 + j2] ----------------
+        {
+            const int v = tid;
+            int t, j2;
+            if (DIM == 1) { t = v >> G::LGM; j2 = v & (M - 1); }
+            else { t = v & (T - 1); j2 = v >> G::LGT; }
+            float2 x[16], y[16];
+            if (a.prologue == PRO_PRESCALE) {
+                const float pre = exp2i(kslice);
 #pragma unroll
-        for (int j = 0; j < 16; j++) x[j] = d[pidx(M * k1 + r * j + j22)];
-        dft16_round<FMT>(x, y, sA, sa_u32, sb_u32, mb, tbase, phase, ok, a, fp);
-        if (r == 1) {
-            // X[k1 + 16 k2]
+                for (int j = 0; j < 16; j++) x[j] = scale2(d[slot<LOGN, DIM>(t, M * j + j2)], pre);
+            } else {
 #pragma unroll
-            for (int k = 0; k < 16; k++) {
-                float2 val = scale_out ? scale2(y[k], post) : y[k];
-                const int e = k1 + 16 * k;
-                if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + e] = val;
-                else out[(size_t)e * a.n1 + t0 + t] = val;
+                for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
             }
-        } else {
-            const float4* tw = reinterpret_cast<const float4*>(a.twC + j22 * 16);
+            dft16_round<FMT>(x, y, mm, a.idesc, emax);
+            const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
-                const float4 w = __ldg(tw + (k >> 1));
-                d[pidx(M * k1 + r * k + j22)] = cmul(make_float2(w.x, w.y), y[k]);
-                d[pidx(M * k1 + r * (k + 1) + j22)] = cmul(make_float2(w.z, w.w), y[k + 1]);
+                const float4 w = tw[k >> 1];
+                d[slot<LOGN, DIM>(t, M * k + j2)] = cmul(make_float2(w.x, w.y), y[k]);
+                d[slot<LOGN, DIM>(t, M * (k + 1) + j2)] = cmul(make_float2(w.z, w.w), y[k + 1]);
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
         }
-    }
-    if (r == 2) {
-        __syncthreads();
-        // ---- C2: radix-2 over j22: X[k1 + 16 (k21 + 16 k22)] ---------------
-        const int items = kT * 256;   // (t, k1, k21)
-        for (int u = tid; u < items; u += kThreads) {
-            int t, k1, k21;
-            if (DIM == 1) { t = u >> 8; k21 = (u >> 4) & 15; k1 = u & 15; }
-            else { t = u & (kT - 1); k1 = (u >> 3) & 15; k21 = u >> 7; }
-            const float2* d = data + t * TS;
-            const float2 p = d[pidx(M * k1 + 2 * k21)], q = d[pidx(M * k1 + 2 * k21 + 1)];
-            float2 s0 = make_float2(__fadd_rn(p.x, q.x), __fadd_rn(p.y, q.y));
-            float2 s1 = make_float2(__fsub_rn(p.x, q.x), __fsub_rn(p.y, q.y));
-            if (scale_out) { s0 = scale2(s0, post); s1 = scale2(s1, post); }
-            const int e0 = k1 + 16 * k21, e1 = e0 + 256;
-            if (DIM == 1) {
-                out[(size_t)(t0 + t) * a.n1 + e0] = s0;
-                out[(size_t)(t0 + t) * a.n1 + e1] = s1;
+
+        float post = 1.0f;
+        if (a.epilogue == EPI_UNSCALE) post = exp2i(-kslice);
+        else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-kslice - a.lg_total);
+        const bool scale_out = a.epilogue != EPI_RAW;
+
+        // ---- round C1: vector (t, k1, j22), elements Y[M k1 + r j21 + j22] -
+        {
+            const int v = tid;
+            int t, rem;
+            if (DIM == 1) { t = v >> G::LGM; rem = v & (M - 1); }
+            else { t = v & (T - 1); rem = v >> G::LGT; }
+            const int k1 = r == 1 ? rem : rem >> 1;
+            const int j22 = r == 1 ? 0 : rem & 1;
+            float2 x[16], y[16];
+            if (DIM == 1 && r == 1) {
+                // own group of 16 consecutive elements, as 16-byte pairs
+                const float4* g = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, M * k1));
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    const float4 q = g[c];
+                    x[2 * c] = make_float2(q.x, q.y);
+                    x[2 * c + 1] = make_float2(q.z, q.w);
+                }
             } else {
-                out[(size_t)e0 * a.n1 + t0 + t] = s0;
-                out[(size_t)e1 * a.n1 + t0 + t] = s1;
+#pragma unroll
+                for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
             }
+            dft16_round<FMT>(x, y, mm, a.idesc, emax);
+            if (r == 1) {
+                // X[k1 + 16 k2]
+#pragma unroll
+                for (int k = 0; k < 16; k++) {
+                    const float2 val = scale_out ? scale2(y[k], post) : y[k];
+                    const int e = k1 + 16 * k;
+                    if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + e] = val;
+                    else out[(size_t)e * a.n1 + t0 + t] = val;
+                }
+            } else {
+                const float4* tw = reinterpret_cast<const float4*>(sTwC + j22 * kTwRow);
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    const float4 w = tw[k >> 1];
+                    d[slot<LOGN, DIM>(t, M * k1 + r * k + j22)] = cmul(make_float2(w.x, w.y), y[k]);
+                    d[slot<LOGN, DIM>(t, M * k1 + r * (k + 1) + j22)] = cmul(make_float2(w.z, w.w), y[k + 1]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+        }
+        // r = 1: the tile is done and its buffer free for the next prefetch;
+        // r = 2: C1's results are visible to C2.  A CTA whose wait timed out
+        // stops at the end of the tile.
+        if (r == 1) {
+            if (__syncthreads_or(!mm.ok)) break;
+            continue;
+        }
+        __syncthreads();
+
+        if (r == 2) {
+            // ---- C2: radix-2 over j22: X[k1 + 16 (k21 + 16 k22)] ----------
+#pragma unroll 2
+            for (int i = 0; i < 8; i++) {
+                const int u = tid + i * kThreads;       // (t, k1, k21), T x 16 x 16
+                int t, k1, k21;
+                if (DIM == 1) { k1 = u & 15; k21 = (u >> 4) & 15; t = u >> 8; }
+                else { t = u & 7; k21 = 8 * ((u >> 3) & 1) + (u >> 8); k1 = (u >> 4) & 15; }
+                const int e = M * k1 + 2 * k21;
+                float2 p, q;
+                if (DIM == 1) {
+                    const float4 pq = *reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, e));
+                    p = make_float2(pq.x, pq.y);
+                    q = make_float2(pq.z, pq.w);
+                } else {
+                    p = d[slot_col<LOGN>(t, e)];
+                    q = d[slot_col<LOGN>(t, e + 1)];
+                }
+                float2 s0 = make_float2(__fadd_rn(p.x, q.x), __fadd_rn(p.y, q.y));
+                float2 s1 = make_float2(__fsub_rn(p.x, q.x), __fsub_rn(p.y, q.y));
+                if (scale_out) { s0 = scale2(s0, post); s1 = scale2(s1, post); }
+                const int e0 = k1 + 16 * k21, e1 = e0 + 256;
+                if (DIM == 1) {
+                    out[(size_t)(t0 + t) * a.n1 + e0] = s0;
+                    out[(size_t)(t0 + t) * a.n1 + e1] = s1;
+                } else {
+                    out[(size_t)e0 * a.n1 + t0 + t] = s0;
+                    out[(size_t)e1 * a.n1 + t0 + t] = s1;
+                }
+            }
+            // the buffer is refilled by the next iteration's prefetch
+            if (__syncthreads_or(!mm.ok)) break;
         }
     }
+    cp_async_wait_all();
 
     // ---- teardown: an abandoned product is waited for once more, then the
     // tensor memory is returned
-    if (!ok) {
-        wait_phase(mb, phase ^ 1u);
+    if (!mm.ok) {
+        wait_phase(mm.mbar, mm.phase ^ 1u);
         if ((tid & 31) == 0) atomicExch(a.err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(mm.tbase), "r"(kTmemCols));
+}
+
+template <int FMT, int DIM, int LOGN>
+cudaError_t launch_one(const Args& a, cudaStream_t s) {
+    using G = Geo<LOGN>;
+    const size_t smem = kOffBuf + 2 * (size_t)G::BUF_SLOTS * sizeof(float2);
+    void (*k)(const Args) = tc16_pass_kernel<FMT, DIM, LOGN>;
+    // per kernel instance: shared-memory opt-in and resident CTAs per SM
+    static int resident = 0;
+    if (resident == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        // the occupancy query reports 1 CTA per SM for these kernels; the
+        // shared-memory and register budgets hold 2, as __launch_bounds__ asks
+        resident = (per_sm > 2 ? per_sm : 2) * sms;
+    }
+    const int other = DIM == 1 ? a.n0 : a.n1;
+    const int ntiles = a.batch * (other / G::T);
+    const int blocks = ntiles < resident ? ntiles : resident;
+    k<<<blocks, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int FMT>
-cudaError_t launch_fmt(const Args& a, int batch, cudaStream_t s) {
-    const int other = a.dim == 1 ? a.n0 : a.n1;
-    const int blocks = batch * (other / kT);
-    const size_t smem = 5120 + (size_t)kT * tstride(a.n) * sizeof(float2);
-    void (*k)(const Args);
-    if (a.n == 256) k = a.dim == 1 ? tc16_pass_kernel<FMT, 1, 8> : tc16_pass_kernel<FMT, 0, 8>;
-    else k = a.dim == 1 ? tc16_pass_kernel<FMT, 1, 9> : tc16_pass_kernel<FMT, 0, 9>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<blocks, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_fmt(const Args& a, cudaStream_t s) {
+    if (a.n == 256) return a.dim == 1 ? launch_one<FMT, 1, 8>(a, s) : launch_one<FMT, 0, 8>(a, s);
+    return a.dim == 1 ? launch_one<FMT, 1, 9>(a, s) : launch_one<FMT, 0, 9>(a, s);
 }
 
 }  // namespace tc16
 
 bool tc16_supported(int n, int other, int fmt) {
-    // n = 256 r (r = 1, 2), 8-bit element formats, whole CTAs of kT transforms
-    return (n == 256 || n == 512) && other >= tc16::kT && other % tc16::kT == 0 && (fmt == 0 || fmt == 1);
+    // n = 256 r (r = 1, 2), 8-bit element formats, whole tiles of 4096 / n transforms
+    if (n != 256 && n != 512) return false;
+    const int T = tc16::kTilePts / n;
+    return other >= T && other % T == 0 && (fmt == 0 || fmt == 1);
 }
 
 cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s) {
-    if (fmt == 0) return tc16::launch_fmt<0>(a, batch, s);
-    if (fmt == 1) return tc16::launch_fmt<1>(a, batch, s);
+    if (batch <= 0) return cudaSuccess;
+    Tc16Args b = a;
+    b.batch = batch;
+    if (fmt == 0) return tc16::launch_fmt<0>(b, s);
+    if (fmt == 1) return tc16::launch_fmt<1>(b, s);
     return cudaErrorNotSupported;
 }
 

@@ -73,3 +73,26 @@ def test_tc16_option_validation(cuda_device):
     p = mxfft.Plan(256, 256, "e4m3", 32, path="tc16")
     mxfft.mxfft_set_option(p.handle, mxfft.OPT_PATH, 0)
     p.close()
+
+
+@pytest.mark.parametrize("n0,n1,batch", [(256, 256, 40), (512, 512, 6), (512, 256, 11)])
+def test_tc16_many_tiles_per_cta(n0, n1, batch, cuda_device):
+    # more 4096-point tiles than resident CTAs: every CTA walks several tiles,
+    # an uneven number each, through both shared buffers
+    x = phantom.random_complex((batch, n0, n1), seed=77, scale=3.0)
+    got = run_tc16(x, "e4m3", "forward")
+    want = tc16_ref.mxfft2d(x, "e4m3", "forward")
+    assert nrmse(got, want.astype(np.complex128)) < 1e-4
+
+
+def test_tc16_in_place(cuda_device):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = phantom.mri_batch(512, 512, 3, 1, config_id=33, domain="image")
+    want = run_tc16(x, "e4m3", "roundtrip")
+    xt = torch.from_numpy(np.ascontiguousarray(x, np.complex64)).cuda()
+    with mxfft.Plan(512, 512, "e4m3", 32, path="tc16") as p:
+        p.roundtrip(xt, out=xt)
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(xt.cpu().numpy().view(np.uint32), want.view(np.uint32))

@@ -162,26 +162,32 @@ __device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams
 // call, lanes that hit the same bin are merged first (__match_any_sync), so a
 // bin shared by many lanes costs one shared atomic instead of one per lane.
 struct StatAcc {
-    uint32_t amax_bits = 0;
+    uint32_t amax_bits = 0;   // max |x| (mag_c3) over points outside the fast range
+    uint32_t smax_bits = 0;   // max re^2 + im^2 over points inside it
     uint32_t nnz = 0;
     uint32_t nonfinite = 0;
+    // Fast range: each component zero or of magnitude in [2^-62, 2^63).  There
+    // |x| = fl(sqrt(s)), s = fl(fl(re^2) + fl(im^2)), exactly as mag_c3
+    // computes it (see mag_c3_fast), and s is zero or normal.  The square root
+    // is correctly rounded, and for the largest float below 2^(2j), 2^(2j) (1 -
+    // 2^-24), it rounds to a value below 2^j; so fl(sqrt(s)) is in [2^j,
+    // 2^(j+1)) exactly when s is in [2^(2j), 2^(2j+2)).  Hence the bin
+    // floor(log2 |x|) is floor(floor(log2 s) / 2), and max |x| = fl(sqrt(max s))
+    // because the rounded square root is monotone: no square root per point.
     __device__ __forceinline__ void add(float re, float im, uint32_t* sh_hist) {
         const uint32_t br = __float_as_uint(re) & 0x7fffffffu;
         const uint32_t bi = __float_as_uint(im) & 0x7fffffffu;
         const uint32_t lo = (uint32_t)(127 - 62) << 23, hi = (uint32_t)(127 + 63) << 23;
         int bin = -1;
-        if ((br == 0 || (br >= lo && br < hi)) && (bi == 0 || (bi >= lo && bi < hi))) {
-            // |x| = sqrt(re^2 + im^2) exactly as mag_c3 computes it (see
-            // mag_c3_fast); the result is zero or normal, so its bin is its
-            // exponent field shifted by 149 - 127
-            const uint32_t mb = __float_as_uint(
-                __fsqrt_rn(__fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im))));
-            if (mb) {
-                amax_bits = max(amax_bits, mb);
+        // (b - 1 wraps zero to the top, so "b == 0 or b >= lo" is one compare)
+        if (min(br - 1u, bi - 1u) >= lo - 1u && max(br, bi) < hi) {
+            const uint32_t sb = __float_as_uint(__fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im)));
+            if (sb) {
+                smax_bits = max(smax_bits, sb);
                 nnz++;
-                bin = (int)(mb >> 23) + 22;
+                bin = (((int)(sb >> 23) - 127) >> 1) + 149;
             }
-        } else if (br >= 0x7f800000u || bi >= 0x7f800000u) {
+        } else if (max(br, bi) >= 0x7f800000u) {
             nonfinite = 1;
         } else {
             const uint32_t mb = __float_as_uint(mag_c3(re, im));
@@ -201,6 +207,10 @@ struct StatAcc {
             atomicAdd(&sh_hist[bin], 1u);
         }
     }
+    // bits of max |x| over everything added
+    __device__ __forceinline__ uint32_t amax() const {
+        return max(amax_bits, __float_as_uint(__fsqrt_rn(__uint_as_float(smax_bits))));
+    }
 };
 
 // CTA-wide flush of StatAcc into a slice's global statistics, then the last
@@ -214,6 +224,7 @@ __device__ __forceinline__ void stats_flush_and_select(StatAcc acc, uint32_t* sh
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     // warp reductions
+    acc.amax_bits = acc.amax();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc.amax_bits = max(acc.amax_bits, __shfl_xor_sync(0xffffffffu, acc.amax_bits, o));

@@ -193,6 +193,138 @@ int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int n
 int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, int format,
                                      float tau, float target, int32_t *k_out, void *stream);
 
+/* ======================================================================
+ * Ragged batch executor.  Not a construct of the paper: it runs many
+ * independent 2D transforms of the method (each exactly as mxfft_forward /
+ * mxfft_inverse / mxfft_roundtrip would on its own) in one set of launches:
+ * one statistics launch over every slice of every item (Alg. 1), one pass
+ * launch per (plan, direction) group and axis, the groups as parallel
+ * branches.  Results are bit-identical to the per-plan calls.
+ * ====================================================================== */
+typedef enum {
+    MXFFT_OP_FORWARD = 0,
+    MXFFT_OP_INVERSE = 1,
+    MXFFT_OP_ROUNDTRIP = 2
+} mxfft_op;
+
+/* One work item: `slices` independent [n0][n1] slices (slices x coils of an
+ * MRI volume) transformed with the plan (n0, n1, format, k) of the engine's
+ * tau and target.  in / out are device pointers, 16-byte aligned; in == out
+ * is allowed, other overlaps (also between items) are not. */
+typedef struct {
+    int n0, n1;
+    int format;
+    int k;
+    int op;          /* mxfft_op */
+    int slices;
+    const void *in;
+    void *out;
+} mxfft_item;
+
+typedef struct mxfft_engine_s *mxfft_engine_t;
+
+/* Engine flags. */
+#define MXFFT_ENGINE_GRAPHS 1  /* capture each batch signature into a CUDA graph, replay it */
+#define MXFFT_ENGINE_TC16 2    /* tensor-core radix-16 passes where a plan supports them */
+
+/*
+ * mxfft_engine_create -- executor bound to the current device, with its own
+ *   plan cache (plans and twiddle tables stay resident), fork streams, and
+ *   for MXFFT_ENGINE_GRAPHS a cache of instantiated graphs keyed by the batch
+ *   signature (the items' shapes, formats, ops and slice counts).  A graph
+ *   reads every buffer address from a table in device memory that is
+ *   refreshed before each replay, so one signature is captured once whatever
+ *   buffers later calls pass.
+ * mxfft_engine_run -- enqueue the items on the stream (asynchronous).
+ *   Errors: MXFFT_ERR_INVALID for a bad item (the checks of mxfft_plan and of
+ *   the data pointers), MXFFT_ERR_NOMEM, MXFFT_ERR_CUDA.  Before rewriting a
+ *   table that an earlier run may still be reading, the call waits for that
+ *   run.  Not safe for concurrent calls on one engine.
+ * mxfft_engine_get_status -- after the stream has been synchronised: flags
+ *   of the last run (bit 0 a non-finite input magnitude, bit 1 a bounded wait
+ *   timed out) and, if k_out is not NULL, 2 int32 per slice in item order
+ *   (prescale exponent of the transform; of the inverse for round trips, else
+ *   0), at most k_out_len values written.
+ */
+int mxfft_engine_create(float tau, float target, int flags, mxfft_engine_t *out);
+int mxfft_engine_run(mxfft_engine_t e, const mxfft_item *items, int n_items, void *stream);
+int mxfft_engine_get_status(mxfft_engine_t e, int *device_flags, int32_t *k_out, int k_out_len);
+int mxfft_engine_destroy(mxfft_engine_t e);
+
+/* ======================================================================
+ * Launch-geometry autotuner.  Measures the CTA shapes of the radix-2 pass
+ * kernel (transform groups per CTA) for a plan's passes at a given batch
+ * and keeps the fastest in a process-wide table that later launches of the
+ * same (length, other extent, axis, format, block size, batch class) use.
+ * Every shape computes the same bits.  The table can be saved to and loaded
+ * from a JSON file.
+ *
+ * mxfft_tune -- synchronous; allocates a scratch batch on the device,
+ *   times each candidate with CUDA events on the stream, frees the scratch.
+ *   n_measured (nullable) receives the number of candidates timed.
+ * mxfft_tune_save / mxfft_tune_load -- write / merge the table (JSON, UTF-8).
+ *   MXFFT_ERR_INVALID for an unreadable or malformed file.
+ * mxfft_tune_clear -- forget every entry.
+ * ====================================================================== */
+int mxfft_tune(mxfft_plan_t p, int batch, void *stream, int *n_measured);
+int mxfft_tune_save(const char *path);
+int mxfft_tune_load(const char *path);
+int mxfft_tune_clear(void);
+
+/* ======================================================================
+ * Request server with continuous batching.  Not a construct of the paper.
+ * Requests (host buffers) are queued; a worker thread admits them in arrival
+ * order into batches as execution slots (streams) and device memory free
+ * up, copies each batch in, runs it through an engine and copies it out,
+ * while earlier batches still run on other slots, so work of requests that
+ * arrive while others are on the GPU overlaps on the device.  Each result
+ * is bit-identical to the same request run alone.
+ * ====================================================================== */
+typedef struct {
+    int n0, n1, format, k, op, slices;   /* as in mxfft_item */
+    const void *host_in;                 /* [slices][n0][n1] complex64; pinned for overlap */
+    void *host_out;                      /* same size; written when the request completes */
+    uint64_t tag;                        /* returned in the completion */
+} mxfft_request;
+
+typedef struct {
+    uint64_t tag;
+    int status;                          /* mxfft_status of the request */
+    int device_flags;                    /* bit 0: a non-finite input magnitude */
+    double t_submit_us, t_admit_us, t_done_us;   /* server clock */
+} mxfft_completion;
+
+typedef struct {
+    int slots;                 /* batches in flight (streams), >= 1 */
+    int max_batch_slices;      /* slices per batch, >= 1 */
+    uint64_t mem_budget;       /* device bytes for request data; 0: 80% of free memory */
+    float tau, target;         /* of every plan */
+    int engine_flags;          /* MXFFT_ENGINE_* */
+} mxfft_server_config;
+
+typedef struct mxfft_server_s *mxfft_server_t;
+
+/*
+ * mxfft_server_create -- start the worker thread on the current device.
+ * mxfft_server_submit -- queue a request (copied; the host buffers must stay
+ *   valid until its completion is polled).  MXFFT_ERR_INVALID for a bad
+ *   request; a request larger than the whole memory budget completes with
+ *   MXFFT_ERR_NOMEM.
+ * mxfft_server_poll -- move up to max finished completions to out; *n_out
+ *   receives their number.
+ * mxfft_server_wait -- block until every submitted request has completed or
+ *   timeout_s has passed (MXFFT_ERR_TIMEOUT).
+ * mxfft_server_stats -- counters: batches launched, peak device bytes held by
+ *   admitted requests (never above the budget), the budget.
+ * mxfft_server_destroy -- finish outstanding work, stop the thread, free.
+ */
+int mxfft_server_create(const mxfft_server_config *cfg, mxfft_server_t *out);
+int mxfft_server_submit(mxfft_server_t s, const mxfft_request *r);
+int mxfft_server_poll(mxfft_server_t s, mxfft_completion *out, int max, int *n_out);
+int mxfft_server_wait(mxfft_server_t s, double timeout_s);
+int mxfft_server_stats(mxfft_server_t s, uint64_t *batches, uint64_t *peak_bytes, uint64_t *budget);
+int mxfft_server_destroy(mxfft_server_t s);
+
 /* mxfft_status_string -- static description of a status code. */
 const char *mxfft_status_string(int status);
 

@@ -1,0 +1,550 @@
+// Ragged batch executor: many independent 2D transforms of the method (Alg. 1
+// prescale, then the Alg. 2 radix-2 passes along rows and columns, Eq. (1)
+// round trips) enqueued as
+//   table upload -> statistics records cleared -> one statistics launch over
+//   every slice of every item -> per (plan, direction) group, as parallel
+//   branches: rows pass, columns pass -> [round trips: one statistics launch
+//   over the forward outputs -> per plan: inverse rows, inverse columns]
+// Every pass kernel reads its slices' buffers and statistics records from a
+// table in device memory (SliceRef), so a group is one launch whatever the
+// addresses, and a captured graph stays valid when a later call passes other
+// buffers: only the table content changes.  Per slice the arithmetic is that
+// of mxfft_forward / mxfft_inverse / mxfft_roundtrip, so results are
+// bit-identical to them.
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "mx_plan.h"
+
+using namespace mxfft;
+
+namespace {
+
+constexpr int kForkStreams = 8;
+constexpr size_t kMaxGraphs = 64;
+
+using PlanKey = std::tuple<int, int, int, int>;   // n0, n1, format, k
+
+struct PassLaunch {
+    mxfft_plan_s* p;
+    int dim, dir, prologue, epilogue;
+    int ref0, count;      // slice references [ref0, ref0 + count)
+    int branch;           // fork branch within its stage
+};
+
+// Host image of one run: the device tables and the launches that read them.
+struct Layout {
+    std::vector<SliceRef> refs;
+    std::vector<StatsRef> srefs;
+    std::vector<int2> ctas;
+    std::vector<PassLaunch> stage1, stage2;
+    int nbranch1 = 0, nbranch2 = 0;
+    int cta1 = 0, ncta1 = 0, cta2 = 0, ncta2 = 0;
+    int nslices = 0;
+    std::vector<char> rt;             // per slice: round trip
+    size_t off_srefs = 0, off_ctas = 0, bytes = 0;
+    std::string signature;
+};
+
+// Buffers of one run shape: pinned staging and device copy of the tables, the
+// statistics records (forward then inverse, nslices each), and the event of
+// the last run that used them.
+struct RunBuffers {
+    void* h_blob = nullptr;
+    void* d_blob = nullptr;
+    size_t cap = 0;
+    SliceStats* d_st = nullptr;
+    int st_cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;             // a run may still read h_blob
+    std::vector<char> last;           // table bytes of the last upload
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    RunBuffers buf;
+};
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+void free_buffers(RunBuffers& b) {
+    if (b.h_blob) cudaFreeHost(b.h_blob);
+    if (b.d_blob) cudaFree(b.d_blob);
+    if (b.d_st) cudaFree(b.d_st);
+    if (b.done) cudaEventDestroy(b.done);
+    b = RunBuffers();
+}
+
+// Capacity for a layout; waits for the buffers' last run before reallocating.
+int reserve(RunBuffers& b, const Layout& L) {
+    if (!b.done) {
+        int rc = cuda_status(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+        if (rc) return rc;
+    }
+    if (L.bytes <= b.cap && L.nslices <= b.st_cap) return MXFFT_OK;
+    if (b.pending) {
+        int rc = cuda_status(cudaEventSynchronize(b.done));
+        if (rc) return rc;
+        b.pending = false;
+    }
+    if (L.bytes > b.cap) {
+        if (b.h_blob) cudaFreeHost(b.h_blob);
+        if (b.d_blob) cudaFree(b.d_blob);
+        b.h_blob = b.d_blob = nullptr;
+        b.cap = 0;
+        size_t cap = 4096;
+        while (cap < L.bytes) cap *= 2;
+        int rc = cuda_status(cudaMallocHost(&b.h_blob, cap));
+        if (rc == MXFFT_OK) rc = cuda_status(cudaMalloc(&b.d_blob, cap));
+        if (rc) return rc;
+        b.cap = cap;
+        b.last.clear();
+    }
+    if (L.nslices > b.st_cap) {
+        if (b.d_st) cudaFree(b.d_st);
+        b.d_st = nullptr;
+        b.st_cap = 0;
+        int cap = 16;
+        while (cap < L.nslices) cap *= 2;
+        int rc = cuda_status(cudaMalloc(&b.d_st, 2 * (size_t)cap * sizeof(SliceStats)));
+        if (rc) return rc;
+        b.st_cap = cap;
+        b.last.clear();
+    }
+    return MXFFT_OK;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+bool item_ok(const mxfft_item& it) {
+    if (it.slices < 0 || it.op < 0 || it.op > 2) return false;
+    if (it.slices == 0) return true;
+    if (!it.in || !it.out || ((uintptr_t)it.in & 15u) || ((uintptr_t)it.out & 15u)) return false;
+    const size_t bytes = (size_t)it.slices * it.n0 * it.n1 * sizeof(float2);
+    const char* ci = (const char*)it.in;
+    const char* co = (const char*)it.out;
+    return ci == co || !(ci < co + bytes && co < ci + bytes);
+}
+
+}  // namespace
+
+struct mxfft_engine_s {
+    int device = -1;
+    float tau = 0.f, target = 0.f;
+    int flags = 0;
+    std::map<PlanKey, mxfft_plan_t> plans;
+    cudaStream_t capture = nullptr;             // stream the graphs are captured on
+    cudaStream_t fork[kForkStreams] = {};
+    std::vector<cudaEvent_t> evs;               // fork / join events
+    RunBuffers direct;
+    std::unordered_map<std::string, GraphEntry*> graphs;
+    // last run, for mxfft_engine_get_status
+    RunBuffers* last_buf = nullptr;
+    int last_slices = 0;
+    std::vector<char> last_rt;
+    std::vector<mxfft_plan_s*> last_plans;
+};
+
+namespace {
+
+int get_plan(mxfft_engine_s* e, const mxfft_item& it, mxfft_plan_s** out) {
+    const PlanKey key(it.n0, it.n1, it.format, it.k);
+    auto f = e->plans.find(key);
+    if (f != e->plans.end()) { *out = f->second; return MXFFT_OK; }
+    mxfft_plan_t p = nullptr;
+    int rc = mxfft_plan(it.n0, it.n1, it.format, it.k, e->tau, e->target, &p);
+    if (rc) return rc;
+    if (e->flags & MXFFT_ENGINE_TC16) {
+        // plans the tensor-core pass does not cover keep the radix-2 pass
+        rc = mxfft_set_option(p, MXFFT_OPT_PATH, 1.0);
+        if (rc != MXFFT_OK && rc != MXFFT_ERR_UNSUPPORTED) { mxfft_destroy(p); return rc; }
+    }
+    e->plans[key] = p;
+    *out = p;
+    return MXFFT_OK;
+}
+
+// Slices in item order get records st_f = d_st + g, st_i = d_st + cap + g.
+int build_layout(mxfft_engine_s* e, const mxfft_item* items, int n, Layout& L,
+                 std::vector<mxfft_plan_s*>& item_plan) {
+    item_plan.assign(n, nullptr);
+    std::string sig;
+    for (int i = 0; i < n; i++) {
+        if (items[i].slices == 0) continue;
+        int rc = get_plan(e, items[i], &item_plan[i]);
+        if (rc) return rc;
+        char b[96];
+        std::snprintf(b, sizeof b, "%d,%d,%d,%d,%d,%d;", items[i].n0, items[i].n1, items[i].format,
+                      items[i].k, items[i].op, items[i].slices);
+        sig += b;
+        L.nslices += items[i].slices;
+    }
+    L.signature = sig;
+    // table sizes: per slice two pass references (rows, columns) and a
+    // statistics reference with its CTAs; round trips add one reference for
+    // the inverse passes and a second statistics reference
+    size_t refs = 0, srefs = 0, ctas = 0;
+    for (int i = 0; i < n; i++) {
+        const size_t sl = (size_t)items[i].slices;
+        const size_t c = ((size_t)items[i].n0 * items[i].n1 + kStatsPtsPerCta - 1) / kStatsPtsPerCta;
+        const size_t rt = items[i].op == MXFFT_OP_ROUNDTRIP ? 1 : 0;
+        refs += sl * (2 + rt);
+        srefs += sl * (1 + rt);
+        ctas += sl * c * (1 + rt);
+    }
+    L.off_srefs = align16(refs * sizeof(SliceRef));
+    L.off_ctas = align16(L.off_srefs + srefs * sizeof(StatsRef));
+    L.bytes = align16(L.off_ctas + ctas * sizeof(int2));
+    return MXFFT_OK;
+}
+
+// Fill the tables for records at st_base (forward) and st_base + st_cap
+// (inverse statistics of round trips).
+void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*>& item_plan,
+                 SliceStats* st_base, int st_cap, Layout& L) {
+    L.refs.clear();
+    L.srefs.clear();
+    L.ctas.clear();
+    L.stage1.clear();
+    L.stage2.clear();
+    L.rt.assign(L.nslices, 0);
+    std::vector<int> first(n, 0);
+    for (int i = 0, g = 0; i < n; i++) { first[i] = g; g += items[i].slices; }
+    auto add_stats = [&](const float2* x, SliceStats* st, int npts, const KParams& kp) {
+        const int ctas = (npts + kStatsPtsPerCta - 1) / kStatsPtsPerCta;
+        const int idx = (int)L.srefs.size();
+        L.srefs.push_back(StatsRef{x, st, npts, (uint32_t)ctas, kp});
+        for (int c = 0; c < ctas; c++) L.ctas.push_back(make_int2(idx, c));
+    };
+    // statistics of every input
+    L.cta1 = 0;
+    for (int i = 0; i < n; i++) {
+        const mxfft_item& it = items[i];
+        const int np = it.n0 * it.n1;
+        for (int s = 0; s < it.slices; s++)
+            add_stats((const float2*)it.in + (size_t)s * np, st_base + first[i] + s, np,
+                      kparams(item_plan[i]));
+    }
+    L.ncta1 = (int)L.ctas.size();
+    // stage 1 groups: (plan, direction) in order of first appearance
+    std::vector<std::pair<mxfft_plan_s*, int>> groups;
+    for (int i = 0; i < n; i++) {
+        if (items[i].slices == 0) continue;
+        const std::pair<mxfft_plan_s*, int> key(item_plan[i], items[i].op == MXFFT_OP_INVERSE ? 1 : 0);
+        if (std::find(groups.begin(), groups.end(), key) == groups.end()) groups.push_back(key);
+    }
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+        mxfft_plan_s* p = groups[gi].first;
+        const int dir = groups[gi].second;
+        const int np = p->n0 * p->n1;
+        const int rows0 = (int)L.refs.size();
+        for (int i = 0; i < n; i++) {
+            if (item_plan[i] != p || (items[i].op == MXFFT_OP_INVERSE ? 1 : 0) != dir) continue;
+            for (int s = 0; s < items[i].slices; s++)
+                L.refs.push_back(SliceRef{(const float2*)items[i].in + (size_t)s * np,
+                                          (float2*)items[i].out + (size_t)s * np,
+                                          st_base + first[i] + s, nullptr});
+        }
+        const int count = (int)L.refs.size() - rows0;
+        const int cols0 = (int)L.refs.size();
+        for (int r = 0; r < count; r++) {
+            SliceRef c = L.refs[rows0 + r];
+            c.in = c.out;
+            L.refs.push_back(c);
+        }
+        L.stage1.push_back(PassLaunch{p, 1, dir, PRO_PRESCALE, EPI_RAW, rows0, count, (int)gi});
+        L.stage1.push_back(PassLaunch{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, (int)gi});
+    }
+    L.nbranch1 = (int)groups.size();
+    // round trips: statistics of the forward outputs, then the inverse passes
+    L.cta2 = (int)L.ctas.size();
+    std::vector<mxfft_plan_s*> rt_plans;
+    for (int i = 0; i < n; i++) {
+        if (items[i].op != MXFFT_OP_ROUNDTRIP || items[i].slices == 0) continue;
+        const int np = items[i].n0 * items[i].n1;
+        for (int s = 0; s < items[i].slices; s++) {
+            add_stats((const float2*)items[i].out + (size_t)s * np, st_base + st_cap + first[i] + s,
+                      np, kparams(item_plan[i]));
+            L.rt[first[i] + s] = 1;
+        }
+        if (std::find(rt_plans.begin(), rt_plans.end(), item_plan[i]) == rt_plans.end())
+            rt_plans.push_back(item_plan[i]);
+    }
+    L.ncta2 = (int)L.ctas.size() - L.cta2;
+    for (size_t gi = 0; gi < rt_plans.size(); gi++) {
+        mxfft_plan_s* p = rt_plans[gi];
+        const int np = p->n0 * p->n1;
+        const int r0 = (int)L.refs.size();
+        for (int i = 0; i < n; i++) {
+            if (item_plan[i] != p || items[i].op != MXFFT_OP_ROUNDTRIP) continue;
+            for (int s = 0; s < items[i].slices; s++) {
+                float2* y = (float2*)items[i].out + (size_t)s * np;
+                L.refs.push_back(SliceRef{y, y, st_base + st_cap + first[i] + s, nullptr});
+            }
+        }
+        const int count = (int)L.refs.size() - r0;
+        L.stage2.push_back(PassLaunch{p, 1, 1, PRO_PRESCALE, EPI_RAW, r0, count, (int)gi});
+        L.stage2.push_back(PassLaunch{p, 0, 1, PRO_NONE, EPI_RT_FINAL, r0, count, (int)gi});
+    }
+    L.nbranch2 = (int)rt_plans.size();
+    L.off_srefs = align16(L.refs.size() * sizeof(SliceRef));
+    L.off_ctas = align16(L.off_srefs + L.srefs.size() * sizeof(StatsRef));
+    L.bytes = align16(L.off_ctas + L.ctas.size() * sizeof(int2));
+}
+
+void pack(const Layout& L, char* dst) {
+    std::memset(dst, 0, L.bytes);
+    std::memcpy(dst, L.refs.data(), L.refs.size() * sizeof(SliceRef));
+    std::memcpy(dst + L.off_srefs, L.srefs.data(), L.srefs.size() * sizeof(StatsRef));
+    std::memcpy(dst + L.off_ctas, L.ctas.data(), L.ctas.size() * sizeof(int2));
+}
+
+cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, int nbranch,
+                      const SliceRef* d_refs, cudaStream_t s, size_t& ev) {
+    if (stage.empty()) return cudaSuccess;
+    const int nf = std::min(nbranch, kForkStreams);
+    cudaError_t err = cudaSuccess;
+    if (nf > 1) {
+        // fork: every branch stream waits for the work so far on s
+        err = cudaEventRecord(e->evs[ev], s);
+        for (int f = 0; f < nf && err == cudaSuccess; f++) err = cudaStreamWaitEvent(e->fork[f], e->evs[ev], 0);
+        ev++;
+    }
+    for (const PassLaunch& pl : stage) {
+        if (err != cudaSuccess) break;
+        PassArgs a = pass_args(pl.p, pl.dim, pl.dir, nullptr, nullptr);
+        a.ref = d_refs + pl.ref0;
+        a.prologue = pl.prologue;
+        a.epilogue = pl.epilogue;
+        err = timed_pass(pl.p, a, pl.count, nf > 1 ? e->fork[pl.branch % nf] : s);
+    }
+    if (nf > 1) {
+        // join
+        for (int f = 0; f < nf && err == cudaSuccess; f++) {
+            err = cudaEventRecord(e->evs[ev], e->fork[f]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e->evs[ev], 0);
+            ev++;
+        }
+    }
+    return err;
+}
+
+// Everything of one run after the tables are in the pinned staging buffer.
+cudaError_t enqueue(mxfft_engine_s* e, const Layout& L, RunBuffers& b, cudaStream_t s) {
+    char* d = (char*)b.d_blob;
+    const SliceRef* d_refs = (const SliceRef*)d;
+    const StatsRef* d_srefs = (const StatsRef*)(d + L.off_srefs);
+    const int2* d_ctas = (const int2*)(d + L.off_ctas);
+    size_t ev = 0;
+    cudaError_t err = cudaMemcpyAsync(b.d_blob, b.h_blob, L.bytes, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(b.d_st, 0, 2 * (size_t)b.st_cap * sizeof(SliceStats), s);
+    if (err == cudaSuccess) err = launch_stats_ref(d_srefs, d_ctas + L.cta1, L.ncta1, s);
+    if (err == cudaSuccess) err = run_stage(e, L.stage1, L.nbranch1, d_refs, s, ev);
+    if (err == cudaSuccess && L.ncta2 > 0) err = launch_stats_ref(d_srefs, d_ctas + L.cta2, L.ncta2, s);
+    if (err == cudaSuccess) err = run_stage(e, L.stage2, L.nbranch2, d_refs, s, ev);
+    return err;
+}
+
+// Make the staging buffer hold the layout's tables; returns whether they
+// changed.  Waits for the buffer's last run before rewriting it.
+int stage_tables(RunBuffers& b, const Layout& L, bool* changed) {
+    std::vector<char> img(L.bytes);
+    pack(L, img.data());
+    *changed = img != b.last;
+    if (!*changed) return MXFFT_OK;
+    if (b.pending) {
+        int rc = cuda_status(cudaEventSynchronize(b.done));
+        if (rc) return rc;
+        b.pending = false;
+    }
+    std::memcpy(b.h_blob, img.data(), L.bytes);
+    b.last.swap(img);
+    return MXFFT_OK;
+}
+
+void clear_graphs(mxfft_engine_s* e) {
+    for (auto& kv : e->graphs) {
+        if (kv.second->buf.pending) cudaEventSynchronize(kv.second->buf.done);
+        if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+        free_buffers(kv.second->buf);
+        delete kv.second;
+    }
+    e->graphs.clear();
+    e->last_buf = nullptr;
+}
+
+}  // namespace
+
+namespace mxfft {
+
+cudaError_t engine_flags_async(mxfft_engine_t e, uint32_t* h_flags, cudaStream_t s) {
+    if (!e || !h_flags) return cudaErrorInvalidValue;
+    if (!e->last_buf || e->last_slices == 0) return cudaSuccess;
+    const RunBuffers& b = *e->last_buf;
+    return cudaMemcpy2DAsync(h_flags, sizeof(uint32_t),
+                             (const char*)b.d_st + offsetof(SliceStats, nonfinite), sizeof(SliceStats),
+                             sizeof(uint32_t), (size_t)e->last_slices, cudaMemcpyDeviceToHost, s);
+}
+
+}  // namespace mxfft
+
+extern "C" {
+
+int mxfft_engine_create(float tau, float target, int flags, mxfft_engine_t* out) {
+    if (!out) return MXFFT_ERR_INVALID;
+    *out = nullptr;
+    if (!(tau > 0.0f && tau < 1.0f) || !(target > 0.0f) || (flags & ~3)) return MXFFT_ERR_INVALID;
+    // validate tau / target the way a plan does
+    mxfft_plan_t probe = nullptr;
+    int rc = mxfft_plan(2, 2, MXFFT_E4M3, 2, tau, target, &probe);
+    if (rc) return rc;
+    mxfft_destroy(probe);
+    mxfft_engine_s* e = new (std::nothrow) mxfft_engine_s;
+    if (!e) return MXFFT_ERR_NOMEM;
+    e->tau = tau;
+    e->target = target;
+    e->flags = flags;
+    rc = cuda_status(cudaGetDevice(&e->device));
+    if (rc == MXFFT_OK) rc = cuda_status(cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking));
+    for (int f = 0; f < kForkStreams && rc == MXFFT_OK; f++)
+        rc = cuda_status(cudaStreamCreateWithFlags(&e->fork[f], cudaStreamNonBlocking));
+    // 2 fork + 2 * kForkStreams join events per stage, two stages
+    e->evs.assign(2 * (1 + kForkStreams) + 2, nullptr);
+    for (size_t i = 0; i < e->evs.size() && rc == MXFFT_OK; i++)
+        rc = cuda_status(cudaEventCreateWithFlags(&e->evs[i], cudaEventDisableTiming));
+    if (rc) { mxfft_engine_destroy(e); return rc; }
+    *out = e;
+    return MXFFT_OK;
+}
+
+int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, void* stream) {
+    if (!e || n_items < 0 || (n_items > 0 && !items)) return MXFFT_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != e->device) return MXFFT_ERR_CUDA;
+    for (int i = 0; i < n_items; i++) {
+        if (!item_ok(items[i])) return MXFFT_ERR_INVALID;
+        if (items[i].slices == 0) continue;
+        // the plan constructor checks the shape, format, k
+        if (!pow2(items[i].n0) || !pow2(items[i].n1)) return MXFFT_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Layout L;
+    std::vector<mxfft_plan_s*> item_plan;
+    int rc = build_layout(e, items, n_items, L, item_plan);
+    if (rc) return rc;
+    if (L.nslices == 0) return MXFFT_OK;
+
+    RunBuffers* b = &e->direct;
+    GraphEntry* g = nullptr;
+    if (e->flags & MXFFT_ENGINE_GRAPHS) {
+        auto f = e->graphs.find(L.signature);
+        if (f != e->graphs.end()) {
+            g = f->second;
+        } else {
+            if (e->graphs.size() >= kMaxGraphs) clear_graphs(e);
+            g = new (std::nothrow) GraphEntry;
+            if (!g) return MXFFT_ERR_NOMEM;
+            e->graphs[L.signature] = g;
+        }
+        b = &g->buf;
+    }
+    // (a signature fixes the table sizes and slice count, so a graph's
+    // buffers are never reallocated under it)
+    rc = reserve(*b, L);
+    if (rc) return rc;
+    fill_layout(items, n_items, item_plan, b->d_st, b->st_cap, L);
+    bool changed = false;
+    rc = stage_tables(*b, L, &changed);
+    if (rc) return rc;
+
+    cudaError_t err = cudaSuccess;
+    if (g) {
+        if (!g->exec) {
+            // capture on the engine's own stream (the caller's may be the
+            // legacy stream, which cannot be captured)
+            cudaGraph_t graph = nullptr;
+            err = cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                cudaError_t e1 = enqueue(e, L, *b, e->capture);
+                cudaError_t e2 = cudaStreamEndCapture(e->capture, &graph);
+                err = e1 != cudaSuccess ? e1 : e2;
+            }
+            if (err == cudaSuccess) err = cudaGraphInstantiate(&g->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (err != cudaSuccess) {
+                g->exec = nullptr;
+                return cuda_status(err);
+            }
+        }
+        err = cudaGraphLaunch(g->exec, s);
+    } else {
+        err = enqueue(e, L, *b, s);
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(b->done, s);
+    if (err != cudaSuccess) return cuda_status(err);
+    b->pending = true;
+    e->last_buf = b;
+    e->last_slices = L.nslices;
+    e->last_rt = L.rt;
+    e->last_plans.clear();
+    for (auto* p : item_plan)
+        if (p && std::find(e->last_plans.begin(), e->last_plans.end(), p) == e->last_plans.end())
+            e->last_plans.push_back(p);
+    return MXFFT_OK;
+}
+
+int mxfft_engine_get_status(mxfft_engine_t e, int* device_flags, int32_t* k_out, int k_out_len) {
+    if (!e || !device_flags || (k_out && k_out_len < 0)) return MXFFT_ERR_INVALID;
+    *device_flags = 0;
+    if (!e->last_buf) return MXFFT_OK;
+    RunBuffers& b = *e->last_buf;
+    int rc = cuda_status(cudaEventSynchronize(b.done));
+    if (rc) return rc;
+    const int S = e->last_slices;
+    std::vector<SliceStats> st(2 * (size_t)b.st_cap);
+    rc = cuda_status(cudaMemcpy(st.data(), b.d_st, st.size() * sizeof(SliceStats), cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    int flags = 0;
+    for (int g = 0; g < S; g++)
+        if (st[g].nonfinite || (e->last_rt[g] && st[b.st_cap + g].nonfinite)) flags |= 1;
+    for (mxfft_plan_s* p : e->last_plans) {
+        if (!p->d_err) continue;
+        int err = 0;
+        rc = cuda_status(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (rc) return rc;
+        if (err) flags |= 2;
+    }
+    *device_flags = flags;
+    if (k_out)
+        for (int g = 0; g < S && 2 * g < k_out_len; g++) {
+            k_out[2 * g] = st[g].k;
+            if (2 * g + 1 < k_out_len) k_out[2 * g + 1] = e->last_rt[g] ? st[b.st_cap + g].k : 0;
+        }
+    return MXFFT_OK;
+}
+
+int mxfft_engine_destroy(mxfft_engine_t e) {
+    if (!e) return MXFFT_ERR_INVALID;
+    clear_graphs(e);
+    if (e->direct.pending) cudaEventSynchronize(e->direct.done);
+    free_buffers(e->direct);
+    for (auto& kv : e->plans) mxfft_destroy(kv.second);
+    for (cudaEvent_t ev : e->evs)
+        if (ev) cudaEventDestroy(ev);
+    for (int f = 0; f < kForkStreams; f++)
+        if (e->fork[f]) cudaStreamDestroy(e->fork[f]);
+    if (e->capture) cudaStreamDestroy(e->capture);
+    delete e;
+    return MXFFT_OK;
+}
+
+}  // extern "C"

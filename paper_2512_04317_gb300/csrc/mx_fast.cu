@@ -1,4 +1,6 @@
 // Dispatch of the register-resident MX pass by element format and block size.
+#include <algorithm>
+
 #include "mx_fast_kernel.cuh"
 
 namespace mxfft {
@@ -28,8 +30,21 @@ bool fast_pass_supported(const PassArgs& a) {
            fast::fast_geometry(a.n, other, &TG, &S, &NG, &threads);
 }
 
-cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
-                             cudaStream_t s) {
+int fast_ng_candidates(int n, int other, int* out, int max) {
+    int TG, S, NG, threads;
+    if (!fast::fast_geometry(n, other, &TG, &S, &NG, &threads)) return 0;
+    const int per_group = TG * (n / 32);
+    int c = 0;
+    for (int ng = 1; per_group * ng <= fast::kMaxThreads && c < max; ng <<= 1) {
+        const size_t smem = (size_t)ng * n * S * sizeof(float2);
+        if (per_group * ng < 32 || other % (TG * ng) != 0 || smem > 227 * 1024) continue;
+        out[c++] = ng;
+    }
+    return c;
+}
+
+cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
+                                int ng, cudaStream_t s) {
     if (!fast_pass_supported(a)) return cudaErrorNotSupported;
     fast::FastArgs fa;
     fa.a = a;
@@ -39,6 +54,13 @@ cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& 
     const int other = a.dim == 1 ? a.n0 : a.n1;
     fast::fast_geometry(a.n, other, &fa.TG, &fa.S, &fa.NG, &threads);
     fa.lgTG = fa.TG == 16 ? 4 : 3;
+    if (ng == 0) ng = fast_ng_tuned(a.n, other, a.dim, a.fmt, a.m, batch);
+    if (ng > 0) {
+        int cand[16];
+        const int nc = fast_ng_candidates(a.n, other, cand, 16);
+        if (std::find(cand, cand + nc, ng) == cand + nc) return cudaErrorInvalidValue;
+        fa.NG = ng;
+    }
     const int logm = log2_exact(a.m);
     switch (a.fmt) {
         case 0: return fast::launch_fast_fmt<0>(fa, logm, batch, s);
@@ -48,6 +70,11 @@ cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& 
         case 4: return fast::launch_fast_fmt<4>(fa, logm, batch, s);
         default: return cudaErrorNotSupported;
     }
+}
+
+cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
+                             cudaStream_t s) {
+    return launch_fast_pass_ng(a, twh, twa, batch, 0, s);
 }
 
 }  // namespace mxfft

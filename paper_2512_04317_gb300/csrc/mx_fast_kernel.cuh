@@ -38,11 +38,12 @@ fast_pass_kernel(const FastArgs fa) {
     const int tr = t0 + (grp << lgTG) + tau;     // row (dim 1) or column (dim 0)
     float2* __restrict__ Gs = sm + (size_t)grp * n * S;
     const size_t sbase = (size_t)slice * a.n0 * a.n1;
-    const float2* __restrict__ in = a.in + sbase;
-    float2* __restrict__ out = a.out + sbase;
+    const float2* __restrict__ in = a.ref ? a.ref[slice].in : a.in + sbase;
+    float2* __restrict__ out = a.ref ? a.ref[slice].out : a.out + sbase;
+    const SliceStats* stp = a.ref ? a.ref[slice].st : a.st + slice;
     const FmtParams fp = a.fp;
 
-    const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
+    const float pre = a.prologue == PRO_PRESCALE ? exp2i(stp->k) : 1.0f;
     const int s = n >> 5;                        // chunk stride of the bit-reversed gather
     const int rc = L > 5 ? (int)(__brev((unsigned)sigma) >> (37 - L)) : 0;
 
@@ -147,8 +148,8 @@ fast_pass_kernel(const FastArgs fa) {
 
     // ---- output in natural order ---------------------------------------------
     float post = 1.0f;
-    if (a.epilogue == EPI_UNSCALE) post = exp2i(-a.st[slice].k);
-    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
+    if (a.epilogue == EPI_UNSCALE) post = exp2i(-stp->k);
+    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-stp->k - a.lg_total);
     if (DIM == 0) {
 #pragma unroll
         for (int q = 0; q < 4; q++)

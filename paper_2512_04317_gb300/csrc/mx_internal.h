@@ -48,9 +48,20 @@ enum PassEpilogue {
     EPI_RT_FINAL = 3      // store 2^(-k - lg_total) * A (k of the inverse)
 };
 
+// Buffers of one slice when the slices of a launch are not one strided batch
+// (the ragged batch executor): the slice reads in, writes out and takes its
+// prescale exponent from *st.
+struct SliceRef {
+    const float2* in;
+    float2* out;
+    SliceStats* st;
+    const void* reserved;   // 32-byte entries
+};
+
 struct PassArgs {
     const float2* in;
     float2* out;
+    const SliceRef* ref;  // non-null: slice i uses ref[i] instead of in/out/st + i
     int n0, n1;           // slice shape
     int dim;              // 1: transform rows (length n1); 0: columns (length n0)
     int n, logn;          // transform length and log2
@@ -77,6 +88,7 @@ struct TwA {
 struct Tc16Args {
     const float2* in;
     float2* out;
+    const SliceRef* ref;              // as in PassArgs
     int n0, n1, dim, n, r;            // n = 256 r
     int batch;                        // slices (set by launch_tc16_pass)
     const uint8_t* bmat;              // B operand: 32 x 32 element codes, core-matrix layout (1 KB)
@@ -88,15 +100,39 @@ struct Tc16Args {
     int* err;                         // set when a bounded wait gives up
 };
 
+// One slice of a ragged statistics launch (slices of different sizes and
+// plans in one grid): its points, its record, its point count (even), the
+// number of CTAs that cover it and its plan's selection parameters.
+struct StatsRef {
+    const float2* x;
+    SliceStats* st;
+    int npts;
+    uint32_t ctas;
+    KParams kp;
+};
+constexpr int kStatsPtsPerCta = 4096;   // points per CTA of the statistics pass
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_stats(const float2* x, int batch, int n0, int n1, SliceStats* st,
                          KParams kp, cudaStream_t s);
+// Ragged statistics: CTA c covers chunk cta_tab[c].y (kStatsPtsPerCta points)
+// of slice refs[cta_tab[c].x]; the tables are device memory.
+cudaError_t launch_stats_ref(const StatsRef* refs, const int2* cta_tab, int nctas, cudaStream_t s);
 cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s);
 // Register-resident pass for n in [64, 2048] and m <= 16; returns
 // cudaErrorNotSupported (launching nothing) outside that range.
 bool fast_pass_supported(const PassArgs& a);
 cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                              cudaStream_t s);
+// Groups of TG transforms per CTA of the register-resident pass: valid values
+// for (n, other), the tuned value for a launch (0 if none), and the table the
+// autotuner fills (mx_tune.cu).
+int fast_ng_candidates(int n, int other, int* out, int max);
+int fast_ng_tuned(int n, int other, int dim, int fmt, int m, int batch);
+void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng, double us);
+// The register-resident pass with ng groups per CTA (ng = 0: tuned or default).
+cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
+                                int ng, cudaStream_t s);
 // Tensor-core radix-16 pass: n in {256, 512}, 8-bit formats, other a multiple
 // of 4096 / n.
 bool tc16_supported(int n, int other, int fmt);

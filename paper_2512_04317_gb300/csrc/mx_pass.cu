@@ -135,11 +135,12 @@ pass_kernel(PassArgs a) {
     const int slice = blockIdx.x / per_slice;
     const int t0 = (blockIdx.x - slice * per_slice) * tpc;
     const size_t sbase = (size_t)slice * a.n0 * a.n1;
-    const float2* __restrict__ in = a.in + sbase;
-    float2* __restrict__ out = a.out + sbase;
+    const float2* __restrict__ in = a.ref ? a.ref[slice].in : a.in + sbase;
+    float2* __restrict__ out = a.ref ? a.ref[slice].out : a.out + sbase;
+    const SliceStats* stp = a.ref ? a.ref[slice].st : a.st + slice;
 
     // load (with the Alg. 1 prescale on the first pass) in bit-reversed order
-    const float pre = a.prologue == PRO_PRESCALE ? exp2i(a.st[slice].k) : 1.0f;
+    const float pre = a.prologue == PRO_PRESCALE ? exp2i(stp->k) : 1.0f;
     const int total = tpc * n;
     for (int idx = tid; idx < total; idx += nthr) {
         int t, i;
@@ -177,8 +178,8 @@ pass_kernel(PassArgs a) {
 
     // epilogue: natural order out
     float post = 1.0f;
-    if (a.epilogue == EPI_UNSCALE) post = exp2i(-a.st[slice].k);
-    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-a.st[slice].k - a.lg_total);
+    if (a.epilogue == EPI_UNSCALE) post = exp2i(-stp->k);
+    else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-stp->k - a.lg_total);
     for (int idx = tid; idx < total; idx += nthr) {
         int t, i;
         size_t g;

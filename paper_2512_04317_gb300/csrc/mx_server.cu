@@ -1,0 +1,325 @@
+// Request server with continuous batching over the ragged batch executor.
+//
+// Requests (host buffers) enter a FIFO queue.  A worker thread admits them in
+// arrival order whenever an execution slot (a stream with its own engine) is
+// free and the device memory budget allows: all queued requests that fit form
+// one batch, which is copied in, transformed in place by one engine run and
+// copied out on that slot while batches admitted earlier still run on other
+// slots.  A host callback at the end of each slot's stream returns the slot
+// and the batch's memory.  No kernel waits on the host: the device-side part
+// of a request is the engine's launches, the host side only enqueues.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstddef>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "mx_plan.h"
+
+using namespace mxfft;
+
+namespace {
+
+double now_us() {
+    using namespace std::chrono;
+    return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct SReq {
+    mxfft_request r;
+    size_t bytes;
+    double t_submit, t_admit;
+};
+
+struct DoneCtx {
+    struct ::mxfft_server_s* srv;
+    int slot;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    mxfft_engine_t eng = nullptr;
+    bool busy = false;
+    std::vector<SReq> reqs;
+    size_t bytes = 0;
+    uint32_t* h_flags = nullptr;      // pinned: per slice, non-finite input magnitude
+    int flags_cap = 0;
+    int status = MXFFT_OK;
+    DoneCtx ctx;
+};
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct mxfft_server_s {
+    mxfft_server_config cfg;
+    int device = -1;
+    std::mutex mu;
+    std::condition_variable cv;        // worker: submissions, finished slots, stop
+    std::condition_variable cv_done;   // waiters: completions
+    std::deque<SReq> pending;
+    std::deque<mxfft_completion> done;
+    std::vector<Slot> slots;
+    std::vector<int> finished;
+    size_t budget = 0, inflight = 0, peak = 0;
+    uint64_t submitted = 0, completed = 0, batches = 0;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+void CUDART_CB slot_done(void* arg) {
+    DoneCtx* c = static_cast<DoneCtx*>(arg);
+    std::lock_guard<std::mutex> lk(c->srv->mu);
+    c->srv->finished.push_back(c->slot);
+    c->srv->cv.notify_all();
+}
+
+// Enqueue a batch on its slot; returns false if nothing was enqueued that will
+// call slot_done (the caller then retires the slot itself).
+bool launch_batch(mxfft_server_s* S, int i) {
+    Slot& sl = S->slots[i];
+    cudaStream_t s = sl.stream;
+    int slices = 0;
+    for (const SReq& q : sl.reqs) slices += q.r.slices;
+    sl.status = MXFFT_OK;
+    if (slices > sl.flags_cap) {
+        if (sl.h_flags) cudaFreeHost(sl.h_flags);
+        sl.h_flags = nullptr;
+        sl.flags_cap = 0;
+        int cap = 64;
+        while (cap < slices) cap *= 2;
+        if (cudaMallocHost(&sl.h_flags, cap * sizeof(uint32_t)) != cudaSuccess) {
+            sl.status = MXFFT_ERR_NOMEM;
+            return false;
+        }
+        sl.flags_cap = cap;
+    }
+    char* d = nullptr;
+    cudaError_t err = cudaMallocAsync((void**)&d, sl.bytes, s);
+    if (err != cudaSuccess) {
+        sl.status = cuda_status(err);
+        return false;
+    }
+    std::vector<mxfft_item> items;
+    size_t off = 0;
+    for (const SReq& q : sl.reqs) {
+        if (err == cudaSuccess) err = cudaMemcpyAsync(d + off, q.r.host_in, q.bytes, cudaMemcpyHostToDevice, s);
+        items.push_back(mxfft_item{q.r.n0, q.r.n1, q.r.format, q.r.k, q.r.op, q.r.slices, d + off, d + off});
+        off += q.bytes;
+    }
+    int rc = err == cudaSuccess ? MXFFT_OK : cuda_status(err);
+    if (rc == MXFFT_OK) rc = mxfft_engine_run(sl.eng, items.data(), (int)items.size(), s);
+    if (rc == MXFFT_OK) rc = cuda_status(engine_flags_async(sl.eng, sl.h_flags, s));
+    off = 0;
+    for (const SReq& q : sl.reqs) {
+        if (rc == MXFFT_OK) rc = cuda_status(cudaMemcpyAsync(q.r.host_out, d + off, q.bytes, cudaMemcpyDeviceToHost, s));
+        off += q.bytes;
+    }
+    cudaFreeAsync(d, s);
+    sl.status = rc;
+    if (rc != MXFFT_OK) std::fill(sl.h_flags, sl.h_flags + slices, 0u);
+    return cudaLaunchHostFunc(s, slot_done, &sl.ctx) == cudaSuccess;
+}
+
+void retire(mxfft_server_s* S, std::unique_lock<std::mutex>& lk, int i) {
+    Slot& sl = S->slots[i];
+    std::vector<SReq> reqs;
+    reqs.swap(sl.reqs);
+    const int status = sl.status;
+    const size_t bytes = sl.bytes;
+    const double t = now_us();
+    std::vector<mxfft_completion> cs;
+    int g = 0;
+    for (const SReq& q : reqs) {
+        int fl = 0;
+        for (int k = 0; k < q.r.slices; k++, g++)
+            if (status == MXFFT_OK && sl.h_flags && sl.h_flags[g]) fl = 1;
+        cs.push_back(mxfft_completion{q.r.tag, status, fl, q.t_submit, q.t_admit, t});
+    }
+    (void)lk;
+    S->inflight -= bytes;
+    sl.bytes = 0;
+    sl.busy = false;
+    for (const auto& c : cs) S->done.push_back(c);
+    S->completed += cs.size();
+    S->cv_done.notify_all();
+}
+
+void worker_main(mxfft_server_s* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        while (!S->finished.empty()) {
+            const int i = S->finished.back();
+            S->finished.pop_back();
+            retire(S, lk, i);
+        }
+        bool busy = false;
+        int free_slot = -1;
+        for (size_t i = 0; i < S->slots.size(); i++) {
+            busy = busy || S->slots[i].busy;
+            if (!S->slots[i].busy && free_slot < 0) free_slot = (int)i;
+        }
+        if (S->stop && S->pending.empty() && !busy) break;
+        if (free_slot >= 0 && !S->pending.empty()) {
+            std::vector<SReq> batch;
+            size_t bytes = 0;
+            int slices = 0;
+            const double ta = now_us();
+            while (!S->pending.empty()) {
+                SReq q = S->pending.front();
+                if (q.bytes > S->budget) {
+                    // can never be admitted
+                    S->pending.pop_front();
+                    S->done.push_back(mxfft_completion{q.r.tag, MXFFT_ERR_NOMEM, 0, q.t_submit, ta, ta});
+                    S->completed++;
+                    S->cv_done.notify_all();
+                    continue;
+                }
+                if (S->inflight + bytes + q.bytes > S->budget) break;
+                if (!batch.empty() && slices + q.r.slices > S->cfg.max_batch_slices) break;
+                q.t_admit = ta;
+                batch.push_back(q);
+                bytes += q.bytes;
+                slices += q.r.slices;
+                S->pending.pop_front();
+            }
+            if (!batch.empty()) {
+                Slot& sl = S->slots[free_slot];
+                sl.busy = true;
+                sl.bytes = bytes;
+                sl.reqs.swap(batch);
+                S->inflight += bytes;
+                S->peak = std::max(S->peak, S->inflight);
+                S->batches++;
+                lk.unlock();
+                const bool queued = launch_batch(S, free_slot);
+                lk.lock();
+                if (!queued) S->finished.push_back(free_slot);
+                continue;
+            }
+        }
+        S->cv.wait_for(lk, std::chrono::milliseconds(5));
+    }
+}
+
+void destroy_slots(mxfft_server_s* S) {
+    for (Slot& sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.eng) mxfft_engine_destroy(sl.eng);
+        if (sl.h_flags) cudaFreeHost(sl.h_flags);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    S->slots.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int mxfft_server_create(const mxfft_server_config* cfg, mxfft_server_t* out) {
+    if (!out || !cfg) return MXFFT_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->slots < 1 || cfg->slots > 64 || cfg->max_batch_slices < 1) return MXFFT_ERR_INVALID;
+    mxfft_server_s* S = new (std::nothrow) mxfft_server_s;
+    if (!S) return MXFFT_ERR_NOMEM;
+    S->cfg = *cfg;
+    int rc = cuda_status(cudaGetDevice(&S->device));
+    if (rc == MXFFT_OK) {
+        size_t fr = 0, tot = 0;
+        rc = cuda_status(cudaMemGetInfo(&fr, &tot));
+        S->budget = cfg->mem_budget ? (size_t)cfg->mem_budget : (size_t)(0.8 * (double)fr);
+    }
+    S->slots.resize(cfg->slots);
+    for (int i = 0; i < cfg->slots && rc == MXFFT_OK; i++) {
+        Slot& sl = S->slots[i];
+        sl.ctx = DoneCtx{S, i};
+        rc = cuda_status(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+        if (rc == MXFFT_OK) rc = mxfft_engine_create(cfg->tau, cfg->target, cfg->engine_flags, &sl.eng);
+    }
+    if (rc != MXFFT_OK) {
+        destroy_slots(S);
+        delete S;
+        return rc;
+    }
+    try {
+        S->worker = std::thread(worker_main, S);
+    } catch (...) {
+        destroy_slots(S);
+        delete S;
+        return MXFFT_ERR_NOMEM;
+    }
+    *out = S;
+    return MXFFT_OK;
+}
+
+int mxfft_server_submit(mxfft_server_t S, const mxfft_request* r) {
+    if (!S || !r) return MXFFT_ERR_INVALID;
+    if (!pow2_in(r->n0, 2, 2048) || !pow2_in(r->n1, 2, 2048) || r->format < 0 || r->format > 4 ||
+        !pow2_in(r->k, 2, 128) || r->op < 0 || r->op > 2 || r->slices < 1 || !r->host_in || !r->host_out)
+        return MXFFT_ERR_INVALID;
+    SReq q;
+    q.r = *r;
+    q.bytes = (size_t)r->slices * r->n0 * r->n1 * sizeof(float2);
+    q.t_submit = now_us();
+    q.t_admit = 0.0;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return MXFFT_ERR_INVALID;
+    S->pending.push_back(q);
+    S->submitted++;
+    S->cv.notify_all();
+    return MXFFT_OK;
+}
+
+int mxfft_server_poll(mxfft_server_t S, mxfft_completion* out, int max, int* n_out) {
+    if (!S || !n_out || max < 0 || (max > 0 && !out)) return MXFFT_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    int n = 0;
+    while (n < max && !S->done.empty()) {
+        out[n++] = S->done.front();
+        S->done.pop_front();
+    }
+    *n_out = n;
+    return MXFFT_OK;
+}
+
+int mxfft_server_wait(mxfft_server_t S, double timeout_s) {
+    if (!S || !(timeout_s >= 0.0)) return MXFFT_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto until = std::chrono::steady_clock::now() +
+                       std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                           std::chrono::duration<double>(timeout_s));
+    const bool ok = S->cv_done.wait_until(lk, until, [S] { return S->completed == S->submitted; });
+    return ok ? MXFFT_OK : MXFFT_ERR_TIMEOUT;
+}
+
+int mxfft_server_stats(mxfft_server_t S, uint64_t* batches, uint64_t* peak_bytes, uint64_t* budget) {
+    if (!S) return MXFFT_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (batches) *batches = S->batches;
+    if (peak_bytes) *peak_bytes = S->peak;
+    if (budget) *budget = S->budget;
+    return MXFFT_OK;
+}
+
+int mxfft_server_destroy(mxfft_server_t S) {
+    if (!S) return MXFFT_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    destroy_slots(S);
+    delete S;
+    return MXFFT_OK;
+}
+
+}  // extern "C"

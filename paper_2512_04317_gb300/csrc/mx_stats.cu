@@ -8,19 +8,18 @@ namespace mxfft {
 namespace {
 
 constexpr int kStatsThreads = 256;
-constexpr int kStatsPtsPerCta = 4096;
 
-__global__ void __launch_bounds__(kStatsThreads)
-stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st,
-             KParams kp, uint32_t ctas_per_slice) {
+// One CTA's share: points [chunk * kStatsPtsPerCta, +kStatsPtsPerCta) of a
+// slice of npts points, then the flush into the slice's record.
+__device__ __forceinline__ void stats_cta(const float2* __restrict__ x, int npts, int chunk,
+                                          SliceStats* st, const KParams& kp, uint32_t ctas) {
     __shared__ uint32_t sh_hist[kHistBins];
     __shared__ uint32_t sh_misc[4];
     const int tid = threadIdx.x;
-    const int slice = blockIdx.y;
     for (int b = tid; b < kHistBins; b += blockDim.x) sh_hist[b] = 0;
     __syncthreads();
-    const float4* xs = reinterpret_cast<const float4*>(x + (size_t)slice * npts);
-    const int begin = blockIdx.x * kStatsPtsPerCta;
+    const float4* xs = reinterpret_cast<const float4*>(x);
+    const int begin = chunk * kStatsPtsPerCta;
     const int end = min(begin + kStatsPtsPerCta, npts);
     StatAcc acc;
     // two 16-byte loads in flight per thread before their arithmetic
@@ -35,7 +34,21 @@ stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st
         acc.add(v1.z, v1.w, sh_hist);
     }
     __syncthreads();
-    stats_flush_and_select(acc, sh_hist, sh_misc, st + slice, ctas_per_slice, kp);
+    stats_flush_and_select(acc, sh_hist, sh_misc, st, ctas, kp);
+}
+
+__global__ void __launch_bounds__(kStatsThreads)
+stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st,
+             KParams kp, uint32_t ctas_per_slice) {
+    const int slice = blockIdx.y;
+    stats_cta(x + (size_t)slice * npts, npts, blockIdx.x, st + slice, kp, ctas_per_slice);
+}
+
+__global__ void __launch_bounds__(kStatsThreads)
+stats_ref_kernel(const StatsRef* __restrict__ refs, const int2* __restrict__ cta_tab) {
+    const int2 w = cta_tab[blockIdx.x];
+    const StatsRef r = refs[w.x];
+    stats_cta(r.x, r.npts, w.y, r.st, r.kp, r.ctas);
 }
 
 }  // namespace
@@ -46,6 +59,12 @@ cudaError_t launch_stats(const float2* x, int batch, int n0, int n1, SliceStats*
     const uint32_t per = (uint32_t)((npts + kStatsPtsPerCta - 1) / kStatsPtsPerCta);
     dim3 grid(per, batch);
     stats_kernel<<<grid, kStatsThreads, 0, s>>>(x, npts, st, kp, per);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_ref(const StatsRef* refs, const int2* cta_tab, int nctas, cudaStream_t s) {
+    if (nctas <= 0) return cudaSuccess;
+    stats_ref_kernel<<<nctas, kStatsThreads, 0, s>>>(refs, cta_tab);
     return cudaGetLastError();
 }
 

@@ -263,7 +263,7 @@ __device__ __forceinline__ void load_tile(const Args& a, int tile, uint32_t buf)
     const int per_slice = other / G::T;
     const int slice = tile / per_slice;
     const int t0 = (tile - slice * per_slice) * G::T;
-    const float2* in = a.in + (size_t)slice * a.n0 * a.n1;
+    const float2* in = a.ref ? a.ref[slice].in : a.in + (size_t)slice * a.n0 * a.n1;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const int q = threadIdx.x + i * kThreads;      // 16-byte chunk of the tile
@@ -339,13 +339,13 @@ tc16_pass_kernel(const Args a) {
         const int slice = tile / per_slice;
         const int t0 = (tile - slice * per_slice) * T;
         // the slice's exponent is fetched while the tile's copies land
-        const int kslice = (a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW) ? a.st[slice].k : 0;
+        const SliceStats* stp = a.ref ? a.ref[slice].st : a.st + slice;
+        const int kslice = (a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW) ? stp->k : 0;
         cp_async_wait_prev();
         __syncthreads();
 
         float2* d = bufs + cur * G::BUF_SLOTS;
-        const size_t sbase = (size_t)slice * a.n0 * a.n1;
-        float2* __restrict__ out = a.out + sbase;
+        float2* __restrict__ out = a.ref ? a.ref[slice].out : a.out + (size_t)slice * a.n0 * a.n1;
 
         // ---- round A: vector (t, j2), elements x[M j1 + j2] ----------------
         {

@@ -10,44 +10,9 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
-#include "mx_internal.h"
-#include "mxfft.h"
+#include "mx_plan.h"
 
 using namespace mxfft;
-
-namespace {
-struct ProfRec {
-    int kind;                  // 0 stats, 1 pass
-    cudaEvent_t a, b;
-};
-}  // namespace
-
-struct mxfft_plan_s {
-    int n0, n1, fmt, kblk;
-    float tau;
-    int t_exp;                 // target = 2^t_exp
-    int taumin_exp;            // tau_min = 2^taumin_exp
-    int kmin, kmax;
-    FmtParams fp;
-    int m[2];                  // MX block size in butterflies per axis (0: n0, 1: n1)
-    float2* d_tw[2][2];        // [axis][0 forward, 1 inverse]
-    int8_t* d_tws[2];          // [axis] twiddle block exponents
-    uint32_t* d_twh[2][2];     // [axis][dir] f16x2 twiddle element values
-    TwA twa[2][2];             // [axis][dir] stages h <= 16 for the register pass
-    int force_generic;         // 1: always use the generic pass kernel
-    int path;                  // 0 radix-2 MX, 1 tensor-core radix-16
-    uint8_t* d_bmat[2];        // [dir] tensor-core DFT matrix codes (core-matrix layout)
-    float2* d_twA[2][2];       // [axis][dir] radix-16 stage twiddles
-    float2* d_twC[2][2];       // [axis][dir] twiddles before the radix-2 stage (n = 512)
-    int* d_err;                // device flag: a bounded wait gave up
-    SliceStats* d_st;          // 2 * st_cap records: forward, inverse
-    int st_cap;
-    int last_batch, last_op;   // of the last transform
-    cudaStream_t last_stream;
-    int device;
-    bool prof;                 // record per-kernel event pairs
-    std::vector<ProfRec>* recs;
-};
 
 namespace {
 
@@ -185,12 +150,6 @@ void twiddle_block16(long m, long N, int sgn, const FmtHost& f, float2* out) {
                              (float)std::ldexp(q_host(std::ldexp(sn[i], -sc), f), sc));
 }
 
-int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return MXFFT_OK;
-    if (e == cudaErrorMemoryAllocation) return MXFFT_ERR_NOMEM;
-    return MXFFT_ERR_CUDA;
-}
-
 void free_plan_device(mxfft_plan_s* p) {
     for (int d = 0; d < 2; d++) {
         if (p->d_bmat[d]) cudaFree(p->d_bmat[d]);
@@ -303,41 +262,6 @@ int build_tc16_tables(mxfft_plan_s* p) {
     return rc;
 }
 
-KParams kparams(const mxfft_plan_s* p) {
-    KParams kp;
-    kp.tau = p->tau;
-    kp.t_exp = p->t_exp;
-    kp.taumin_exp = p->taumin_exp;
-    kp.kmin = p->kmin;
-    kp.kmax = p->kmax;
-    return kp;
-}
-
-PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out) {
-    PassArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.in = in;
-    a.out = out;
-    a.n0 = p->n0;
-    a.n1 = p->n1;
-    a.dim = dim;
-    a.n = dim == 1 ? p->n1 : p->n0;
-    a.logn = ilog2(a.n);
-    const int other = dim == 1 ? p->n0 : p->n1;
-    int tpc = 8192 / a.n;
-    if (tpc < 1) tpc = 1;
-    if (tpc > other) tpc = other;
-    a.tpc = tpc;
-    a.m = p->m[dim];
-    a.tw = p->d_tw[dim][dir];
-    a.tws = p->d_tws[dim];
-    a.fmt = p->fmt;
-    a.fp = p->fp;
-    a.kp = kparams(p);
-    a.lg_total = ilog2(p->n0) + ilog2(p->n1);
-    return a;
-}
-
 bool aligned16(const void* q) { return ((uintptr_t)q & 15u) == 0; }
 
 // Event pair around one launch when profiling is on (nullptr otherwise).
@@ -353,43 +277,6 @@ ProfRec* prof_begin(mxfft_plan_s* p, int kind, cudaStream_t s) {
 
 void prof_end(ProfRec* r, cudaStream_t s) {
     if (r) cudaEventRecord(r->b, s);
-}
-
-// The tensor-core pass when that path is selected, else the register-resident
-// kernel where it applies (n in [64, 2048], m <= 16), else the generic
-// shared-memory kernel.
-cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
-    const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
-    if (p->path == 1) {
-        Tc16Args t;
-        t.in = a.in;
-        t.out = a.out;
-        t.n0 = a.n0;
-        t.n1 = a.n1;
-        t.dim = a.dim;
-        t.n = a.n;
-        t.r = a.n / 256;
-        t.bmat = p->d_bmat[dir];
-        t.twA = p->d_twA[a.dim][dir];
-        t.twC = p->d_twC[a.dim][dir];
-        t.st = a.st;
-        t.prologue = a.prologue;
-        t.epilogue = a.epilogue;
-        t.lg_total = a.lg_total;
-        const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
-        t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-        t.err = p->d_err;
-        ProfRec* r = prof_begin(p, 3, s);
-        cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
-        prof_end(r, s);
-        return e;
-    }
-    const bool fast = !p->force_generic && fast_pass_supported(a);
-    ProfRec* r = prof_begin(p, fast ? 2 : 1, s);
-    cudaError_t e = fast ? launch_fast_pass(a, p->d_twh[a.dim][dir], p->twa[a.dim][dir], batch, s)
-                         : launch_pass(a, batch, s);
-    prof_end(r, s);
-    return e;
 }
 
 void prof_clear(mxfft_plan_s* p) {
@@ -461,6 +348,89 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
 }
 
 }  // namespace
+
+namespace mxfft {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MXFFT_OK;
+    if (e == cudaErrorMemoryAllocation) return MXFFT_ERR_NOMEM;
+    return MXFFT_ERR_CUDA;
+}
+
+KParams kparams(const mxfft_plan_s* p) {
+    KParams kp;
+    kp.tau = p->tau;
+    kp.t_exp = p->t_exp;
+    kp.taumin_exp = p->taumin_exp;
+    kp.kmin = p->kmin;
+    kp.kmax = p->kmax;
+    return kp;
+}
+
+PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.n0 = p->n0;
+    a.n1 = p->n1;
+    a.dim = dim;
+    a.n = dim == 1 ? p->n1 : p->n0;
+    a.logn = ilog2(a.n);
+    const int other = dim == 1 ? p->n0 : p->n1;
+    int tpc = 8192 / a.n;
+    if (tpc < 1) tpc = 1;
+    if (tpc > other) tpc = other;
+    a.tpc = tpc;
+    a.m = p->m[dim];
+    a.tw = p->d_tw[dim][dir];
+    a.tws = p->d_tws[dim];
+    a.fmt = p->fmt;
+    a.fp = p->fp;
+    a.kp = kparams(p);
+    a.lg_total = ilog2(p->n0) + ilog2(p->n1);
+    return a;
+}
+
+// The tensor-core pass when that path is selected, else the register-resident
+// kernel where it applies (n in [64, 2048], m <= 16), else the generic
+// shared-memory kernel.
+cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
+    const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
+    if (p->path == 1) {
+        Tc16Args t;
+        t.in = a.in;
+        t.out = a.out;
+        t.ref = a.ref;
+        t.n0 = a.n0;
+        t.n1 = a.n1;
+        t.dim = a.dim;
+        t.n = a.n;
+        t.r = a.n / 256;
+        t.bmat = p->d_bmat[dir];
+        t.twA = p->d_twA[a.dim][dir];
+        t.twC = p->d_twC[a.dim][dir];
+        t.st = a.st;
+        t.prologue = a.prologue;
+        t.epilogue = a.epilogue;
+        t.lg_total = a.lg_total;
+        const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
+        t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+        t.err = p->d_err;
+        ProfRec* r = prof_begin(p, 3, s);
+        cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
+        prof_end(r, s);
+        return e;
+    }
+    const bool fast = !p->force_generic && fast_pass_supported(a);
+    ProfRec* r = prof_begin(p, fast ? 2 : 1, s);
+    cudaError_t e = fast ? launch_fast_pass(a, p->d_twh[a.dim][dir], p->twa[a.dim][dir], batch, s)
+                         : launch_pass(a, batch, s);
+    prof_end(r, s);
+    return e;
+}
+
+}  // namespace mxfft
 
 extern "C" {
 

@@ -24,10 +24,47 @@ MXFFT_ERR_TIMEOUT = 6
 FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4}
 OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH = 0, 1, 2, 3, 4
 
+OPS = {"forward": 0, "inverse": 1, "roundtrip": 2}
+ENGINE_GRAPHS, ENGINE_TC16 = 1, 2
+
 # every symbol include/mxfft.h declares
 EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
            "mxfft_roundtrip", "mxfft_get_status", "mxfft_destroy", "mxfft_profile",
-           "mxfft_profile_read", "mxfft_prescale_exponents_noalloc", "mxfft_status_string")
+           "mxfft_profile_read", "mxfft_prescale_exponents_noalloc",
+           "mxfft_engine_create", "mxfft_engine_run", "mxfft_engine_get_status",
+           "mxfft_engine_destroy", "mxfft_tune", "mxfft_tune_save", "mxfft_tune_load",
+           "mxfft_tune_clear", "mxfft_server_create", "mxfft_server_submit",
+           "mxfft_server_poll", "mxfft_server_wait", "mxfft_server_stats",
+           "mxfft_server_destroy", "mxfft_status_string")
+
+
+class Item(ctypes.Structure):
+    """mxfft_item"""
+    _fields_ = [("n0", ctypes.c_int), ("n1", ctypes.c_int), ("format", ctypes.c_int),
+                ("k", ctypes.c_int), ("op", ctypes.c_int), ("slices", ctypes.c_int),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    """mxfft_request"""
+    _fields_ = [("n0", ctypes.c_int), ("n1", ctypes.c_int), ("format", ctypes.c_int),
+                ("k", ctypes.c_int), ("op", ctypes.c_int), ("slices", ctypes.c_int),
+                ("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p),
+                ("tag", ctypes.c_uint64)]
+
+
+class Completion(ctypes.Structure):
+    """mxfft_completion"""
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("device_flags", ctypes.c_int), ("t_submit_us", ctypes.c_double),
+                ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+class ServerConfig(ctypes.Structure):
+    """mxfft_server_config"""
+    _fields_ = [("slots", ctypes.c_int), ("max_batch_slices", ctypes.c_int),
+                ("mem_budget", ctypes.c_uint64), ("tau", ctypes.c_float),
+                ("target", ctypes.c_float), ("engine_flags", ctypes.c_int)]
 
 _lock = threading.Lock()
 _lib = None
@@ -63,6 +100,21 @@ def load(path: str | None = None):
         lib.mxfft_profile.argtypes = [P, I]
         lib.mxfft_profile_read.argtypes = [P, P, P, I]
         lib.mxfft_prescale_exponents_noalloc.argtypes = [P, I, I, I, I, F, F, P, P]
+        PP, U64 = ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64
+        lib.mxfft_engine_create.argtypes = [F, F, I, PP]
+        lib.mxfft_engine_run.argtypes = [P, ctypes.POINTER(Item), I, P]
+        lib.mxfft_engine_get_status.argtypes = [P, P, P, I]
+        lib.mxfft_engine_destroy.argtypes = [P]
+        lib.mxfft_tune.argtypes = [P, I, P, P]
+        lib.mxfft_tune_save.argtypes = [ctypes.c_char_p]
+        lib.mxfft_tune_load.argtypes = [ctypes.c_char_p]
+        lib.mxfft_tune_clear.argtypes = []
+        lib.mxfft_server_create.argtypes = [ctypes.POINTER(ServerConfig), PP]
+        lib.mxfft_server_submit.argtypes = [P, ctypes.POINTER(Request)]
+        lib.mxfft_server_poll.argtypes = [P, ctypes.POINTER(Completion), I, P]
+        lib.mxfft_server_wait.argtypes = [P, D]
+        lib.mxfft_server_stats.argtypes = [P, P, P, P]
+        lib.mxfft_server_destroy.argtypes = [P]
         lib.mxfft_status_string.argtypes = [I]
         lib.mxfft_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -162,6 +214,104 @@ def _fmt(fmt) -> int:
     return FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
 
 
+def _op(op) -> int:
+    return OPS[op] if isinstance(op, str) else int(op)
+
+
+def _check(st, what):
+    if st:
+        raise MxfftError(st, what)
+
+
+# ---- ragged batch executor ------------------------------------------------------
+
+def mxfft_engine_create(tau: float = 1e-3, target: float = 0.5, flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().mxfft_engine_create(float(tau), float(target), int(flags), ctypes.byref(h)),
+           "mxfft_engine_create")
+    return h.value
+
+
+def mxfft_engine_run(engine, items, stream=None) -> None:
+    arr = (Item * max(len(items), 1))(*items)
+    _check(load().mxfft_engine_run(engine, arr, len(items), stream), "mxfft_engine_run")
+
+
+def mxfft_engine_get_status(engine, k_count: int = 0):
+    """(device_flags, k list of length k_count) of the engine's last run."""
+    flags = ctypes.c_int(0)
+    karr = (ctypes.c_int32 * max(k_count, 1))()
+    _check(load().mxfft_engine_get_status(engine, ctypes.byref(flags), karr if k_count else None,
+                                          int(k_count)), "mxfft_engine_get_status")
+    return flags.value, list(karr)[:k_count]
+
+
+def mxfft_engine_destroy(engine) -> None:
+    if engine:
+        load().mxfft_engine_destroy(engine)
+
+
+# ---- autotuner -------------------------------------------------------------------
+
+def mxfft_tune(plan, batch: int, stream=None) -> int:
+    """Measure the radix-2 pass geometries of `plan` at `batch`; returns the
+    number of candidates timed."""
+    n = ctypes.c_int(0)
+    _check(load().mxfft_tune(plan, int(batch), stream, ctypes.byref(n)), "mxfft_tune")
+    return n.value
+
+
+def mxfft_tune_save(path: str) -> None:
+    _check(load().mxfft_tune_save(os.fsencode(path)), "mxfft_tune_save")
+
+
+def mxfft_tune_load(path: str) -> None:
+    _check(load().mxfft_tune_load(os.fsencode(path)), "mxfft_tune_load")
+
+
+def mxfft_tune_clear() -> None:
+    _check(load().mxfft_tune_clear(), "mxfft_tune_clear")
+
+
+# ---- request server --------------------------------------------------------------
+
+def mxfft_server_create(slots=4, max_batch_slices=256, mem_budget=0, tau=1e-3, target=0.5,
+                        engine_flags=0) -> int:
+    cfg = ServerConfig(int(slots), int(max_batch_slices), int(mem_budget), float(tau),
+                       float(target), int(engine_flags))
+    h = ctypes.c_void_p()
+    _check(load().mxfft_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mxfft_server_create")
+    return h.value
+
+
+def mxfft_server_submit(server, req: Request) -> None:
+    _check(load().mxfft_server_submit(server, ctypes.byref(req)), "mxfft_server_submit")
+
+
+def mxfft_server_poll(server, max_n: int = 256):
+    arr = (Completion * max(max_n, 1))()
+    n = ctypes.c_int(0)
+    _check(load().mxfft_server_poll(server, arr, int(max_n), ctypes.byref(n)), "mxfft_server_poll")
+    return [arr[i] for i in range(n.value)]
+
+
+def mxfft_server_wait(server, timeout_s: float) -> int:
+    return load().mxfft_server_wait(server, float(timeout_s))
+
+
+def mxfft_server_stats(server):
+    """(batches, peak device bytes of admitted requests, budget)."""
+    b, pk, bud = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(load().mxfft_server_stats(server, ctypes.byref(b), ctypes.byref(pk), ctypes.byref(bud)),
+           "mxfft_server_stats")
+    return b.value, pk.value, bud.value
+
+
+def mxfft_server_destroy(server) -> None:
+    if server:
+        load().mxfft_server_destroy(server)
+
+
 # ---- torch convenience ---------------------------------------------------------
 
 class Plan:
@@ -226,6 +376,117 @@ class Plan:
         if getattr(self, "handle", None):
             mxfft_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _check_tensor(x, name):
+    import torch
+    if x.dtype != torch.complex64 or not x.is_contiguous() or x.dim() < 2:
+        raise ValueError(f"{name}: expected a contiguous complex64 tensor [..., n0, n1]")
+
+
+class Engine:
+    """Ragged batch executor: run([(op, x, out, fmt, k), ...]) transforms each
+    CUDA tensor x [..., n0, n1] into out (may be x) in one set of launches on the
+    current torch stream, with the same bits as the per-plan calls."""
+
+    def __init__(self, tau: float = 1e-3, target: float = 0.5, graphs: bool = False,
+                 tc16: bool = False):
+        flags = (ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0)
+        self.handle = mxfft_engine_create(tau, target, flags)
+        self._slices = 0
+
+    def run(self, work, stream=None):
+        import torch
+        items = []
+        dev = None
+        for op, x, out, fmt, k in work:
+            _check_tensor(x, "x")
+            _check_tensor(out, "out")
+            if not x.is_cuda or out.shape != x.shape:
+                raise ValueError("x must be a CUDA tensor and out must match it")
+            dev = x.device
+            n0, n1 = x.shape[-2], x.shape[-1]
+            items.append(Item(n0, n1, _fmt(fmt), int(k), _op(op), x.numel() // (n0 * n1),
+                              x.data_ptr(), out.data_ptr()))
+        if stream is None and dev is not None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        mxfft_engine_run(self.handle, items, stream)
+        self._slices = sum(it.slices for it in items)
+
+    def status(self):
+        """(device_flags, [[k, k_inverse] per slice]) of the last run."""
+        flags, k = mxfft_engine_get_status(self.handle, 2 * self._slices)
+        return flags, [k[2 * i:2 * i + 2] for i in range(self._slices)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mxfft_engine_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Request server with continuous batching.  submit() takes host tensors
+    (pinned CPU complex64 [slices, n0, n1] for overlapped copies) that must
+    stay alive until their completion is returned by poll()."""
+
+    def __init__(self, slots=4, max_batch_slices=256, mem_budget=0, tau=1e-3, target=0.5,
+                 graphs=False, tc16=False):
+        flags = (ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0)
+        self.handle = mxfft_server_create(slots, max_batch_slices, mem_budget, tau, target, flags)
+        self._keep = {}
+
+    def submit(self, tag: int, x, out, fmt="e4m3", k: int = 32, op="forward") -> None:
+        _check_tensor(x, "x")
+        _check_tensor(out, "out")
+        if x.is_cuda or out.is_cuda or out.shape != x.shape:
+            raise ValueError("host tensors of equal shape expected")
+        n0, n1 = x.shape[-2], x.shape[-1]
+        req = Request(n0, n1, _fmt(fmt), int(k), _op(op), x.numel() // (n0 * n1), x.data_ptr(),
+                      out.data_ptr(), int(tag))
+        self._keep[int(tag)] = (x, out)
+        mxfft_server_submit(self.handle, req)
+
+    def poll(self, max_n: int = 1024):
+        done = mxfft_server_poll(self.handle, max_n)
+        for c in done:
+            self._keep.pop(int(c.tag), None)
+        return done
+
+    def wait(self, timeout_s: float = 60.0) -> bool:
+        return mxfft_server_wait(self.handle, timeout_s) == MXFFT_OK
+
+    def stats(self):
+        return mxfft_server_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mxfft_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

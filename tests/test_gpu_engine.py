@@ -1,0 +1,158 @@
+"""Ragged batch executor and autotuner on the GPU: an engine run over items
+of different shapes, formats, block sizes and ops gives the same bits as the
+per-plan calls (each of which matches the oracle bit for bit elsewhere), with
+and without CUDA graphs, when a graph is replayed on other buffers, in place,
+and under every tuned launch geometry."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2512_04317_gb300 import phantom
+
+pytestmark = pytest.mark.gpu
+
+# (n0, n1, format, k, op, slices)
+MIX = [
+    (64, 128, "e4m3", 32, "forward", 3),
+    (256, 256, "e5m2", 16, "roundtrip", 2),
+    (128, 128, "e4m3", 32, "inverse", 1),
+    (256, 256, "e5m2", 16, "forward", 2),     # same plan as item 2, other op
+    (2048, 64, "e2m1", 64, "forward", 1),
+    (512, 512, "e4m3", 32, "roundtrip", 1),
+    (8, 4, "e3m2", 8, "roundtrip", 2),
+]
+
+
+def inputs(seed):
+    import torch
+    xs = []
+    for i, (n0, n1, fmt, k, op, sl) in enumerate(MIX):
+        x = phantom.random_complex((sl, n0, n1), seed=seed * 100 + i, scale=2.0 + i)
+        xs.append(torch.from_numpy(x).cuda())
+    return xs
+
+
+def per_plan(xs):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    outs, ks = [], []
+    for (n0, n1, fmt, k, op, sl), x in zip(MIX, xs):
+        with mxfft.Plan(n0, n1, fmt, k) as p:
+            y = getattr(p, op)(x)
+            torch.cuda.synchronize()
+            st, flags, kk = p.status()
+            assert st == 0 and flags == 0
+            outs.append(y.cpu().numpy())
+            ks.extend(kk if op == "roundtrip" else [[v, 0] for v in kk])
+    return outs, ks
+
+
+def engine_run(eng, xs, in_place=False):
+    import torch
+    outs = [x if in_place else torch.empty_like(x) for x in xs]
+    eng.run([(op, x, y, fmt, k) for (n0, n1, fmt, k, op, sl), x, y in zip(MIX, xs, outs)])
+    torch.cuda.synchronize()
+    flags, ks = eng.status()
+    assert flags == 0
+    return [y.cpu().numpy() for y in outs], ks
+
+
+def assert_same(a, b):
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u.view(np.uint32), v.view(np.uint32))
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_engine_equals_per_plan_calls(graphs, cuda_device):
+    from paper_2512_04317_gb300 import mxfft
+    xs = inputs(1)
+    want, kwant = per_plan(xs)
+    with mxfft.Engine(graphs=graphs) as eng:
+        got, k = engine_run(eng, xs)
+        assert_same(got, want)
+        assert k == kwant
+        # same signature, other buffers and data: a graph is replayed with new tables
+        xs2 = inputs(2)
+        want2, _ = per_plan(xs2)
+        got2, _ = engine_run(eng, xs2)
+        assert_same(got2, want2)
+        # and the first buffers once more
+        got3, _ = engine_run(eng, xs)
+        assert_same(got3, want)
+
+
+def test_engine_in_place(cuda_device):
+    from paper_2512_04317_gb300 import mxfft
+    xs = inputs(3)
+    want, _ = per_plan(xs)
+    with mxfft.Engine(graphs=True) as eng:
+        got, _ = engine_run(eng, [x.clone() for x in xs], in_place=True)
+    assert_same(got, want)
+
+
+def test_engine_tensor_core_plans(cuda_device):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = torch.from_numpy(phantom.mri_batch(256, 256, 3, 1, config_id=41)).cuda()
+    z = torch.from_numpy(phantom.random_complex((2, 128, 128), seed=5)).cuda()
+    with mxfft.Plan(256, 256, "e4m3", 32, path="tc16") as p:
+        want = p.roundtrip(x).cpu().numpy()
+    with mxfft.Plan(128, 128, "e4m3", 32) as p:       # not covered by the tensor-core pass
+        wantz = p.forward(z).cpu().numpy()
+    with mxfft.Engine(tc16=True, graphs=True) as eng:
+        y, w = torch.empty_like(x), torch.empty_like(z)
+        eng.run([("roundtrip", x, y, "e4m3", 32), ("forward", z, w, "e4m3", 32)])
+        torch.cuda.synchronize()
+        assert eng.status()[0] == 0
+    np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    np.testing.assert_array_equal(w.cpu().numpy().view(np.uint32), wantz.view(np.uint32))
+
+
+def test_engine_rejects_bad_items(cuda_device):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = torch.zeros(4, 64, 64, dtype=torch.complex64, device="cuda")
+    with mxfft.Engine() as eng:
+        bad = [
+            mxfft.Item(64, 64, 0, 32, 0, 1, x.data_ptr() + 8, x.data_ptr() + 8),     # misaligned
+            mxfft.Item(64, 64, 0, 32, 0, 2, x.data_ptr(), x.data_ptr() + 64 * 64 * 8),  # overlap
+            mxfft.Item(48, 64, 0, 32, 0, 1, x.data_ptr(), x.data_ptr()),             # not 2^j
+            mxfft.Item(64, 64, 9, 32, 0, 1, x.data_ptr(), x.data_ptr()),             # format
+            mxfft.Item(64, 64, 0, 32, 5, 1, x.data_ptr(), x.data_ptr()),             # op
+        ]
+        for it in bad:
+            with pytest.raises(mxfft.MxfftError) as ei:
+                mxfft.mxfft_engine_run(eng.handle, [it], None)
+            assert ei.value.status == mxfft.MXFFT_ERR_INVALID
+        mxfft.mxfft_engine_run(eng.handle, [], None)   # nothing to do
+
+
+def test_tuned_geometries_give_the_same_bits(cuda_device, tmp_path):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = torch.from_numpy(phantom.mri_batch(256, 256, 8, 1, config_id=42)).cuda()
+    mxfft.mxfft_tune_clear()
+    with mxfft.Plan(256, 256, "e4m3", 32) as p:
+        want = p.roundtrip(x).cpu().numpy()
+        n = mxfft.mxfft_tune(p.handle, 8)
+        assert n >= 2
+        path = tmp_path / "tune.json"
+        mxfft.mxfft_tune_save(str(path))
+        entries = json.loads(path.read_text())["entries"]
+        assert {e["dim"] for e in entries} == {0, 1}
+        np.testing.assert_array_equal(p.roundtrip(x).cpu().numpy().view(np.uint32),
+                                      want.view(np.uint32))
+        # every candidate geometry, forced through the table
+        for ng in (1, 2, 4):
+            for e in entries:
+                e["ng"] = ng
+            path.write_text(json.dumps({"mxfft_tune": 1, "entries": entries}))
+            mxfft.mxfft_tune_load(str(path))
+            np.testing.assert_array_equal(p.roundtrip(x).cpu().numpy().view(np.uint32),
+                                          want.view(np.uint32))
+    mxfft.mxfft_tune_clear()

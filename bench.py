@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--path", choices=["radix2", "tc16"], default="radix2",
                     help="radix2: bit-exact radix-2 MX path; tc16: radix-16 tcgen05 variant")
+    ap.add_argument("--api", choices=["engine", "plan"], default="engine",
+                    help="engine: one batch-executor run per step, replayed as a CUDA graph; "
+                         "plan: mxfft_forward + mxfft_roundtrip calls")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -243,6 +248,130 @@ def cpu_baseline(w, ksp, img):
             "sample": f"{ns} of {ksp.shape[0]} slices, forward + round trip, {dt:.2f} s wall"}
 
 
+SERVING_SIZES = (128, 256, 512, 1024)
+SERVING_FRACTIONS = (0.3, 0.5, 0.7, 0.9)
+
+
+def serving_requests(n, seed=20251204):
+    """The serving mix: sizes uniform in {128, 256, 512, 1024}^2, 1-16 coils,
+    e4m3 / e5m2, k = 32, forward or round trip, Poisson arrivals (unit rate)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(SERVING_SIZES, n)
+    coils = rng.integers(1, 17, n)
+    fmts = rng.choice(["e4m3", "e5m2"], n)
+    ops = rng.choice(["forward", "roundtrip"], n)
+    gaps = rng.exponential(1.0, n)
+    return [dict(size=int(sizes[i]), coils=int(coils[i]), fmt=str(fmts[i]), op=str(ops[i]),
+                 gap=float(gaps[i])) for i in range(n)]
+
+
+def _pct(lat_ms):
+    import numpy as np
+    p50, p99 = np.percentile(lat_ms, [50, 99])
+    return float(p50), float(p99)
+
+
+def serving_leg(n_req, torch):
+    """Continuous-batching server under the serving mix: saturated rate, then
+    Poisson arrivals at fractions of it, p50 / p99 latency (submit to result in
+    host memory); the plain FP32 per-slice GPU path (torch.fft, one call per
+    coil slice, FIFO on one stream) under the same arrivals as comparator."""
+    from paper_2512_04317_gb300 import mxfft, phantom
+    reqs = serving_requests(n_req)
+    pool = 4
+    h_in, h_out = {}, {}
+    for sz in SERVING_SIZES:
+        x = phantom.mri_batch(sz, sz, 1, 16, config_id=4000 + sz)
+        h_in[sz] = torch.from_numpy(x).pin_memory()
+        h_out[sz] = [torch.empty_like(h_in[sz]).pin_memory() for _ in range(pool)]
+    work = [r["coils"] * r["size"] ** 2 * (3 if r["op"] == "roundtrip" else 1) for r in reqs]
+    pts_total = sum(r["coils"] * r["size"] ** 2 * (2 if r["op"] == "roundtrip" else 1)
+                    for r in reqs)
+
+    def run_mx(rate):
+        with mxfft.Server(slots=4, max_batch_slices=256) as srv:
+            # plans of every (size, format) resident before the clock starts
+            for i, sz in enumerate(SERVING_SIZES):
+                for f in ("e4m3", "e5m2"):
+                    srv.submit(10 ** 6 + 2 * i + (f == "e5m2"), h_in[sz][:1], h_out[sz][0][:1], f,
+                               32, "roundtrip")
+            srv.wait(60.0)
+            srv.poll(100)
+            t = time.perf_counter()
+            t0 = t
+            for i, r in enumerate(reqs):
+                if rate:
+                    t += r["gap"] / rate
+                    while time.perf_counter() < t:
+                        pass
+                sz, c = r["size"], r["coils"]
+                srv.submit(i, h_in[sz][:c], h_out[sz][i % pool][:c], r["fmt"], 32, r["op"])
+            assert srv.wait(600.0)
+            wall = time.perf_counter() - t0
+            done = srv.poll(len(reqs) + 16)
+            batches, peak, budget = srv.stats()
+        lat = [(c.t_done_us - c.t_submit_us) / 1e3 for c in done if c.tag < 10 ** 6]
+        assert len(lat) == len(reqs) and all(c.status == 0 for c in done)
+        return wall, lat, batches
+
+    def run_fp32(rate):
+        dev = torch.device("cuda")
+        d = {sz: torch.empty_like(h_in[sz], device=dev) for sz in SERVING_SIZES}
+        arrivals = []
+        t = time.perf_counter()
+        for r in reqs:
+            if rate:
+                t += r["gap"] / rate
+            arrivals.append(t)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        base = arrivals[0] if rate else t0
+        arrivals = [t0 + (a - base) if rate else t0 for a in arrivals]
+        lat = []
+        for i, r in enumerate(reqs):
+            while time.perf_counter() < arrivals[i]:
+                pass
+            sz, c = r["size"], r["coils"]
+            x = d[sz][:c]
+            x.copy_(h_in[sz][:c], non_blocking=True)
+            for j in range(c):
+                y = torch.fft.fft2(x[j])
+                if r["op"] == "roundtrip":
+                    y = torch.fft.ifft2(y)
+                x[j].copy_(y)
+            h_out[sz][i % pool][:c].copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - arrivals[i]) * 1e3)
+        return time.perf_counter() - t0, lat
+
+    out = {"requests": n_req, "mix": "sizes {128,256,512,1024}^2, 1-16 coils, e4m3/e5m2, "
+                                     "k=32, forward/roundtrip, Poisson arrivals",
+           "latency": "submit to result in pinned host memory",
+           "server": "4 slots, 256 slices per batch, memory budget 80% of free"}
+    wall, lat, batches = run_mx(0.0)
+    sat = n_req / wall
+    out["saturated"] = {"req_per_s": sat, "mpts_per_s": pts_total / wall / 1e6,
+                        "batches": batches, "p50_ms": _pct(lat)[0], "p99_ms": _pct(lat)[1]}
+    fw, flat = run_fp32(0.0)
+    out["fp32_per_slice_saturated"] = {"req_per_s": n_req / fw, "mpts_per_s": pts_total / fw / 1e6,
+                                       "p50_ms": _pct(flat)[0], "p99_ms": _pct(flat)[1]}
+    out["poisson"] = []
+    for frac in SERVING_FRACTIONS:
+        rate = frac * sat
+        wall, lat, batches = run_mx(rate)
+        p50, p99 = _pct(lat)
+        fw, flat = run_fp32(rate)
+        f50, f99 = _pct(flat)
+        out["poisson"].append({"load": frac, "req_per_s": rate,
+                               "mx": {"p50_ms": p50, "p99_ms": p99, "batches": batches,
+                                      "mpts_per_s": pts_total / wall / 1e6},
+                               "fp32_per_slice": {"p50_ms": f50, "p99_ms": f99,
+                                                  "mpts_per_s": pts_total / fw / 1e6}})
+    del work
+    return out
+
+
 def accuracy(plan, xk, xi, torch):
     """NRMSE / PSNR of the forward and round trip against FP64 (cuFFT double)."""
     y = plan.forward(xk)
@@ -297,10 +426,22 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     plan = mxfft.Plan(n0, n1, w["fmt"], w["k"], path=args.path)
     stream = torch.cuda.current_stream(dev)
+    engine = None
+    if args.api == "engine":
+        # one run per step: a statistics launch over both batches, the forward
+        # passes of both as one launch per axis, then the round trip's
+        # statistics and inverse passes; captured once, replayed as a graph
+        engine = mxfft.Engine(graphs=True, tc16=args.path == "tc16")
+        work = [("forward", xk, yk, w["fmt"], w["k"]), ("roundtrip", xi, yi, w["fmt"], w["k"])]
 
-    def step():
-        plan.forward(xk, out=yk)
-        plan.roundtrip(xi, out=yi)
+        def step():
+            engine.run(work)
+        launches_per_step = 6
+    else:
+        def step():
+            plan.forward(xk, out=yk)
+            plan.roundtrip(xi, out=yi)
+        launches_per_step = 3 + 6   # forward: stats, rows, cols; round trip: twice that
 
     for _ in range(args.warmup):
         step()
@@ -325,13 +466,15 @@ def main():
     t_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evs), world, dist, dev)
     ms_per_step = t_ms / args.steps
     value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, t_ms)
-    launches_per_step = 3 + 6   # forward: stats, rows, cols; round trip: twice that
 
-    # ---- per-kernel device time (event pairs on the launch stream) -----------
+    # ---- per-kernel device time (event pairs around each launch on the launch
+    # stream; the same kernels through the plan calls, since launches inside a
+    # graph cannot be bracketed one by one) ------------------------------------
     mxfft.mxfft_profile(plan.handle, True)
     for i in range(args.steps):
         flush.fill_(i & 0xff)
-        step()
+        plan.forward(xk, out=yk)
+        plan.roundtrip(xi, out=yi)
     torch.cuda.synchronize()
     mxfft.mxfft_profile(plan.handle, False)
     prof = mxfft.mxfft_profile_read(plan.handle)
@@ -375,6 +518,18 @@ def main():
     e2e_value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, e2e_steps, te_ms)
     bytes_io = 2 * pts * 8
 
+    # ---- the step's results equal the plan calls bit for bit -------------------
+    same = None
+    if engine is not None:
+        xk.copy_(torch.from_numpy(ksp_np).to(dev))
+        xi.copy_(torch.from_numpy(img_np).to(dev))
+        step()
+        a = torch.cat([yk.view(torch.int32).flatten(), yi.view(torch.int32).flatten()])
+        plan.forward(xk, out=yk)
+        plan.roundtrip(xi, out=yi)
+        b = torch.cat([yk.view(torch.int32).flatten(), yi.view(torch.int32).flatten()])
+        same = bool(torch.equal(a, b))
+
     # ---- accuracy and the FP32 comparator (context) ----------------------------
     acc = accuracy(plan, xk, xi, torch)
     st, flags, _ = plan.status()
@@ -400,6 +555,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, ksp_np, img_np)
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = serving_leg(args.serving_requests, torch)
 
     if rank == 0:
         out = {
@@ -408,6 +566,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "path": args.path,
+                       "api": args.api,
                        "n0": n0, "n1": n1,
                        "batch_per_gpu": batch, "format": w["fmt"], "k": w["k"],
                        "transforms_per_step": TRANSFORMS_PER_STEP,
@@ -425,8 +584,12 @@ def main():
                                       "batched_mpts_s": batched_fp32},
             "clocks": clk,
             "wall_s_timed_region": wall,
+            "engine_equals_plan_calls": same,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
+    if engine is not None:
+        engine.close()
     plan.close()
     if world > 1:
         dist.destroy_process_group()

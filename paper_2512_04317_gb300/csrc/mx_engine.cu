@@ -337,16 +337,14 @@ cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, i
     return err;
 }
 
-// Everything of one run after the tables are in the pinned staging buffer.
+// Everything of one run after its tables are in device memory.
 cudaError_t enqueue(mxfft_engine_s* e, const Layout& L, RunBuffers& b, cudaStream_t s) {
     char* d = (char*)b.d_blob;
     const SliceRef* d_refs = (const SliceRef*)d;
     const StatsRef* d_srefs = (const StatsRef*)(d + L.off_srefs);
     const int2* d_ctas = (const int2*)(d + L.off_ctas);
     size_t ev = 0;
-    cudaError_t err = cudaMemcpyAsync(b.d_blob, b.h_blob, L.bytes, cudaMemcpyHostToDevice, s);
-    if (err == cudaSuccess)
-        err = cudaMemsetAsync(b.d_st, 0, 2 * (size_t)b.st_cap * sizeof(SliceStats), s);
+    cudaError_t err = cudaMemsetAsync(b.d_st, 0, 2 * (size_t)b.st_cap * sizeof(SliceStats), s);
     if (err == cudaSuccess) err = launch_stats_ref(d_srefs, d_ctas + L.cta1, L.ncta1, s);
     if (err == cudaSuccess) err = run_stage(e, L.stage1, L.nbranch1, d_refs, s, ev);
     if (err == cudaSuccess && L.ncta2 > 0) err = launch_stats_ref(d_srefs, d_ctas + L.cta2, L.ncta2, s);
@@ -465,8 +463,11 @@ int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, voi
     bool changed = false;
     rc = stage_tables(*b, L, &changed);
     if (rc) return rc;
-
+    // the tables go up (stream-ordered, from the pinned staging buffer) only
+    // when they differ from the last upload into these buffers
     cudaError_t err = cudaSuccess;
+    if (changed) err = cudaMemcpyAsync(b->d_blob, b->h_blob, L.bytes, cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return cuda_status(err);
     if (g) {
         if (!g->exec) {
             // capture on the engine's own stream (the caller's may be the

@@ -22,10 +22,11 @@
 // slice), which is exactly 256 vectors per radix-16 stage, so a CTA of 256
 // threads runs each stage as one round of two MMAs (rows 0-127 and 128-255,
 // accumulators in tensor-memory columns 0-31 and 32-63); thread i owns
-// vector i.  CTAs are persistent: each walks tiles blockIdx.x, + gridDim.x,
-// ... and copies the next tile into its second shared buffer (cp.async, 16 B
-// per thread and copy) while it transforms the current one, so that HBM
-// reads overlap the MMA rounds.  The shared layouts are padded so that every
+// vector i.  CTAs are persistent: each walks a contiguous range of tiles
+// (mostly of one slice, whose buffers and exponent it resolves once) and
+// copies the next tile into its second shared buffer (cp.async, 16 B per
+// thread and copy) while it transforms the current one, so that HBM reads
+// overlap the MMA rounds.  The shared layouts are padded so that every
 // access pattern below is free of bank conflicts (see slot_row / slot_col).
 //
 // The only spin wait is on the MMA completion mbarrier, with an iteration
@@ -255,15 +256,38 @@ __device__ __forceinline__ float2 scale2(float2 v, float s) {
     return make_float2(__fmul_rn(v.x, s), __fmul_rn(v.y, s));
 }
 
-// Issue the cp.async copies of one tile into buffer buf (8 x 16 B per thread).
+// Buffers of the slice a CTA works on, resolved once per slice (a CTA walks
+// a contiguous range of tiles, so the slice rarely changes between tiles).
+struct SliceCache {
+    int slice = -1;
+    const float2* in;
+    float2* out;
+    int k;          // prescale exponent (when with_k)
+};
+
+__device__ __forceinline__ void resolve(const Args& a, int slice, bool with_k, SliceCache& c) {
+    if (c.slice == slice) return;
+    c.slice = slice;
+    const SliceStats* st;
+    if (a.ref) {
+        const SliceRef r = a.ref[slice];
+        c.in = r.in;
+        c.out = r.out;
+        st = r.st;
+    } else {
+        const size_t b = (size_t)slice * a.n0 * a.n1;
+        c.in = a.in + b;
+        c.out = a.out + b;
+        st = a.st + slice;
+    }
+    c.k = with_k ? st->k : 0;
+}
+
+// Issue the cp.async copies of one tile (transforms t0 .. t0 + T - 1 of the
+// slice whose input is in) into buffer buf (8 x 16 B per thread).
 template <int LOGN, int DIM>
-__device__ __forceinline__ void load_tile(const Args& a, int tile, uint32_t buf) {
+__device__ __forceinline__ void load_tile(const Args& a, const float2* in, int t0, uint32_t buf) {
     using G = Geo<LOGN>;
-    const int other = DIM == 1 ? a.n0 : a.n1;
-    const int per_slice = other / G::T;
-    const int slice = tile / per_slice;
-    const int t0 = (tile - slice * per_slice) * G::T;
-    const float2* in = a.ref ? a.ref[slice].in : a.in + (size_t)slice * a.n0 * a.n1;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const int q = threadIdx.x + i * kThreads;      // 16-byte chunk of the tile
@@ -313,7 +337,18 @@ tc16_pass_kernel(const Args a) {
     if (tid < 64) reinterpret_cast<uint4*>(sB)[tid] = __ldg(reinterpret_cast<const uint4*>(a.bmat) + tid);
     for (int i = tid; i < M * 16; i += kThreads) sTwA[(i >> 4) * kTwRow + (i & 15)] = __ldg(a.twA + i);
     if (r > 1 && tid < r * 16) sTwC[(tid >> 4) * kTwRow + (tid & 15)] = __ldg(a.twC + tid);
-    if ((int)blockIdx.x < ntiles) load_tile<LOGN, DIM>(a, blockIdx.x, buf_u32);
+    // CTA b takes the contiguous tiles [tile_begin, tile_end), shares equal to
+    // within one tile
+    const int share = ntiles / (int)gridDim.x, extra = ntiles % (int)gridDim.x;
+    const int tile_begin = (int)blockIdx.x * share + min((int)blockIdx.x, extra);
+    const int tile_end = tile_begin + share + ((int)blockIdx.x < extra ? 1 : 0);
+    const bool with_k = a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW;
+    SliceCache ld, cs;   // slices of the tile being loaded and of the current tile
+    if (tile_begin < tile_end) {
+        const int sl = tile_begin / per_slice;
+        resolve(a, sl, false, ld);
+        load_tile<LOGN, DIM>(a, ld.in, (tile_begin - sl * per_slice) * T, buf_u32);
+    }
     cp_async_commit();
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -329,23 +364,27 @@ tc16_pass_kernel(const Args a) {
     mm.ok = true;
 
     int cur = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, cur ^= 1) {
+    for (int tile = tile_begin; tile < tile_end; tile++, cur ^= 1) {
         // prefetch the next tile into the other buffer (free since the last
         // barrier of the previous iteration), then wait for this one
-        const int next = tile + gridDim.x;
-        if (next < ntiles)
-            load_tile<LOGN, DIM>(a, next, buf_u32 + (uint32_t)((cur ^ 1) * G::BUF_SLOTS * 8));
+        const int next = tile + 1;
+        if (next < tile_end) {
+            const int sl = next / per_slice;
+            resolve(a, sl, false, ld);
+            load_tile<LOGN, DIM>(a, ld.in, (next - sl * per_slice) * T,
+                                 buf_u32 + (uint32_t)((cur ^ 1) * G::BUF_SLOTS * 8));
+        }
         cp_async_commit();
         const int slice = tile / per_slice;
         const int t0 = (tile - slice * per_slice) * T;
         // the slice's exponent is fetched while the tile's copies land
-        const SliceStats* stp = a.ref ? a.ref[slice].st : a.st + slice;
-        const int kslice = (a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW) ? stp->k : 0;
+        resolve(a, slice, with_k, cs);
+        const int kslice = cs.k;
         cp_async_wait_prev();
         __syncthreads();
 
         float2* d = bufs + cur * G::BUF_SLOTS;
-        float2* __restrict__ out = a.ref ? a.ref[slice].out : a.out + (size_t)slice * a.n0 * a.n1;
+        float2* __restrict__ out = cs.out;
 
         // ---- round A: vector (t, j2), elements x[M j1 + j2] ----------------
         {

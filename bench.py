@@ -66,6 +66,8 @@ def parse():
                     help="engine: one batch-executor run per step, replayed as a CUDA graph; "
                          "plan: mxfft_forward + mxfft_roundtrip calls")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="smaller case of a workload (profiling): about this many slices")
     ap.add_argument("--serving-requests", type=int, default=2000)
     return ap.parse_args()
 
@@ -115,30 +117,43 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def source_digest():
-    h = hashlib.sha256()
+# sources each kernel is compiled from (its own file(s) and the shared headers)
+KERNEL_SOURCES = {
+    "fast_pass_kernel": ("mx_fast", "mx_device.cuh", "mx_internal.h"),
+    "pass_kernel": ("mx_pass.cu", "mx_device.cuh", "mx_internal.h"),
+    "tc16_pass_kernel": ("mx_tc16.cu", "mx_device.cuh", "mx_internal.h"),
+    "stats_kernel": ("mx_stats.cu", "mx_device.cuh", "mx_internal.h"),
+}
+
+
+def source_digest(kernel, read=None):
+    """Digest of the sources of one kernel (see KERNEL_SOURCES)."""
     csrc = os.path.join(ROOT, "paper_2512_04317_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+    if read is None:
+        def read(name):
             with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+                return f.read()
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")) and name.startswith(KERNEL_SOURCES[kernel]):
+            h.update(name.encode() + b"\0" + read(name))
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload, pts_per_launch):
-    """DRAM bytes per launch from the committed ncu summary, when it was taken
-    on the current kernel sources; else None."""
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, when it was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except Exception:
         return None
-    ent = rec.get(kernel, {})
-    if ent.get("source_digest") != source_digest():
-        return None
-    per_pt = ent.get("dram_bytes_per_point_per_launch")
-    return None if per_pt is None else float(per_pt) * pts_per_launch
+    for ent in rec.get("entries", []):
+        if (ent.get("kernel") == kernel and ent.get("workload") == workload and
+                ent.get("source_digest") == source_digest(kernel)):
+            return float(ent["dram_bytes_per_point_per_launch"]) * pts_per_launch
+    return None
 
 
 class ClockSampler:
@@ -391,7 +406,10 @@ def accuracy(plan, xk, xi, torch):
 
 def main():
     args = parse()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.slices > 0:
+        w["nslices"] = max(1, -(-args.slices // w["ncoils"]))
+        w["desc"] += f" (reduced to {w['nslices'] * w['ncoils']} slices)"
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, w, world, rank)

@@ -69,7 +69,13 @@ typedef enum {
                                16-point input vector one MX block (k must be 32), MX-quantised
                                twiddles between the radix-16 stages; approximate, not bit-exact.
                                Needs n0, n1 in {256, 512} and format E4M3 or E5M2, else
-                               MXFFT_ERR_UNSUPPORTED. */
+                               MXFFT_ERR_UNSUPPORTED. */,
+    MXFFT_OPT_TEST_STALL = 5  /* test hook of the bounded wait, 0 or 1; default 0.  1: the
+                               tensor-core pass withholds its matrix products, so every CTA's
+                               wait for their completion runs out (after 100 ms), the CTA
+                               stops, and mxfft_get_status returns MXFFT_ERR_TIMEOUT (device
+                               flag bit 1); the outputs of such a call are undefined.  No
+                               effect on the radix-2 path. */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;

@@ -345,6 +345,14 @@ cudaError_t enqueue(mxfft_engine_s* e, const Layout& L, RunBuffers& b, cudaStrea
     const int2* d_ctas = (const int2*)(d + L.off_ctas);
     size_t ev = 0;
     cudaError_t err = cudaMemsetAsync(b.d_st, 0, 2 * (size_t)b.st_cap * sizeof(SliceStats), s);
+    // the plans' timeout flags report this run only
+    std::vector<mxfft_plan_s*> seen;
+    for (const std::vector<PassLaunch>* st : {&L.stage1, &L.stage2})
+        for (const PassLaunch& pl : *st)
+            if (err == cudaSuccess && pl.p->d_err && std::find(seen.begin(), seen.end(), pl.p) == seen.end()) {
+                seen.push_back(pl.p);
+                err = cudaMemsetAsync(pl.p->d_err, 0, sizeof(int), s);
+            }
     if (err == cudaSuccess) err = launch_stats_ref(d_srefs, d_ctas + L.cta1, L.ncta1, s);
     if (err == cudaSuccess) err = run_stage(e, L.stage1, L.nbranch1, d_refs, s, ev);
     if (err == cudaSuccess && L.ncta2 > 0) err = launch_stats_ref(d_srefs, d_ctas + L.cta2, L.ncta2, s);

@@ -98,6 +98,7 @@ struct Tc16Args {
     int prologue, epilogue, lg_total;
     uint32_t idesc;                   // tcgen05 instruction descriptor
     int* err;                         // set when a bounded wait gives up
+    int stall;                        // test hook: issue no matrix product
 };
 
 // One slice of a ragged statistics launch (slices of different sizes and

@@ -30,6 +30,7 @@ struct mxfft_plan_s {
     mxfft::TwA twa[2][2];             // [axis][dir] stages h <= 16 for the register pass
     int force_generic;         // 1: always use the generic pass kernel
     int path;                  // 0 radix-2 MX, 1 tensor-core radix-16
+    int test_stall;            // MXFFT_OPT_TEST_STALL
     uint8_t* d_bmat[2];        // [dir] tensor-core DFT matrix codes (core-matrix layout)
     float2* d_twA[2][2];       // [axis][dir] radix-16 stage twiddles
     float2* d_twC[2][2];       // [axis][dir] twiddles before the radix-2 stage (n = 512)

@@ -29,9 +29,9 @@
 // overlap the MMA rounds.  The shared layouts are padded so that every
 // access pattern below is free of bank conflicts (see slot_row / slot_col).
 //
-// The only spin wait is on the MMA completion mbarrier, with an iteration
-// limit: on time-out the kernel sets the plan's error flag, waits once more
-// (bounded) for its own MMA, frees its tensor memory and finishes.
+// The only spin wait is on the MMA completion mbarrier, bounded to 100 ms by
+// the global timer: on time-out the kernel sets the plan's error flag, waits
+// once more (bounded) for its own MMA, frees its tensor memory and finishes.
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -43,7 +43,7 @@ namespace tc16 {
 constexpr int kThreads = 256;
 constexpr int kTilePts = 4096;        // points per tile = 256 vectors x 16
 constexpr uint32_t kTmemCols = 64;    // two 128 x 32 FP32 accumulators
-constexpr int kWaitLimit = 1 << 22;
+constexpr uint64_t kWaitNs = 100000000;   // bound of one completion wait: 100 ms
 // Dynamic shared memory: A operand (2 x 128 rows x 32 B), B operand (32 x 32
 // B), twiddles (rows of 16 padded to 18 values so that a quarter-warp's 16-byte
 // reads of 8 consecutive rows hit distinct banks), then the two tile buffers.
@@ -126,12 +126,21 @@ __device__ __forceinline__ float fmax_nan(float a, float b) {
     return d;
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase of parity `phase` to complete, at most kWaitNs.
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase) {
     uint32_t done = 0;
-    for (int it = 0; it < kWaitLimit && !done; it++) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
                      " selp.u32 %0, 1, 0, p; }"
                      : "=r"(done) : "r"(mbar), "r"(phase));
+        if (done || globaltimer_ns() - t0 > kWaitNs) break;
     }
     return done != 0;
 }
@@ -181,7 +190,7 @@ struct Mma {
 // before the call may be reused / are visible.
 template <int FMT>
 __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
-                                            uint32_t idesc, int emax) {
+                                            uint32_t idesc, int emax, bool issue) {
     const int tid = threadIdx.x, warp = tid >> 5;
     float m[16];
 #pragma unroll
@@ -210,7 +219,7 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
+    if (tid == 0 && issue) {
         const uint64_t bd = smem_desc(mm.sb, 128, 256);
         const uint64_t a0 = smem_desc(mm.sa, 128, 256);
         const uint64_t a1 = smem_desc(mm.sa + 4096, 128, 256);
@@ -401,7 +410,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
             }
-            dft16_round<FMT>(x, y, mm, a.idesc, emax);
+            dft16_round<FMT>(x, y, mm, a.idesc, emax, !a.stall);
             const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
@@ -440,7 +449,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
             }
-            dft16_round<FMT>(x, y, mm, a.idesc, emax);
+            dft16_round<FMT>(x, y, mm, a.idesc, emax, !a.stall);
             if (r == 1) {
                 // X[k1 + 16 k2]
 #pragma unroll

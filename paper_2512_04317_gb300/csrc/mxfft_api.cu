@@ -306,6 +306,8 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
     SliceStats* st_i = p->d_st + p->st_cap;
     cudaError_t e = cudaMemsetAsync(st_f, 0, sizeof(SliceStats) * (size_t)batch, s);
     if (e == cudaSuccess && op == 2) e = cudaMemsetAsync(st_i, 0, sizeof(SliceStats) * (size_t)batch, s);
+    // the timeout flag reports this call only
+    if (e == cudaSuccess && p->d_err) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_status(e);
     const float2* x = (const float2*)in;
     float2* y = (float2*)out;
@@ -417,6 +419,7 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
         const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
         t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
         t.err = p->d_err;
+        t.stall = p->test_stall;
         ProfRec* r = prof_begin(p, 3, s);
         cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
         prof_end(r, s);
@@ -546,6 +549,10 @@ int mxfft_set_option(mxfft_plan_t p, int key, double value) {
         case MXFFT_OPT_GENERIC:
             if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
             p->force_generic = value != 0.0;
+            return MXFFT_OK;
+        case MXFFT_OPT_TEST_STALL:
+            if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
+            p->test_stall = value != 0.0;
             return MXFFT_OK;
         default:
             return MXFFT_ERR_INVALID;

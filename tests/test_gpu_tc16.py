@@ -96,3 +96,27 @@ def test_tc16_in_place(cuda_device):
         p.roundtrip(xt, out=xt)
         torch.cuda.synchronize()
     np.testing.assert_array_equal(xt.cpu().numpy().view(np.uint32), want.view(np.uint32))
+
+
+def test_bounded_wait_times_out_and_the_context_stays_usable(cuda_device):
+    # the products are withheld, so the completion mbarrier is never arrived
+    # on: every CTA's wait must run out (100 ms), set the timeout flag and let
+    # the kernel finish; afterwards the same plan computes correctly
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = torch.from_numpy(phantom.mri_batch(256, 256, 2, 1, config_id=34)).cuda()
+    with mxfft.Plan(256, 256, "e4m3", 32, path="tc16") as ref:
+        want = ref.forward(x).cpu().numpy()
+    with mxfft.Plan(256, 256, "e4m3", 32, path="tc16") as p:
+        mxfft.mxfft_set_option(p.handle, mxfft.OPT_TEST_STALL, 1)
+        p.forward(x)
+        torch.cuda.synchronize()
+        st, flags, _ = p.status()
+        assert st == mxfft.MXFFT_ERR_TIMEOUT and flags & 2
+        mxfft.mxfft_set_option(p.handle, mxfft.OPT_TEST_STALL, 0)
+        got = p.forward(x)
+        torch.cuda.synchronize()
+        st, flags, _ = p.status()
+        assert st == 0 and flags == 0
+        np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), want.view(np.uint32))

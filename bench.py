@@ -287,7 +287,8 @@ def _pct(lat_ms):
     return float(p50), float(p99)
 
 
-def serving_leg(n_req, torch):
+def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
+                fractions=SERVING_FRACTIONS, rates=None):
     """Continuous-batching server under the serving mix: saturated rate, then
     Poisson arrivals at fractions of it, p50 / p99 latency (submit to result in
     host memory); the plain FP32 per-slice GPU path (torch.fft, one call per
@@ -305,7 +306,8 @@ def serving_leg(n_req, torch):
                     for r in reqs)
 
     def run_mx(rate):
-        with mxfft.Server(slots=4, max_batch_slices=256) as srv:
+        with mxfft.Server(slots=slots, max_batch_slices=batch_slices,
+                          max_batch_bytes=batch_mb << 20) as srv:
             # plans of every (size, format) resident before the clock starts
             for i, sz in enumerate(SERVING_SIZES):
                 for f in ("e4m3", "e5m2"):
@@ -363,26 +365,31 @@ def serving_leg(n_req, torch):
     out = {"requests": n_req, "mix": "sizes {128,256,512,1024}^2, 1-16 coils, e4m3/e5m2, "
                                      "k=32, forward/roundtrip, Poisson arrivals",
            "latency": "submit to result in pinned host memory",
-           "server": "4 slots, 256 slices per batch, memory budget 80% of free"}
+           "server": f"{slots} slots, batches of at most {batch_slices} slices and "
+                     f"{batch_mb} MiB, memory budget 80% of free"}
     wall, lat, batches = run_mx(0.0)
     sat = n_req / wall
     out["saturated"] = {"req_per_s": sat, "mpts_per_s": pts_total / wall / 1e6,
                         "batches": batches, "p50_ms": _pct(lat)[0], "p99_ms": _pct(lat)[1]}
-    fw, flat = run_fp32(0.0)
-    out["fp32_per_slice_saturated"] = {"req_per_s": n_req / fw, "mpts_per_s": pts_total / fw / 1e6,
-                                       "p50_ms": _pct(flat)[0], "p99_ms": _pct(flat)[1]}
+    if fp32:
+        fw, flat = run_fp32(0.0)
+        out["fp32_per_slice_saturated"] = {"req_per_s": n_req / fw,
+                                           "mpts_per_s": pts_total / fw / 1e6,
+                                           "p50_ms": _pct(flat)[0], "p99_ms": _pct(flat)[1]}
     out["poisson"] = []
-    for frac in SERVING_FRACTIONS:
-        rate = frac * sat
+    for frac in (rates if rates else fractions):
+        rate = frac if rates else frac * sat
         wall, lat, batches = run_mx(rate)
         p50, p99 = _pct(lat)
-        fw, flat = run_fp32(rate)
-        f50, f99 = _pct(flat)
-        out["poisson"].append({"load": frac, "req_per_s": rate,
-                               "mx": {"p50_ms": p50, "p99_ms": p99, "batches": batches,
-                                      "mpts_per_s": pts_total / wall / 1e6},
-                               "fp32_per_slice": {"p50_ms": f50, "p99_ms": f99,
-                                                  "mpts_per_s": pts_total / fw / 1e6}})
+        ent = {"load": frac, "req_per_s": rate,
+               "mx": {"p50_ms": p50, "p99_ms": p99, "batches": batches,
+                      "mpts_per_s": pts_total / wall / 1e6}}
+        if fp32:
+            fw, flat = run_fp32(rate)
+            f50, f99 = _pct(flat)
+            ent["fp32_per_slice"] = {"p50_ms": f50, "p99_ms": f99,
+                                     "mpts_per_s": pts_total / fw / 1e6}
+        out["poisson"].append(ent)
     del work
     return out
 

@@ -306,6 +306,8 @@ typedef struct {
     uint64_t mem_budget;       /* device bytes for request data; 0: 80% of free memory */
     float tau, target;         /* of every plan */
     int engine_flags;          /* MXFFT_ENGINE_* */
+    uint64_t max_batch_bytes;  /* request bytes per batch (a larger request forms a batch
+                                  alone); 0: no limit */
 } mxfft_server_config;
 
 typedef struct mxfft_server_s *mxfft_server_t;
@@ -317,7 +319,8 @@ typedef struct mxfft_server_s *mxfft_server_t;
  *   request; a request larger than the whole memory budget completes with
  *   MXFFT_ERR_NOMEM.
  * mxfft_server_poll -- move up to max finished completions to out; *n_out
- *   receives their number.
+ *   receives their number.  A request completes when its own result is in
+ *   host memory (each request's copy-out ends with its own host callback).
  * mxfft_server_wait -- block until every submitted request has completed or
  *   timeout_s has passed (MXFFT_ERR_TIMEOUT).
  * mxfft_server_stats -- counters: batches launched, peak device bytes held by

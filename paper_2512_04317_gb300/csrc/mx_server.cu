@@ -5,13 +5,14 @@
 // free and the device memory budget allows: all queued requests that fit form
 // one batch, which is copied in, transformed in place by one engine run and
 // copied out on that slot while batches admitted earlier still run on other
-// slots.  A host callback at the end of each slot's stream returns the slot
-// and the batch's memory.  No kernel waits on the host: the device-side part
+// slots.  Each request's copy out ends with its own host callback, which
+// completes that request; the last one returns the slot and its memory.  No kernel waits on the host: the device-side part
 // of a request is the engine's launches, the host side only enqueues.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstddef>
+#include <cstdint>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -37,7 +38,12 @@ struct SReq {
 
 struct DoneCtx {
     struct ::mxfft_server_s* srv;
-    int slot;
+    int slot, req;
+};
+
+struct Finished {
+    int slot, req;
+    double t;
 };
 
 struct Slot {
@@ -45,11 +51,13 @@ struct Slot {
     mxfft_engine_t eng = nullptr;
     bool busy = false;
     std::vector<SReq> reqs;
+    std::vector<DoneCtx> ctx;         // one per request, stable while the batch runs
+    int n_done = 0;
+    int first_slice = 0;              // running slice offset while retiring
     size_t bytes = 0;
     uint32_t* h_flags = nullptr;      // pinned: per slice, non-finite input magnitude
     int flags_cap = 0;
     int status = MXFFT_OK;
-    DoneCtx ctx;
 };
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
@@ -65,7 +73,7 @@ struct mxfft_server_s {
     std::deque<SReq> pending;
     std::deque<mxfft_completion> done;
     std::vector<Slot> slots;
-    std::vector<int> finished;
+    std::vector<Finished> finished;
     size_t budget = 0, inflight = 0, peak = 0;
     uint64_t submitted = 0, completed = 0, batches = 0;
     bool stop = false;
@@ -74,16 +82,18 @@ struct mxfft_server_s {
 
 namespace {
 
-void CUDART_CB slot_done(void* arg) {
+void CUDART_CB request_done(void* arg) {
     DoneCtx* c = static_cast<DoneCtx*>(arg);
+    const double t = now_us();
     std::lock_guard<std::mutex> lk(c->srv->mu);
-    c->srv->finished.push_back(c->slot);
+    c->srv->finished.push_back(Finished{c->slot, c->req, t});
     c->srv->cv.notify_all();
 }
 
-// Enqueue a batch on its slot; returns false if nothing was enqueued that will
-// call slot_done (the caller then retires the slot itself).
-bool launch_batch(mxfft_server_s* S, int i) {
+// Enqueue a batch on its slot: copies in, one engine run, the flags, then per
+// request its copy out and a host callback.  Returns the number of requests
+// whose callback was enqueued (the caller completes the rest itself).
+int launch_batch(mxfft_server_s* S, int i) {
     Slot& sl = S->slots[i];
     cudaStream_t s = sl.stream;
     int slices = 0;
@@ -97,7 +107,7 @@ bool launch_batch(mxfft_server_s* S, int i) {
         while (cap < slices) cap *= 2;
         if (cudaMallocHost(&sl.h_flags, cap * sizeof(uint32_t)) != cudaSuccess) {
             sl.status = MXFFT_ERR_NOMEM;
-            return false;
+            return 0;
         }
         sl.flags_cap = cap;
     }
@@ -105,7 +115,7 @@ bool launch_batch(mxfft_server_s* S, int i) {
     cudaError_t err = cudaMallocAsync((void**)&d, sl.bytes, s);
     if (err != cudaSuccess) {
         sl.status = cuda_status(err);
-        return false;
+        return 0;
     }
     std::vector<mxfft_item> items;
     size_t off = 0;
@@ -117,50 +127,52 @@ bool launch_batch(mxfft_server_s* S, int i) {
     int rc = err == cudaSuccess ? MXFFT_OK : cuda_status(err);
     if (rc == MXFFT_OK) rc = mxfft_engine_run(sl.eng, items.data(), (int)items.size(), s);
     if (rc == MXFFT_OK) rc = cuda_status(engine_flags_async(sl.eng, sl.h_flags, s));
-    off = 0;
-    for (const SReq& q : sl.reqs) {
-        if (rc == MXFFT_OK) rc = cuda_status(cudaMemcpyAsync(q.r.host_out, d + off, q.bytes, cudaMemcpyDeviceToHost, s));
-        off += q.bytes;
-    }
-    cudaFreeAsync(d, s);
     sl.status = rc;
     if (rc != MXFFT_OK) std::fill(sl.h_flags, sl.h_flags + slices, 0u);
-    return cudaLaunchHostFunc(s, slot_done, &sl.ctx) == cudaSuccess;
+    sl.ctx.assign(sl.reqs.size(), DoneCtx{S, i, 0});
+    off = 0;
+    int queued = 0;
+    for (size_t j = 0; j < sl.reqs.size(); j++) {
+        const SReq& q = sl.reqs[j];
+        if (rc == MXFFT_OK)
+            rc = cuda_status(cudaMemcpyAsync(q.r.host_out, d + off, q.bytes, cudaMemcpyDeviceToHost, s));
+        if (rc != MXFFT_OK) sl.status = rc;
+        off += q.bytes;
+        sl.ctx[j].req = (int)j;
+        if (cudaLaunchHostFunc(s, request_done, &sl.ctx[j]) != cudaSuccess) break;
+        queued++;
+    }
+    cudaFreeAsync(d, s);
+    return queued;
 }
 
-void retire(mxfft_server_s* S, std::unique_lock<std::mutex>& lk, int i) {
+// One request of a slot's batch has its result in host memory.
+void complete(mxfft_server_s* S, int i, int j, double t) {
     Slot& sl = S->slots[i];
-    std::vector<SReq> reqs;
-    reqs.swap(sl.reqs);
-    const int status = sl.status;
-    const size_t bytes = sl.bytes;
-    const double t = now_us();
-    std::vector<mxfft_completion> cs;
-    int g = 0;
-    for (const SReq& q : reqs) {
-        int fl = 0;
-        for (int k = 0; k < q.r.slices; k++, g++)
-            if (status == MXFFT_OK && sl.h_flags && sl.h_flags[g]) fl = 1;
-        cs.push_back(mxfft_completion{q.r.tag, status, fl, q.t_submit, q.t_admit, t});
-    }
-    (void)lk;
-    S->inflight -= bytes;
-    sl.bytes = 0;
-    sl.busy = false;
-    for (const auto& c : cs) S->done.push_back(c);
-    S->completed += cs.size();
+    const SReq& q = sl.reqs[j];
+    int first = 0;
+    for (int r = 0; r < j; r++) first += sl.reqs[r].r.slices;
+    int fl = 0;
+    for (int k = 0; k < q.r.slices; k++)
+        if (sl.status == MXFFT_OK && sl.h_flags && sl.h_flags[first + k]) fl = 1;
+    S->done.push_back(mxfft_completion{q.r.tag, sl.status, fl, q.t_submit, q.t_admit, t});
+    S->completed++;
     S->cv_done.notify_all();
+    if (++sl.n_done == (int)sl.reqs.size()) {
+        S->inflight -= sl.bytes;
+        sl.bytes = 0;
+        sl.reqs.clear();
+        sl.n_done = 0;
+        sl.busy = false;
+    }
 }
 
 void worker_main(mxfft_server_s* S) {
     cudaSetDevice(S->device);
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
-        while (!S->finished.empty()) {
-            const int i = S->finished.back();
-            S->finished.pop_back();
-            retire(S, lk, i);
-        }
+        for (const Finished& f : S->finished) complete(S, f.slot, f.req, f.t);
+        S->finished.clear();
         bool busy = false;
         int free_slot = -1;
         for (size_t i = 0; i < S->slots.size(); i++) {
@@ -173,6 +185,7 @@ void worker_main(mxfft_server_s* S) {
             size_t bytes = 0;
             int slices = 0;
             const double ta = now_us();
+            const size_t max_bytes = S->cfg.max_batch_bytes ? (size_t)S->cfg.max_batch_bytes : SIZE_MAX;
             while (!S->pending.empty()) {
                 SReq q = S->pending.front();
                 if (q.bytes > S->budget) {
@@ -184,7 +197,9 @@ void worker_main(mxfft_server_s* S) {
                     continue;
                 }
                 if (S->inflight + bytes + q.bytes > S->budget) break;
-                if (!batch.empty() && slices + q.r.slices > S->cfg.max_batch_slices) break;
+                if (!batch.empty() &&
+                    (slices + q.r.slices > S->cfg.max_batch_slices || bytes + q.bytes > max_bytes))
+                    break;
                 q.t_admit = ta;
                 batch.push_back(q);
                 bytes += q.bytes;
@@ -195,14 +210,19 @@ void worker_main(mxfft_server_s* S) {
                 Slot& sl = S->slots[free_slot];
                 sl.busy = true;
                 sl.bytes = bytes;
+                sl.n_done = 0;
                 sl.reqs.swap(batch);
                 S->inflight += bytes;
                 S->peak = std::max(S->peak, S->inflight);
                 S->batches++;
                 lk.unlock();
-                const bool queued = launch_batch(S, free_slot);
+                const int queued = launch_batch(S, free_slot);
                 lk.lock();
-                if (!queued) S->finished.push_back(free_slot);
+                // requests without a callback complete here, with the slot's status
+                Slot& sl2 = S->slots[free_slot];
+                if (queued < (int)sl2.reqs.size() && sl2.status == MXFFT_OK) sl2.status = MXFFT_ERR_CUDA;
+                for (int j = queued, n = (int)sl2.reqs.size(); j < n; j++)
+                    S->finished.push_back(Finished{free_slot, j, now_us()});
                 continue;
             }
         }
@@ -240,7 +260,6 @@ int mxfft_server_create(const mxfft_server_config* cfg, mxfft_server_t* out) {
     S->slots.resize(cfg->slots);
     for (int i = 0; i < cfg->slots && rc == MXFFT_OK; i++) {
         Slot& sl = S->slots[i];
-        sl.ctx = DoneCtx{S, i};
         rc = cuda_status(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
         if (rc == MXFFT_OK) rc = mxfft_engine_create(cfg->tau, cfg->target, cfg->engine_flags, &sl.eng);
     }

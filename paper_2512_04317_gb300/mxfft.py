@@ -64,7 +64,8 @@ class ServerConfig(ctypes.Structure):
     """mxfft_server_config"""
     _fields_ = [("slots", ctypes.c_int), ("max_batch_slices", ctypes.c_int),
                 ("mem_budget", ctypes.c_uint64), ("tau", ctypes.c_float),
-                ("target", ctypes.c_float), ("engine_flags", ctypes.c_int)]
+                ("target", ctypes.c_float), ("engine_flags", ctypes.c_int),
+                ("max_batch_bytes", ctypes.c_uint64)]
 
 _lock = threading.Lock()
 _lib = None
@@ -276,9 +277,9 @@ def mxfft_tune_clear() -> None:
 # ---- request server --------------------------------------------------------------
 
 def mxfft_server_create(slots=4, max_batch_slices=256, mem_budget=0, tau=1e-3, target=0.5,
-                        engine_flags=0) -> int:
+                        engine_flags=0, max_batch_bytes=0) -> int:
     cfg = ServerConfig(int(slots), int(max_batch_slices), int(mem_budget), float(tau),
-                       float(target), int(engine_flags))
+                       float(target), int(engine_flags), int(max_batch_bytes))
     h = ctypes.c_void_p()
     _check(load().mxfft_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mxfft_server_create")
     return h.value
@@ -454,9 +455,10 @@ class Server:
     stay alive until their completion is returned by poll()."""
 
     def __init__(self, slots=4, max_batch_slices=256, mem_budget=0, tau=1e-3, target=0.5,
-                 graphs=False, tc16=False):
+                 graphs=False, tc16=False, max_batch_bytes=0):
         flags = (ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0)
-        self.handle = mxfft_server_create(slots, max_batch_slices, mem_budget, tau, target, flags)
+        self.handle = mxfft_server_create(slots, max_batch_slices, mem_budget, tau, target, flags,
+                                          max_batch_bytes)
         self._keep = {}
 
     def submit(self, tag: int, x, out, fmt="e4m3", k: int = 32, op="forward") -> None:

@@ -26,7 +26,7 @@ def test_engine_and_server_argument_checks(lib):
     assert lib.mxfft_engine_destroy(None) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_tune(None, 1, None, None) == mxfft.MXFFT_ERR_INVALID
     for slots, mbs in [(0, 16), (65, 16), (2, 0)]:
-        cfg = mxfft.ServerConfig(slots, mbs, 0, 1e-3, 0.5, 0)
+        cfg = mxfft.ServerConfig(slots, mbs, 0, 1e-3, 0.5, 0, 0)
         assert lib.mxfft_server_create(ctypes.byref(cfg), ctypes.byref(h)) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_server_submit(None, None) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_server_poll(None, None, 0, None) == mxfft.MXFFT_ERR_INVALID
@@ -40,7 +40,8 @@ def test_item_and_request_layouts_match_the_header():
     assert ctypes.sizeof(mxfft.Item) == 40 and mxfft.Item.in_.offset == 24
     assert ctypes.sizeof(mxfft.Request) == 48 and mxfft.Request.tag.offset == 40
     assert ctypes.sizeof(mxfft.Completion) == 40 and mxfft.Completion.t_done_us.offset == 32
-    assert ctypes.sizeof(mxfft.ServerConfig) == 32 and mxfft.ServerConfig.tau.offset == 16
+    assert ctypes.sizeof(mxfft.ServerConfig) == 40 and mxfft.ServerConfig.tau.offset == 16
+    assert mxfft.ServerConfig.max_batch_bytes.offset == 32
 
 
 def test_tuning_file_round_trip(lib, tmp_path):

@@ -80,6 +80,8 @@ def _load():
         lib.oracle_format_info.restype = i32
         lib.oracle_fft2d_exact.argtypes = [P, P, i32, i32, i32, i32]
         lib.oracle_fft2d_exact.restype = i32
+        lib.oracle_rss.argtypes = [P, P, i64, i32, i64]
+        lib.oracle_rss.restype = None
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = i32
         _lib = lib
@@ -200,6 +202,20 @@ def butterfly_block(u, v, w, fmt="e4m3", renorm=True, direct_enc=False):
     if rc:
         raise ValueError("bad butterfly arguments")
     return y0, y1
+
+
+def rss(z: np.ndarray, coils: int) -> np.ndarray:
+    """Eq. (1) coil combine: z complex64 [images * coils, n0, n1] (coil fastest)
+    -> float32 [images, n0, n1]."""
+    lib = _load()
+    z = np.ascontiguousarray(z, dtype=np.complex64)
+    if z.ndim < 2 or coils < 1 or z.shape[0] % coils:
+        raise ValueError("z must be [images * coils, n0, n1]")
+    images = z.shape[0] // coils
+    npts = int(np.prod(z.shape[1:]))
+    out = np.empty((images,) + z.shape[1:], np.float32)
+    lib.oracle_rss(_ptr(z), _ptr(out), images, int(coils), npts)
+    return out
 
 
 def fft2d_exact(x: np.ndarray, op: str = "forward") -> np.ndarray:

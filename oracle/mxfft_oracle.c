@@ -19,6 +19,7 @@
  *     1/N^2 outside); round trip = (1/(n0 n1)) F^-1{F{x}} (Eq. 1).
  *   - An FP64 "exact" mode with the same dataflow and no quantisation, used only
  *     to pin the dataflow (bit reversal, stage indexing, twiddles) to a DFT.
+ *   - The root-sum-of-squares coil combine of Eq. (1) (oracle_rss).
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   C1 k1 uses round-to-nearest; target and tau_min are powers of two.
@@ -605,6 +606,34 @@ int oracle_fft2d_exact(const double *in, double *out, int batch, int n0, int n1,
     free(tmp);
     free(col);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. (1): root-sum-of-squares coil combine.                                 */
+/* ------------------------------------------------------------------------- */
+
+/* x_RSS = (sum over coils c of |T_c|^2)^(1/2) per point.  z holds images * coils
+ * slices of npts interleaved complex points, slice i * coils + c being coil c
+ * of image i; out[i * npts + p] (FP32).  Coils are added in the order
+ * c = 0, 1, ...: acc = fl(acc + fl(fl(re*re) + fl(im*im))), then one correctly
+ * rounded square root. */
+void oracle_rss(const float *z, float *out, long images, int coils, long npts)
+{
+    long i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < images; i++) {
+        for (long p = 0; p < npts; p++) {
+            float acc = 0.0f;
+            for (int c = 0; c < coils; c++) {
+                const float *v = z + 2 * (((long)i * coils + c) * npts + p);
+                float re2 = v[0] * v[0];
+                float im2 = v[1] * v[1];
+                float m2 = re2 + im2;
+                acc = acc + m2;
+            }
+            out[i * npts + p] = sqrtf(acc);
+        }
+    }
 }
 
 int oracle_num_threads(void)

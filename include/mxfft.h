@@ -225,6 +225,10 @@ typedef struct {
     int slices;
     const void *in;
     void *out;
+    int coils;       /* with rss: coil images per RSS image (slices a multiple of it) */
+    int reserved;    /* 0 */
+    void *rss;       /* optional device float [slices / coils][n0][n1], 16-byte aligned:
+                        mxfft_rss of out after the transform; NULL: none */
 } mxfft_item;
 
 typedef struct mxfft_engine_s *mxfft_engine_t;
@@ -289,8 +293,13 @@ int mxfft_tune_clear(void);
 typedef struct {
     int n0, n1, format, k, op, slices;   /* as in mxfft_item */
     const void *host_in;                 /* [slices][n0][n1] complex64; pinned for overlap */
-    void *host_out;                      /* same size; written when the request completes */
+    void *host_out;                      /* same size, written when the request completes;
+                                            may be NULL when host_rss is given */
     uint64_t tag;                        /* returned in the completion */
+    int coils;                           /* with host_rss: coil images per RSS image */
+    int reserved;                        /* 0 */
+    void *host_rss;                      /* optional float [slices / coils][n0][n1]: the
+                                            RSS images of the result (Eq. (1)); NULL: none */
 } mxfft_request;
 
 typedef struct {
@@ -333,6 +342,17 @@ int mxfft_server_poll(mxfft_server_t s, mxfft_completion *out, int max, int *n_o
 int mxfft_server_wait(mxfft_server_t s, double timeout_s);
 int mxfft_server_stats(mxfft_server_t s, uint64_t *batches, uint64_t *peak_bytes, uint64_t *budget);
 int mxfft_server_destroy(mxfft_server_t s);
+
+/*
+ * mxfft_rss -- root-sum-of-squares coil combine of Eq. (1) (Sec. 2.3):
+ *   out[i][p] = (sum over c of |z[i * coils + c][p]|^2)^(1/2), the coils of
+ *   image i being consecutive [n0][n1] complex64 slices of z; out is float
+ *   [images][n0][n1].  FP32, coils added in order c = 0, 1, ..., then one
+ *   correctly rounded square root.  z, out: device, 16-byte aligned, not
+ *   overlapping; n0 * n1 even.  Asynchronous on the stream; MXFFT_ERR_INVALID
+ *   for bad arguments.
+ */
+int mxfft_rss(const void *z, void *out, int images, int coils, int n0, int n1, void *stream);
 
 /* mxfft_status_string -- static description of a status code. */
 const char *mxfft_status_string(int status);

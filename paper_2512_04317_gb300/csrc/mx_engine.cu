@@ -46,11 +46,12 @@ struct Layout {
     std::vector<StatsRef> srefs;
     std::vector<int2> ctas;
     std::vector<PassLaunch> stage1, stage2;
+    std::vector<RssRef> rrefs;        // RSS outputs, in item order
     int nbranch1 = 0, nbranch2 = 0;
     int cta1 = 0, ncta1 = 0, cta2 = 0, ncta2 = 0;
     int nslices = 0;
     std::vector<char> rt;             // per slice: round trip
-    size_t off_srefs = 0, off_ctas = 0, bytes = 0;
+    size_t off_srefs = 0, off_ctas = 0, off_rss = 0, bytes = 0;
     std::string signature;
 };
 
@@ -124,14 +125,24 @@ int reserve(RunBuffers& b, const Layout& L) {
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const char* ca = (const char*)a;
+    const char* cb = (const char*)b;
+    return ca < cb + nb && cb < ca + na;
+}
+
 bool item_ok(const mxfft_item& it) {
-    if (it.slices < 0 || it.op < 0 || it.op > 2) return false;
+    if (it.slices < 0 || it.op < 0 || it.op > 2 || it.reserved != 0) return false;
     if (it.slices == 0) return true;
     if (!it.in || !it.out || ((uintptr_t)it.in & 15u) || ((uintptr_t)it.out & 15u)) return false;
     const size_t bytes = (size_t)it.slices * it.n0 * it.n1 * sizeof(float2);
-    const char* ci = (const char*)it.in;
-    const char* co = (const char*)it.out;
-    return ci == co || !(ci < co + bytes && co < ci + bytes);
+    if (it.in != it.out && overlap(it.in, bytes, it.out, bytes)) return false;
+    if (it.rss) {
+        if (it.coils < 1 || it.slices % it.coils || ((uintptr_t)it.rss & 15u)) return false;
+        const size_t rb = (size_t)(it.slices / it.coils) * it.n0 * it.n1 * sizeof(float);
+        if (overlap(it.rss, rb, it.in, bytes) || overlap(it.rss, rb, it.out, bytes)) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -181,9 +192,9 @@ int build_layout(mxfft_engine_s* e, const mxfft_item* items, int n, Layout& L,
         if (items[i].slices == 0) continue;
         int rc = get_plan(e, items[i], &item_plan[i]);
         if (rc) return rc;
-        char b[96];
-        std::snprintf(b, sizeof b, "%d,%d,%d,%d,%d,%d;", items[i].n0, items[i].n1, items[i].format,
-                      items[i].k, items[i].op, items[i].slices);
+        char b[128];
+        std::snprintf(b, sizeof b, "%d,%d,%d,%d,%d,%d,%d;", items[i].n0, items[i].n1, items[i].format,
+                      items[i].k, items[i].op, items[i].slices, items[i].rss ? items[i].coils : 0);
         sig += b;
         L.nslices += items[i].slices;
     }
@@ -191,7 +202,7 @@ int build_layout(mxfft_engine_s* e, const mxfft_item* items, int n, Layout& L,
     // table sizes: per slice two pass references (rows, columns) and a
     // statistics reference with its CTAs; round trips add one reference for
     // the inverse passes and a second statistics reference
-    size_t refs = 0, srefs = 0, ctas = 0;
+    size_t refs = 0, srefs = 0, ctas = 0, rss = 0;
     for (int i = 0; i < n; i++) {
         const size_t sl = (size_t)items[i].slices;
         const size_t c = ((size_t)items[i].n0 * items[i].n1 + kStatsPtsPerCta - 1) / kStatsPtsPerCta;
@@ -199,10 +210,12 @@ int build_layout(mxfft_engine_s* e, const mxfft_item* items, int n, Layout& L,
         refs += sl * (2 + rt);
         srefs += sl * (1 + rt);
         ctas += sl * c * (1 + rt);
+        rss += (sl > 0 && items[i].rss) ? 1 : 0;
     }
     L.off_srefs = align16(refs * sizeof(SliceRef));
     L.off_ctas = align16(L.off_srefs + srefs * sizeof(StatsRef));
-    L.bytes = align16(L.off_ctas + ctas * sizeof(int2));
+    L.off_rss = align16(L.off_ctas + ctas * sizeof(int2));
+    L.bytes = align16(L.off_rss + rss * sizeof(RssRef));
     return MXFFT_OK;
 }
 
@@ -295,9 +308,17 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         L.stage2.push_back(PassLaunch{p, 0, 1, PRO_NONE, EPI_RT_FINAL, r0, count, (int)gi});
     }
     L.nbranch2 = (int)rt_plans.size();
+    // root-sum-of-squares outputs of the items that ask for them
+    L.rrefs.clear();
+    for (int i = 0; i < n; i++)
+        if (items[i].slices > 0 && items[i].rss)
+            L.rrefs.push_back(RssRef{(const float2*)items[i].out, (float*)items[i].rss, items[i].coils,
+                                     items[i].slices / items[i].coils,
+                                     (long long)items[i].n0 * items[i].n1});
     L.off_srefs = align16(L.refs.size() * sizeof(SliceRef));
     L.off_ctas = align16(L.off_srefs + L.srefs.size() * sizeof(StatsRef));
-    L.bytes = align16(L.off_ctas + L.ctas.size() * sizeof(int2));
+    L.off_rss = align16(L.off_ctas + L.ctas.size() * sizeof(int2));
+    L.bytes = align16(L.off_rss + L.rrefs.size() * sizeof(RssRef));
 }
 
 void pack(const Layout& L, char* dst) {
@@ -305,6 +326,7 @@ void pack(const Layout& L, char* dst) {
     std::memcpy(dst, L.refs.data(), L.refs.size() * sizeof(SliceRef));
     std::memcpy(dst + L.off_srefs, L.srefs.data(), L.srefs.size() * sizeof(StatsRef));
     std::memcpy(dst + L.off_ctas, L.ctas.data(), L.ctas.size() * sizeof(int2));
+    std::memcpy(dst + L.off_rss, L.rrefs.data(), L.rrefs.size() * sizeof(RssRef));
 }
 
 cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, int nbranch,
@@ -357,6 +379,9 @@ cudaError_t enqueue(mxfft_engine_s* e, const Layout& L, RunBuffers& b, cudaStrea
     if (err == cudaSuccess) err = run_stage(e, L.stage1, L.nbranch1, d_refs, s, ev);
     if (err == cudaSuccess && L.ncta2 > 0) err = launch_stats_ref(d_srefs, d_ctas + L.cta2, L.ncta2, s);
     if (err == cudaSuccess) err = run_stage(e, L.stage2, L.nbranch2, d_refs, s, ev);
+    const RssRef* d_rss = (const RssRef*)(d + L.off_rss);
+    for (size_t j = 0; j < L.rrefs.size() && err == cudaSuccess; j++)
+        err = launch_rss(L.rrefs[j], d_rss + j, L.rrefs[j].images, L.rrefs[j].npts, s);
     return err;
 }
 

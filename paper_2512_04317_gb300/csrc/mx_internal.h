@@ -125,6 +125,20 @@ cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s);
 bool fast_pass_supported(const PassArgs& a);
 cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                              cudaStream_t s);
+// The root-sum-of-squares coil combine of one item: images x coils consecutive
+// complex slices of npts points -> images real slices (mx_rss.cu).
+struct RssRef {
+    const float2* z;
+    float* out;
+    int coils;
+    int images;
+    long long npts;
+};
+// With dev non-null the kernel reads the item from device memory (so that a
+// captured graph follows table updates); else it uses val.
+cudaError_t launch_rss(const RssRef& val, const RssRef* dev, long long images, long long npts,
+                       cudaStream_t s);
+
 // Groups of TG transforms per CTA of the register-resident pass: valid values
 // for (n, other), the tuned value for a launch (0 if none), and the table the
 // autotuner fills (mx_tune.cu).

@@ -32,7 +32,8 @@ double now_us() {
 
 struct SReq {
     mxfft_request r;
-    size_t bytes;
+    size_t bytes;          // complex data on the device
+    size_t rss_bytes;      // RSS images on the device
     double t_submit, t_admit;
 };
 
@@ -117,12 +118,17 @@ int launch_batch(mxfft_server_s* S, int i) {
         sl.status = cuda_status(err);
         return 0;
     }
+    // layout of the batch buffer: each request's data, then its RSS images
     std::vector<mxfft_item> items;
+    std::vector<size_t> offs;
     size_t off = 0;
     for (const SReq& q : sl.reqs) {
         if (err == cudaSuccess) err = cudaMemcpyAsync(d + off, q.r.host_in, q.bytes, cudaMemcpyHostToDevice, s);
-        items.push_back(mxfft_item{q.r.n0, q.r.n1, q.r.format, q.r.k, q.r.op, q.r.slices, d + off, d + off});
-        off += q.bytes;
+        void* rss = q.rss_bytes ? d + off + q.bytes : nullptr;
+        items.push_back(mxfft_item{q.r.n0, q.r.n1, q.r.format, q.r.k, q.r.op, q.r.slices, d + off, d + off,
+                                   q.r.coils, 0, rss});
+        offs.push_back(off);
+        off += q.bytes + q.rss_bytes;
     }
     int rc = err == cudaSuccess ? MXFFT_OK : cuda_status(err);
     if (rc == MXFFT_OK) rc = mxfft_engine_run(sl.eng, items.data(), (int)items.size(), s);
@@ -130,14 +136,15 @@ int launch_batch(mxfft_server_s* S, int i) {
     sl.status = rc;
     if (rc != MXFFT_OK) std::fill(sl.h_flags, sl.h_flags + slices, 0u);
     sl.ctx.assign(sl.reqs.size(), DoneCtx{S, i, 0});
-    off = 0;
     int queued = 0;
     for (size_t j = 0; j < sl.reqs.size(); j++) {
         const SReq& q = sl.reqs[j];
-        if (rc == MXFFT_OK)
-            rc = cuda_status(cudaMemcpyAsync(q.r.host_out, d + off, q.bytes, cudaMemcpyDeviceToHost, s));
+        if (rc == MXFFT_OK && q.r.host_out)
+            rc = cuda_status(cudaMemcpyAsync(q.r.host_out, d + offs[j], q.bytes, cudaMemcpyDeviceToHost, s));
+        if (rc == MXFFT_OK && q.rss_bytes)
+            rc = cuda_status(cudaMemcpyAsync(q.r.host_rss, d + offs[j] + q.bytes, q.rss_bytes,
+                                             cudaMemcpyDeviceToHost, s));
         if (rc != MXFFT_OK) sl.status = rc;
-        off += q.bytes;
         sl.ctx[j].req = (int)j;
         if (cudaLaunchHostFunc(s, request_done, &sl.ctx[j]) != cudaSuccess) break;
         queued++;
@@ -188,7 +195,8 @@ void worker_main(mxfft_server_s* S) {
             const size_t max_bytes = S->cfg.max_batch_bytes ? (size_t)S->cfg.max_batch_bytes : SIZE_MAX;
             while (!S->pending.empty()) {
                 SReq q = S->pending.front();
-                if (q.bytes > S->budget) {
+                const size_t qb = q.bytes + q.rss_bytes;
+                if (qb > S->budget) {
                     // can never be admitted
                     S->pending.pop_front();
                     S->done.push_back(mxfft_completion{q.r.tag, MXFFT_ERR_NOMEM, 0, q.t_submit, ta, ta});
@@ -196,13 +204,13 @@ void worker_main(mxfft_server_s* S) {
                     S->cv_done.notify_all();
                     continue;
                 }
-                if (S->inflight + bytes + q.bytes > S->budget) break;
+                if (S->inflight + bytes + qb > S->budget) break;
                 if (!batch.empty() &&
-                    (slices + q.r.slices > S->cfg.max_batch_slices || bytes + q.bytes > max_bytes))
+                    (slices + q.r.slices > S->cfg.max_batch_slices || bytes + qb > max_bytes))
                     break;
                 q.t_admit = ta;
                 batch.push_back(q);
-                bytes += q.bytes;
+                bytes += qb;
                 slices += q.r.slices;
                 S->pending.pop_front();
             }
@@ -282,11 +290,15 @@ int mxfft_server_create(const mxfft_server_config* cfg, mxfft_server_t* out) {
 int mxfft_server_submit(mxfft_server_t S, const mxfft_request* r) {
     if (!S || !r) return MXFFT_ERR_INVALID;
     if (!pow2_in(r->n0, 2, 2048) || !pow2_in(r->n1, 2, 2048) || r->format < 0 || r->format > 4 ||
-        !pow2_in(r->k, 2, 128) || r->op < 0 || r->op > 2 || r->slices < 1 || !r->host_in || !r->host_out)
+        !pow2_in(r->k, 2, 128) || r->op < 0 || r->op > 2 || r->slices < 1 || !r->host_in ||
+        r->reserved != 0 || (!r->host_out && !r->host_rss))
         return MXFFT_ERR_INVALID;
+    if (r->host_rss && (r->coils < 1 || r->slices % r->coils)) return MXFFT_ERR_INVALID;
     SReq q;
     q.r = *r;
     q.bytes = (size_t)r->slices * r->n0 * r->n1 * sizeof(float2);
+    // (a multiple of 16 bytes: n0 n1 >= 4 points of 4 bytes)
+    q.rss_bytes = r->host_rss ? (size_t)(r->slices / r->coils) * r->n0 * r->n1 * sizeof(float) : 0;
     q.t_submit = now_us();
     q.t_admit = 0.0;
     std::lock_guard<std::mutex> lk(S->mu);

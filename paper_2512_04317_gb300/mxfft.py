@@ -35,14 +35,15 @@ EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
            "mxfft_engine_destroy", "mxfft_tune", "mxfft_tune_save", "mxfft_tune_load",
            "mxfft_tune_clear", "mxfft_server_create", "mxfft_server_submit",
            "mxfft_server_poll", "mxfft_server_wait", "mxfft_server_stats",
-           "mxfft_server_destroy", "mxfft_status_string")
+           "mxfft_server_destroy", "mxfft_rss", "mxfft_status_string")
 
 
 class Item(ctypes.Structure):
     """mxfft_item"""
     _fields_ = [("n0", ctypes.c_int), ("n1", ctypes.c_int), ("format", ctypes.c_int),
                 ("k", ctypes.c_int), ("op", ctypes.c_int), ("slices", ctypes.c_int),
-                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("coils", ctypes.c_int), ("reserved", ctypes.c_int), ("rss", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -50,7 +51,8 @@ class Request(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int), ("n1", ctypes.c_int), ("format", ctypes.c_int),
                 ("k", ctypes.c_int), ("op", ctypes.c_int), ("slices", ctypes.c_int),
                 ("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p),
-                ("tag", ctypes.c_uint64)]
+                ("tag", ctypes.c_uint64), ("coils", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("host_rss", ctypes.c_void_p)]
 
 
 class Completion(ctypes.Structure):
@@ -116,6 +118,7 @@ def load(path: str | None = None):
         lib.mxfft_server_wait.argtypes = [P, D]
         lib.mxfft_server_stats.argtypes = [P, P, P, P]
         lib.mxfft_server_destroy.argtypes = [P]
+        lib.mxfft_rss.argtypes = [P, P, I, I, I, I, P]
         lib.mxfft_status_string.argtypes = [I]
         lib.mxfft_status_string.restype = ctypes.c_char_p
         for name in EXPORTS[:-1]:
@@ -250,6 +253,28 @@ def mxfft_engine_get_status(engine, k_count: int = 0):
 def mxfft_engine_destroy(engine) -> None:
     if engine:
         load().mxfft_engine_destroy(engine)
+
+
+# ---- root-sum-of-squares coil combine (Eq. (1)) -------------------------------------
+
+def mxfft_rss(z_ptr, out_ptr, images, coils, n0, n1, stream=None) -> None:
+    _check(load().mxfft_rss(z_ptr, out_ptr, int(images), int(coils), int(n0), int(n1), stream),
+           "mxfft_rss")
+
+
+def rss(z, coils: int, out=None):
+    """RSS images float32 [images, n0, n1] of z complex64 CUDA [images * coils, n0, n1]."""
+    import torch
+    _check_tensor(z, "z")
+    if not z.is_cuda or z.shape[0] % coils:
+        raise ValueError("z must be a CUDA tensor [images * coils, n0, n1]")
+    images = z.shape[0] // coils
+    n0, n1 = z.shape[-2], z.shape[-1]
+    if out is None:
+        out = torch.empty((images, n0, n1), dtype=torch.float32, device=z.device)
+    mxfft_rss(z.data_ptr(), out.data_ptr(), images, coils, n0, n1,
+              torch.cuda.current_stream(z.device).cuda_stream)
+    return out
 
 
 # ---- autotuner -------------------------------------------------------------------
@@ -409,10 +434,14 @@ class Engine:
         self._slices = 0
 
     def run(self, work, stream=None):
+        """work: (op, x, out, fmt, k) or (op, x, out, fmt, k, rss, coils) tuples; rss is a
+        float32 CUDA tensor [slices / coils, n0, n1] receiving the RSS images of out."""
         import torch
         items = []
         dev = None
-        for op, x, out, fmt, k in work:
+        for w in work:
+            op, x, out, fmt, k = w[:5]
+            rss_t, coils = (w[5], int(w[6])) if len(w) > 5 else (None, 0)
             _check_tensor(x, "x")
             _check_tensor(out, "out")
             if not x.is_cuda or out.shape != x.shape:
@@ -420,7 +449,8 @@ class Engine:
             dev = x.device
             n0, n1 = x.shape[-2], x.shape[-1]
             items.append(Item(n0, n1, _fmt(fmt), int(k), _op(op), x.numel() // (n0 * n1),
-                              x.data_ptr(), out.data_ptr()))
+                              x.data_ptr(), out.data_ptr(), coils, 0,
+                              rss_t.data_ptr() if rss_t is not None else None))
         if stream is None and dev is not None:
             stream = torch.cuda.current_stream(dev).cuda_stream
         mxfft_engine_run(self.handle, items, stream)
@@ -461,15 +491,23 @@ class Server:
                                           max_batch_bytes)
         self._keep = {}
 
-    def submit(self, tag: int, x, out, fmt="e4m3", k: int = 32, op="forward") -> None:
+    def submit(self, tag: int, x, out, fmt="e4m3", k: int = 32, op="forward", rss=None,
+               coils: int = 1) -> None:
+        """out: host tensor like x, or None when rss (float32 host [slices / coils, n0, n1])
+        receives the RSS images of the result."""
         _check_tensor(x, "x")
-        _check_tensor(out, "out")
-        if x.is_cuda or out.is_cuda or out.shape != x.shape:
-            raise ValueError("host tensors of equal shape expected")
+        if out is not None:
+            _check_tensor(out, "out")
+            if out.is_cuda or out.shape != x.shape:
+                raise ValueError("out: a host tensor like x")
+        if x.is_cuda or (out is None and rss is None):
+            raise ValueError("host tensors expected, and out or rss")
         n0, n1 = x.shape[-2], x.shape[-1]
         req = Request(n0, n1, _fmt(fmt), int(k), _op(op), x.numel() // (n0 * n1), x.data_ptr(),
-                      out.data_ptr(), int(tag))
-        self._keep[int(tag)] = (x, out)
+                      out.data_ptr() if out is not None else None, int(tag),
+                      int(coils) if rss is not None else 0, 0,
+                      rss.data_ptr() if rss is not None else None)
+        self._keep[int(tag)] = (x, out, rss)
         mxfft_server_submit(self.handle, req)
 
     def poll(self, max_n: int = 1024):

@@ -37,8 +37,10 @@ def test_engine_and_server_argument_checks(lib):
 
 def test_item_and_request_layouts_match_the_header():
     # field offsets of the C structs (x86-64 and aarch64 LP64)
-    assert ctypes.sizeof(mxfft.Item) == 40 and mxfft.Item.in_.offset == 24
-    assert ctypes.sizeof(mxfft.Request) == 48 and mxfft.Request.tag.offset == 40
+    assert ctypes.sizeof(mxfft.Item) == 56 and mxfft.Item.in_.offset == 24
+    assert mxfft.Item.rss.offset == 48
+    assert ctypes.sizeof(mxfft.Request) == 64 and mxfft.Request.tag.offset == 40
+    assert mxfft.Request.host_rss.offset == 56
     assert ctypes.sizeof(mxfft.Completion) == 40 and mxfft.Completion.t_done_us.offset == 32
     assert ctypes.sizeof(mxfft.ServerConfig) == 40 and mxfft.ServerConfig.tau.offset == 16
     assert mxfft.ServerConfig.max_batch_bytes.offset == 32
@@ -83,3 +85,14 @@ def test_tuning_file_rejects_malformed(lib, tmp_path, bad):
     assert ei.value.status == mxfft.MXFFT_ERR_INVALID
     with pytest.raises(mxfft.MxfftError):
         mxfft.mxfft_tune_load(str(tmp_path / "missing.json"))
+
+
+def test_rss_argument_checks(lib):
+    bad = [(-1, 1, 4, 4), (1, 0, 4, 4), (1, 1, 0, 4)]
+    for images, coils, n0, n1 in bad:
+        assert lib.mxfft_rss(None, None, images, coils, n0, n1, None) == mxfft.MXFFT_ERR_INVALID
+    assert lib.mxfft_rss(None, None, 1, 1, 4, 4, None) == mxfft.MXFFT_ERR_INVALID   # null
+    # z occupies [16, 144), out [64, 128): overlapping
+    assert lib.mxfft_rss(16, 64, 1, 1, 4, 4, None) == mxfft.MXFFT_ERR_INVALID       # overlap
+    assert lib.mxfft_rss(8, 65536, 1, 1, 4, 4, None) == mxfft.MXFFT_ERR_INVALID     # alignment
+    assert lib.mxfft_rss(None, None, 0, 1, 4, 4, None) == mxfft.MXFFT_OK            # nothing

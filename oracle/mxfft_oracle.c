@@ -20,6 +20,8 @@
  *   - An FP64 "exact" mode with the same dataflow and no quantisation, used only
  *     to pin the dataflow (bit reversal, stage indexing, twiddles) to a DFT.
  *   - The root-sum-of-squares coil combine of Eq. (1) (oracle_rss).
+ *   - The FP16 positive control of Sec. 2.2 (format code 5): the same dataflow
+ *     with binary16 inputs and outputs and binary16 twiddle products.
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   C1 k1 uses round-to-nearest; target and tau_min are powers of two.
@@ -38,6 +40,11 @@
  *   C10 twiddles are exact FP64 values exp(-+ 2 pi i j / (2h)), quantised
  *       directly from FP64.
  *   C15 signed zeros and subnormals are kept (IEEE); no FMA contraction.
+ *   C16 the FP16 control keeps Alg. 1's prescale and the radix-2 dataflow;
+ *       each transform's input is rounded to binary16 after the prescale and
+ *       its output after the unscale; in each butterfly the twiddle (rounded
+ *       from FP64) and v are binary16, the complex product is formed with
+ *       binary16 operations (each rounded once), u +- wv stays FP32.
  *
  * Floating-point contract: compile with -ffp-contract=off and without
  * fast-math.  Every FP32 result below is one IEEE operation on FP32 operands.
@@ -61,6 +68,7 @@ typedef struct {
     int emax;       /* unbiased exponent of the largest normal */
     int emin;       /* unbiased exponent of the smallest normal: 1 - bias */
     double maxnorm; /* largest finite magnitude */
+    int fp16;       /* 1: the FP16 positive control, not an MX element format */
 } elem_fmt;
 
 /* Format codes shared with the Python wrapper: 0 E4M3, 1 E5M2, 2 E2M3,
@@ -85,10 +93,31 @@ static int get_fmt(int code, elem_fmt *f)
             f->maxnorm = ldexp(1.0 + 3.0 / 4.0, f->emax); break;
     case 4: f->ebits = 2; f->mbits = 1; f->bias = 1;  f->emax = 3 - 1;
             f->maxnorm = ldexp(1.0 + 1.0 / 2.0, f->emax); break;
+    case 5: f->ebits = 5; f->mbits = 10; f->bias = 15; f->emax = 30 - 15;   /* IEEE binary16 */
+            f->maxnorm = ldexp(2.0 - 1.0 / 1024.0, f->emax); break;
     default: return -1;
     }
     f->emin = 1 - f->bias;
+    f->fp16 = code == 5;
     return 0;
+}
+
+/* IEEE 754 binary16 rounding, for the FP16 positive control (Sec. 2.2): round
+ * to nearest with ties to even, subnormals below 2^-14 (spacing 2^-24), and
+ * overflow to infinity from 65520 up: the midpoint between the largest finite
+ * value 65504 (odd significand) and 2^16 rounds up to even, i.e. to infinity.
+ * NaN stays NaN, zero keeps its sign. */
+static double q_fp16(double x)
+{
+    if (x != x || x == 0.0) return x;
+    double a = fabs(x);
+    if (a >= 65520.0) return copysign(INFINITY, x);
+    int ex;
+    frexp(a, &ex);              /* a = m 2^ex, m in [0.5, 1) */
+    int e = ex - 1;             /* floor(log2 a) */
+    if (e < -14) e = -14;
+    double q = ldexp(1.0, e - 10);
+    return copysign(rint(a / q) * q, x);
 }
 
 /* Round x to the nearest value of the element grid, ties to the even code,
@@ -283,6 +312,27 @@ static void ws_free(fft_ws *w)
     free(w->Wr); free(w->Wi); free(w->tmp);
 }
 
+/* FP16 positive control (Sec. 2.2): the twiddle product of each butterfly in
+ * IEEE binary16 arithmetic -- the twiddle rounded to binary16 from FP64, v
+ * rounded to binary16, every product, sum and difference rounded once to
+ * binary16 (its exact value is formed in FP64, which holds any product, sum or
+ * difference of two binary16 values exactly) -- then u +- wv in FP32. */
+static void fp16_butterflies(int nb, const float *U, const float *V, const double *Wr,
+                             const double *Wi, float *Y0, float *Y1)
+{
+    for (int b = 0; b < nb; b++) {
+        double wr = q_fp16(Wr[b]), wi = q_fp16(Wi[b]);
+        double vr = q_fp16(V[2 * b]), vi = q_fp16(V[2 * b + 1]);
+        double pr = q_fp16(q_fp16(wr * vr) - q_fp16(wi * vi));
+        double pi = q_fp16(q_fp16(wr * vi) + q_fp16(wi * vr));
+        float fr = (float)pr, fi = (float)pi;   /* exact */
+        Y0[2 * b] = U[2 * b] + fr;
+        Y0[2 * b + 1] = U[2 * b + 1] + fi;
+        Y1[2 * b] = U[2 * b] - fr;
+        Y1[2 * b + 1] = U[2 * b + 1] - fi;
+    }
+}
+
 /* A: n complex values (interleaved FP32), transformed in place. */
 static void fft1d_mx(float *A, int n, int kblk, int inverse, const elem_fmt *f,
                      const bf_opts *o, fft_ws *ws)
@@ -312,11 +362,15 @@ static void fft1d_mx(float *A, int n, int kblk, int inverse, const elem_fmt *f,
             ws->Wr[b] = cos(ang);
             ws->Wi[b] = sgn * sin(ang);
         }
-        for (int beta = 0; beta < nbf / m; beta++) {
-            int b0 = beta * m;
-            mx_butterfly_block(m, ws->U + 2 * b0, ws->V + 2 * b0, ws->Wr + b0,
-                               ws->Wi + b0, ws->Y0 + 2 * b0, ws->Y1 + 2 * b0,
-                               f, o, ws->scr);
+        if (f->fp16) {
+            fp16_butterflies(nbf, ws->U, ws->V, ws->Wr, ws->Wi, ws->Y0, ws->Y1);
+        } else {
+            for (int beta = 0; beta < nbf / m; beta++) {
+                int b0 = beta * m;
+                mx_butterfly_block(m, ws->U + 2 * b0, ws->V + 2 * b0, ws->Wr + b0,
+                                   ws->Wi + b0, ws->Y0 + 2 * b0, ws->Y1 + 2 * b0,
+                                   f, o, ws->scr);
+            }
         }
         for (int b = 0; b < nbf; b++) {
             int g = b / h, j = b % h;
@@ -451,19 +505,25 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
         int nf = 0, k;
         int inv0 = (op == 1);
         /* first transform: forward (op 0, 2) or inverse (op 1) */
+        /* the FP16 control rounds each transform's input (after the
+         * prescale) and output (after the unscale) to binary16 */
+        const int q16 = f.fp16;
         k = prescale_k(S, npts, &pp, &nf, mag);
         int flag = nf;
         for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], k);
+        if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
         transform_slice(S, n0, n1, kblk, inv0, &f, &o, &ws);
         if (op == 2) {
             if (k_out) k_out[2 * s] = k;
             /* forward output y = ldexp(A, -k), then the inverse with its own
              * prescale, and one combined scaling by 2^(-k_inv - log2(n0 n1)) */
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k);
+            if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             int nf2 = 0;
             int kinv = prescale_k(S, npts, &pp, &nf2, mag);
             flag |= nf2;
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], kinv);
+            if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             transform_slice(S, n0, n1, kblk, 1, &f, &o, &ws);
             int lg = ilog2i(n0) + ilog2i(n1);
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -kinv - lg);
@@ -472,6 +532,7 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k);
             if (k_out) k_out[s] = k;
         }
+        if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
         if (flags_out) flags_out[s] = flag;
         memcpy(out + 2 * npts * s, S, sizeof(float) * 2 * npts);
         ws_free(&ws);
@@ -506,7 +567,8 @@ int oracle_quantize(const float *in, float *out, long count, int fmt)
 {
     elem_fmt f;
     if (get_fmt(fmt, &f)) return -1;
-    for (long i = 0; i < count; i++) out[i] = (float)q_elem((double)in[i], &f);
+    for (long i = 0; i < count; i++)
+        out[i] = (float)(f.fp16 ? q_fp16((double)in[i]) : q_elem((double)in[i], &f));
     return 0;
 }
 
@@ -515,7 +577,7 @@ int oracle_quantize_f64(const double *in, double *out, long count, int fmt)
 {
     elem_fmt f;
     if (get_fmt(fmt, &f)) return -1;
-    for (long i = 0; i < count; i++) out[i] = q_elem(in[i], &f);
+    for (long i = 0; i < count; i++) out[i] = (f.fp16 ? q_fp16(in[i]) : q_elem(in[i], &f));
     return 0;
 }
 
@@ -526,6 +588,10 @@ int oracle_butterfly_block(int nb, const float *u, const float *v,
 {
     elem_fmt f;
     if (get_fmt(fmt, &f) || nb < 1) return -1;
+    if (f.fp16) {
+        fp16_butterflies(nb, u, v, wre, wim, y0, y1);
+        return 0;
+    }
     bf_opts o = {renorm, direct_enc};
     float *scr = malloc(sizeof(float) * 6 * nb);
     mx_butterfly_block(nb, u, v, wre, wim, y0, y1, &f, &o, scr);

@@ -46,19 +46,30 @@ typedef enum {
     MXFFT_ERR_TIMEOUT = 6       /* a bounded device wait gave up */
 } mxfft_status;
 
-/* Element formats of the MX blocks (OCP 8-bit FP and OCP MX v1.0 types). */
+/* Element formats of the MX blocks (OCP 8-bit FP and OCP MX v1.0 types), and
+ * the FP16 positive control. */
 typedef enum {
     MXFFT_E4M3 = 0,   /* FP8, 3 mantissa bits, largest normal 448 */
     MXFFT_E5M2 = 1,   /* FP8, 2 mantissa bits, largest normal 57344 */
     MXFFT_E2M3 = 2,   /* FP6, 3 mantissa bits, largest normal 7.5 */
     MXFFT_E3M2 = 3,   /* FP6, 2 mantissa bits, largest normal 28 */
-    MXFFT_E2M1 = 4    /* FP4, 1 mantissa bit, largest normal 6 */
+    MXFFT_E2M1 = 4,   /* FP4, 1 mantissa bit, largest normal 6 */
+    MXFFT_FP16 = 5    /* the FP16 positive control of Sec. 2.2, not an MX format: the same
+                         prescale and radix-2 dataflow, each transform's input (after the
+                         prescale) and output (before the exact unscale) rounded to IEEE
+                         binary16 -- the control runs in the prescaled domain --
+                         each butterfly's twiddle product formed in binary16 arithmetic
+                         (twiddle and v in binary16, every operation rounded once), u +- wv
+                         in FP32.  k is ignored; tau_min default 2^-24 (binary16's smallest
+                         magnitude), so the prescale sets the peak to the target and stage
+                         values stay below n0 n1 target (no overflow up to 256x256 at
+                         target 0.5); products overflow to infinity above 65504. */
 } mxfft_format;
 
 /* Keys of mxfft_set_option. */
 typedef enum {
     MXFFT_OPT_TAU_MIN = 0,  /* tail floor tau_min of Alg. 1; a power of two.
-                               Default 2^-10 (e4m3, FP6, FP4), 2^-12 (e5m2). */
+                               Default 2^-10 (e4m3, FP6, FP4), 2^-12 (e5m2), 2^-24 (FP16). */
     MXFFT_OPT_K_MIN = 1,    /* lower clip k_min of Alg. 1, integer in [-126, 126]; default -126 */
     MXFFT_OPT_K_MAX = 2,    /* upper clip k_max of Alg. 1, integer in [-126, 126]; default 126 */
     MXFFT_OPT_GENERIC = 3,  /* 1: run every pass on the generic shared-memory kernel instead of

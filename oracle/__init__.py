@@ -34,7 +34,7 @@ FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
 # tau_min defaults: 2^-10 for e4m3 and 2^-12 for e5m2 (Alg. 1 notes); 2^-10 for
 # the FP6/FP4 formats, where the paper gives none.
 TAU_MIN_DEFAULT = {"e4m3": 2.0**-10, "e5m2": 2.0**-12, "e2m3": 2.0**-10,
-                   "e3m2": 2.0**-10, "e2m1": 2.0**-10, "fp16": 2.0**-10}
+                   "e3m2": 2.0**-10, "e2m1": 2.0**-10, "fp16": 2.0**-24}
 OP = {"forward": 0, "inverse": 1, "roundtrip": 2}
 
 _lock = threading.Lock()

@@ -40,11 +40,15 @@
  *   C10 twiddles are exact FP64 values exp(-+ 2 pi i j / (2h)), quantised
  *       directly from FP64.
  *   C15 signed zeros and subnormals are kept (IEEE); no FMA contraction.
- *   C16 the FP16 control keeps Alg. 1's prescale and the radix-2 dataflow;
- *       each transform's input is rounded to binary16 after the prescale and
- *       its output after the unscale; in each butterfly the twiddle (rounded
- *       from FP64) and v are binary16, the complex product is formed with
- *       binary16 operations (each rounded once), u +- wv stays FP32.
+ *   C16 the FP16 control keeps Alg. 1's prescale (default tau_min 2^-24, the
+ *       smallest binary16 magnitude, so that the prescale sets the peak to the
+ *       target and stage values stay below n0 n1 target) and the radix-2
+ *       dataflow; each transform's input is rounded to binary16 after the
+ *       prescale and its output before the exact unscale (the control runs in
+ *       the prescaled domain, where outputs stay below n0 n1 target); in each
+ *       butterfly the
+ *       twiddle (rounded from FP64) and v are binary16, the complex product is
+ *       formed with binary16 operations (each rounded once), u +- wv stays FP32.
  *
  * Floating-point contract: compile with -ffp-contract=off and without
  * fast-math.  Every FP32 result below is one IEEE operation on FP32 operands.
@@ -506,7 +510,8 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
         int inv0 = (op == 1);
         /* first transform: forward (op 0, 2) or inverse (op 1) */
         /* the FP16 control rounds each transform's input (after the
-         * prescale) and output (after the unscale) to binary16 */
+         * prescale) and output (before the exact unscale) to binary16: it runs
+         * in the prescaled domain */
         const int q16 = f.fp16;
         k = prescale_k(S, npts, &pp, &nf, mag);
         int flag = nf;
@@ -517,8 +522,8 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
             if (k_out) k_out[2 * s] = k;
             /* forward output y = ldexp(A, -k), then the inverse with its own
              * prescale, and one combined scaling by 2^(-k_inv - log2(n0 n1)) */
-            for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k);
             if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
+            for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k);
             int nf2 = 0;
             int kinv = prescale_k(S, npts, &pp, &nf2, mag);
             flag |= nf2;
@@ -526,13 +531,14 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
             if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             transform_slice(S, n0, n1, kblk, 1, &f, &o, &ws);
             int lg = ilog2i(n0) + ilog2i(n1);
+            if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -kinv - lg);
             if (k_out) k_out[2 * s + 1] = kinv;
         } else {
+            if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k);
             if (k_out) k_out[s] = k;
         }
-        if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
         if (flags_out) flags_out[s] = flag;
         memcpy(out + 2 * npts * s, S, sizeof(float) * 2 * npts);
         ws_free(&ws);

@@ -26,7 +26,7 @@ bool fast_pass_supported(const PassArgs& a) {
     int TG, S, NG, threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
     const int logm = log2_exact(a.m);
-    return logm >= 0 && logm <= 4 && a.fp.mbits > 0 &&
+    return a.fmt <= 4 && logm >= 0 && logm <= 4 && a.fp.mbits > 0 &&
            fast::fast_geometry(a.n, other, &TG, &S, &NG, &threads);
 }
 

@@ -7,7 +7,10 @@
 // (two per lane: b and b + 32) of one transform; the butterflies of an MX
 // block (m consecutive b, m <= 64) therefore sit in aligned groups of lanes,
 // and the block maxima of Alg. 2 are reduced with xor shuffles.
+#include <cuda_fp16.h>
+
 #include "mx_device.cuh"
+#include "mxfft.h"
 
 namespace mxfft {
 
@@ -125,6 +128,35 @@ __device__ __forceinline__ void mx_butterfly_pair(float2* A, int b0, int nb, int
     }
 }
 
+// FP16 positive control (Sec. 2.2): the twiddle product in IEEE binary16
+// arithmetic -- twiddle (a binary16 value) and v rounded to binary16, each
+// product, sum and difference rounded once (__hmul_rn is never contracted into
+// an FMA) -- then u +- wv in FP32.
+__device__ __forceinline__ float2 fp16_product(float2 w, float2 v) {
+    const __half wr = __float2half_rn(w.x), wi = __float2half_rn(w.y);   // exact
+    const __half vr = __float2half_rn(v.x), vi = __float2half_rn(v.y);
+    const __half pr = __hsub(__hmul_rn(wr, vr), __hmul_rn(wi, vi));
+    const __half pi = __hadd(__hmul_rn(wr, vi), __hmul_rn(wi, vr));
+    return make_float2(__half2float(pr), __half2float(pi));
+}
+
+__device__ __forceinline__ void fp16_butterfly_pair(float2* A, int b0, int nb, int h,
+                                                    const float2* __restrict__ tw) {
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int b = b0 + 32 * r;
+        if (b >= nb) continue;
+        const int j = b & (h - 1);
+        const int iu = 2 * b - j, iv = iu + h;
+        const float2 u = A[iu];
+        const float2 p = fp16_product(__ldg(tw + (h - 1) + j), A[iv]);
+        A[iu] = make_float2(__fadd_rn(u.x, p.x), __fadd_rn(u.y, p.y));
+        A[iv] = make_float2(__fsub_rn(u.x, p.x), __fsub_rn(u.y, p.y));
+    }
+}
+
+__device__ __forceinline__ float to_fp16(float x) { return __half2float(__float2half_rn(x)); }
+
 __global__ void __launch_bounds__(kPassThreads)
 pass_kernel(PassArgs a) {
     extern __shared__ float2 sm[];
@@ -141,6 +173,7 @@ pass_kernel(PassArgs a) {
 
     // load (with the Alg. 1 prescale on the first pass) in bit-reversed order
     const float pre = a.prologue == PRO_PRESCALE ? exp2i(stp->k) : 1.0f;
+    const bool fp16 = a.fmt == MXFFT_FP16;
     const int total = tpc * n;
     for (int idx = tid; idx < total; idx += nthr) {
         int t, i;
@@ -158,6 +191,7 @@ pass_kernel(PassArgs a) {
         if (a.prologue == PRO_PRESCALE) {
             v.x = __fmul_rn(v.x, pre);
             v.y = __fmul_rn(v.y, pre);
+            if (fp16) { v.x = to_fp16(v.x); v.y = to_fp16(v.y); }   // input rounding
         }
         sm[t * n + (int)(__brev((unsigned)i) >> (32 - logn))] = v;
     }
@@ -171,7 +205,8 @@ pass_kernel(PassArgs a) {
         for (int task = warp; task < tasks; task += nwarps) {
             const int t = task / sb_per;
             const int sb = task - t * sb_per;
-            mx_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.m, a.tw, a.tws, a.fp);
+            if (fp16) fp16_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.tw);
+            else mx_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.m, a.tw, a.tws, a.fp);
         }
         __syncthreads();
     }
@@ -194,6 +229,9 @@ pass_kernel(PassArgs a) {
         }
         float2 v = sm[t * n + i];
         if (a.epilogue != EPI_RAW) {
+            // FP16 control: output rounding in the prescaled domain, then the
+            // exact unscale
+            if (fp16) { v.x = to_fp16(v.x); v.y = to_fp16(v.y); }
             v.x = __fmul_rn(v.x, post);
             v.y = __fmul_rn(v.y, post);
         }

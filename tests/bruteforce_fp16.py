@@ -61,16 +61,17 @@ def fft2d(x, k, inverse):
 
 def mxfft2d_fp16(x, k, op, k_inv=None):
     """x: complex64 [n0, n1]; k (and k_inv for the round trip) from Alg. 1."""
+    # outputs rounded to binary16 in the prescaled domain, then unscaled exactly
     inv0 = op == "inverse"
     re, im = fft2d(x, k, inv0)
+    re, im = h16(re).astype(np.float32), h16(im).astype(np.float32)
     re = np.ldexp(re, -k).astype(np.float32)
     im = np.ldexp(im, -k).astype(np.float32)
-    re, im = h16(re).astype(np.float32), h16(im).astype(np.float32)
     if op == "roundtrip":
         y = (re + 1j * im).astype(np.complex64)
         re, im = fft2d(y, k_inv, True)
         lg = (x.shape[0].bit_length() - 1) + (x.shape[1].bit_length() - 1)
+        re, im = h16(re).astype(np.float32), h16(im).astype(np.float32)
         re = np.ldexp(re, -k_inv - lg).astype(np.float32)
         im = np.ldexp(im, -k_inv - lg).astype(np.float32)
-        re, im = h16(re).astype(np.float32), h16(im).astype(np.float32)
     return (re + 1j * im).astype(np.complex64)

@@ -53,7 +53,8 @@ def test_closed_forms():
 
 
 def test_positive_control_accuracy():
-    ksp = phantom.mri_batch(128, 128, 2, 1, config_id=1)
+    # at 256 x 256 with the default tail floor no stage value can overflow
+    ksp = phantom.mri_batch(256, 256, 2, 1, config_id=1)
     ref = np.fft.fft2(ksp.astype(np.complex128))
     def nrmse(a):
         return np.linalg.norm(a - ref) / np.linalg.norm(ref)
@@ -78,3 +79,14 @@ def test_fp16_twiddles_are_far_from_rounding_ties():
                 continue
             worst = min(worst, abs(frac - 0.5))
     assert worst > 1e-9, worst
+
+
+def test_default_prescale_keeps_binary16_in_range():
+    # tau_min = 2^-24: k = k1, the peak lands on the target 0.5, and every
+    # output of a 256 x 256 forward stays finite
+    ksp = phantom.mri_batch(256, 256, 3, 2, config_id=2)
+    y, ks, _ = oracle.mxfft2d(ksp, "fp16", 32)
+    assert np.isfinite(y).all()
+    for s in range(ksp.shape[0]):
+        peak = np.abs(ksp[s]).max()
+        assert 0.25 < peak * 2.0 ** int(ks[s]) <= 0.5 * 2 ** 0.5

@@ -140,6 +140,23 @@ def source_digest(kernel, read=None):
     return h.hexdigest()[:16]
 
 
+def recorded_lane_instructions(kernel, workload):
+    """Executed lane instructions per point of a launch (ncu) of this kernel on
+    this workload, when taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    for ent in rec.get("entries", []):
+        if (ent.get("kernel") == kernel and ent.get("workload") == workload and
+                ent.get("source_digest") == source_digest(kernel) and
+                ent.get("lane_instructions_per_point_per_launch") is not None):
+            return float(ent["lane_instructions_per_point_per_launch"])
+    return None
+
+
 def recorded_traffic(kernel, workload, pts_per_launch):
     """DRAM bytes per launch from the committed ncu summary of this kernel on
     this workload, when it was taken on the current kernel sources; else None."""
@@ -581,29 +598,83 @@ def main():
                 "kernel_share": {k: v[0] / max(sum(x[0] for x in prof.values()), 1e-12)
                                  for k, v in prof.items()}}
     whole = pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (ms_per_step * 1e-3) / 1e9
+    # instruction-issue roofline of the same kernel: one warp instruction per
+    # scheduler and cycle, 4 schedulers of 32 lanes per SM, at the sampled clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    alu_peak = sms * 4 * 32 * mhz * 1e6 / 1e12
+    ipp = recorded_lane_instructions(dom, args.workload)
+    roofline_alu = None
+    if ipp is not None:
+        ach = ipp * pts / (avg_ms * 1e-3) / 1e12
+        roofline_alu = {"bound": "alu", "achieved": ach, "peak": alu_peak,
+                        "unit": "T lane-instructions/s", "frac": ach / alu_peak, "kernel": dom,
+                        "lane_instructions_per_point": ipp,
+                        "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz"}
 
     # ---- end to end through the public API with host buffers ------------------
     hk = torch.from_numpy(ksp_np).pin_memory()
     hi = torch.from_numpy(img_np).pin_memory()
     ok = torch.empty_like(hk).pin_memory()
     oi = torch.empty_like(hi).pin_memory()
-    e2e_steps = max(3, min(args.steps, 50))
-    for i in range(2):
-        xk.copy_(hk, non_blocking=True); xi.copy_(hi, non_blocking=True)
-        step()
-        ok.copy_(yk, non_blocking=True); oi.copy_(yi, non_blocking=True)
-    torch.cuda.synchronize()
+    e2e_steps = max(6, min(args.steps, 60))
+    e2e_mode = "one stream, steps in sequence"
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for i in range(e2e_steps):
-        xk.copy_(hk, non_blocking=True)
-        xi.copy_(hi, non_blocking=True)
-        step()
-        ok.copy_(yk, non_blocking=True)
-        oi.copy_(yi, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    if engine is not None:
+        # the way a caller streams batches through the executor: steps round-robin
+        # over 3 streams, each with its own device buffers and engine, so one
+        # step's copy in, another's transforms and a third's copy out overlap;
+        # every step still copies its inputs in and its results out
+        e2e_mode = "3 streams, one step in flight per stream"
+        lanes = []
+        for j in range(3):
+            b = {"xk": torch.empty_like(xk), "xi": torch.empty_like(xi), "yk": torch.empty_like(yk),
+                 "yi": torch.empty_like(yi), "ok": torch.empty_like(hk).pin_memory(),
+                 "oi": torch.empty_like(hi).pin_memory()}
+            lanes.append((torch.cuda.Stream(dev), mxfft.Engine(graphs=True, tc16=args.path == "tc16"), b))
+
+        def e2e_step(i):
+            st_, eng_j, b = lanes[i % len(lanes)]
+            with torch.cuda.stream(st_):
+                b["xk"].copy_(hk, non_blocking=True)
+                b["xi"].copy_(hi, non_blocking=True)
+                eng_j.run([("forward", b["xk"], b["yk"], w["fmt"], w["k"]),
+                           ("roundtrip", b["xi"], b["yi"], w["fmt"], w["k"])])
+                b["ok"].copy_(b["yk"], non_blocking=True)
+                b["oi"].copy_(b["yi"], non_blocking=True)
+        for i in range(2 * len(lanes)):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for st_, _, _ in lanes:
+            st_.wait_event(e0)
+        for i in range(e2e_steps):
+            e2e_step(i)
+        for st_, _, _ in lanes:
+            ev = torch.cuda.Event()
+            ev.record(st_)
+            stream.wait_event(ev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for _, eng_j, _ in lanes:
+            eng_j.close()
+    else:
+        for i in range(2):
+            xk.copy_(hk, non_blocking=True); xi.copy_(hi, non_blocking=True)
+            step()
+            ok.copy_(yk, non_blocking=True); oi.copy_(yi, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for i in range(e2e_steps):
+            xk.copy_(hk, non_blocking=True)
+            xi.copy_(hi, non_blocking=True)
+            step()
+            ok.copy_(yk, non_blocking=True)
+            oi.copy_(yi, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
     te_ms = job_time_ms(e0.elapsed_time(e1), world, dist, dev)
     e2e_value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, e2e_steps, te_ms)
     bytes_io = 2 * pts * 8
@@ -665,9 +736,10 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "hbm_roofline_frac_whole_step": whole / peak,
             "roofline": roofline,
+            "roofline_alu": roofline_alu,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Mpts/s", "h2d_bytes_per_step": bytes_io,
-                    "d2h_bytes_per_step": bytes_io},
+                    "d2h_bytes_per_step": bytes_io, "steps": e2e_steps, "mode": e2e_mode},
             "gpu_launches": launches_per_step * args.steps,
             "accuracy_vs_fp64": acc,
             "device_status": st,

@@ -77,8 +77,10 @@ typedef enum {
     MXFFT_OPT_PATH = 4      /* 0: radix-2 MX path (Alg. 2 in every butterfly, bit-exact with the
                                oracle), the default.  1: tensor-core variant: radix-16 sub-DFTs
                                as MXFP8 matrix products on tcgen05 (FP32 accumulation), each
-                               16-point input vector one MX block (k must be 32), MX-quantised
-                               twiddles between the radix-16 stages; approximate, not bit-exact.
+                               16-point input vector one MX block for k = 32 (k = 64 / 128: a
+                               block of 2 / 4 consecutive vectors of a transform; other k
+                               MXFFT_ERR_UNSUPPORTED), MX-quantised twiddles between the
+                               radix-16 stages; approximate, not bit-exact.
                                Needs n0, n1 in {256, 512} and format E4M3 or E5M2, else
                                MXFFT_ERR_UNSUPPORTED. */,
     MXFFT_OPT_TEST_STALL = 5  /* test hook of the bounded wait, 0 or 1; default 0.  1: the

@@ -99,6 +99,7 @@ struct Tc16Args {
     uint32_t idesc;                   // tcgen05 instruction descriptor
     int* err;                         // set when a bounded wait gives up
     int stall;                        // test hook: issue no matrix product
+    int g;                            // vectors per MX block: k / 32 (1, 2, 4)
 };
 
 // One slice of a ragged statistics launch (slices of different sizes and

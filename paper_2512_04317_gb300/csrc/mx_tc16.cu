@@ -9,9 +9,10 @@
 //       times W_M^(j22 k21) when r > 1
 //   C2: r-point DFT over j22 (r = 2: a sum and a difference, FP32)
 //   X[k1 + 16 (k21 + 16 k22)]
-// Every 16-point input vector (32 reals) is one MX block: shared power-of-two
-// scale 2^s from its largest component, elements rounded to the 8-bit format
-// (cvt.rn.satfinite).  The real 32 x 32 DFT matrix is prequantised with one
+// Every 16-point input vector (32 reals) is one MX block for k = 32 (for k =
+// 64 / 128 a block is 2 / 4 consecutive vectors of a transform): shared
+// power-of-two scale 2^s from its largest component, elements rounded to the
+// 8-bit format (cvt.rn.satfinite).  The real 32 x 32 DFT matrix is prequantised with one
 // shared scale per output row.  One tcgen05.mma (M = 128 vectors, N = 32, K =
 // 32, kind::f8f6f4) multiplies 128 vectors; because K is one block, the two
 // power-of-two scales factor out of the dot product and are applied exactly
@@ -188,9 +189,22 @@ struct Mma {
 // DFT outputs (scales applied) in y.  Ends with a CTA barrier, after which the
 // A operand, the accumulators and the caller's shared-memory writes made
 // before the call may be reused / are visible.
-template <int FMT>
+// Vector v of a round belongs to transform t and has index q in the round's
+// order (round A: j2; round C1: r k1 + j22): v = t M + q on the rows pass, v =
+// q T + t on the columns pass.  With k = 32 g an MX block is g consecutive q of
+// one transform; member i of v's block:
+template <int DIM>
+__device__ __forceinline__ int block_member(int v, int g, int lgt, int i) {
+    if (DIM == 1) return (v & ~(g - 1)) + i;
+    const int t = v & ((1 << lgt) - 1);
+    const int q = (v >> lgt) & ~(g - 1);
+    return ((q + i) << lgt) | t;
+}
+
+template <int FMT, int DIM>
 __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
-                                            uint32_t idesc, int emax, bool issue) {
+                                            uint32_t idesc, int emax, bool issue, int g,
+                                            int lgt, uint32_t* sAm) {
     const int tid = threadIdx.x, warp = tid >> 5;
     float m[16];
 #pragma unroll
@@ -199,7 +213,15 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
     for (int w = 1; w < 16; w <<= 1)
 #pragma unroll
         for (int j = 0; j + w < 16; j += 2 * w) m[j] = fmax_nan(m[j], m[j + w]);
-    const float A = m[0];
+    float A = m[0];
+    if (g > 1) {
+        // one shared scale for the g vectors of the block (members may sit in
+        // other warps: exchanged through shared memory; the previous round's
+        // reads of sAm finished before its product was issued)
+        sAm[tid] = __float_as_uint(A);
+        __syncthreads();
+        for (int i = 0; i < g; i++) A = fmax_nan(A, __uint_as_float(sAm[block_member<DIM>(tid, g, lgt, i)]));
+    }
     const bool bad = !(A <= 3.402823466e38f);
     const int sv = mx_scale_exp(__float_as_uint(A), emax);
     const float inv = exp2i(-sv);
@@ -323,6 +345,7 @@ tc16_pass_kernel(const Args a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ uint32_t sAm[kThreads];   // block maxima exchange (k > 32)
     uint8_t* sB = smem + kOffB;
     float2* sTwA = reinterpret_cast<float2*>(smem + kOffTwA);
     float2* sTwC = reinterpret_cast<float2*>(smem + kOffTwC);
@@ -410,7 +433,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
             }
-            dft16_round<FMT>(x, y, mm, a.idesc, emax, !a.stall);
+            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
@@ -449,7 +472,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
             }
-            dft16_round<FMT>(x, y, mm, a.idesc, emax, !a.stall);
+            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             if (r == 1) {
                 // X[k1 + 16 k2]
 #pragma unroll

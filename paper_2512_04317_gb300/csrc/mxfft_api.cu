@@ -422,6 +422,7 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
         t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
         t.err = p->d_err;
         t.stall = p->test_stall;
+        t.g = p->kblk / 32;
         ProfRec* r = prof_begin(p, 3, s);
         cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
         prof_end(r, s);
@@ -542,7 +543,8 @@ int mxfft_set_option(mxfft_plan_t p, int key, double value) {
         case MXFFT_OPT_PATH: {
             if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
             if (value == 0.0) { p->path = 0; return MXFFT_OK; }
-            if (p->kblk != 32 || !tc16_supported(p->n1, p->n0, p->fmt) ||
+            if ((p->kblk != 32 && p->kblk != 64 && p->kblk != 128) ||
+                !tc16_supported(p->n1, p->n0, p->fmt) ||
                 !tc16_supported(p->n0, p->n1, p->fmt))
                 return MXFFT_ERR_UNSUPPORTED;
             const int rc = build_tc16_tables(p);

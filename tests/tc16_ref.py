@@ -1,6 +1,7 @@
 """numpy emulation of the tensor-core radix-16 variant (MXFFT_OPT_PATH = 1),
 written from its description: four-step n = 16 x 16 r, each 16-point input
-vector one MX block, the real 32 x 32 DFT matrix quantised with one shared
+vector one MX block (k = 32; for k = 64 / 128 a block is 2 / 4 consecutive
+vectors of a transform), the real 32 x 32 DFT matrix quantised with one shared
 scale per output row, products exact and accumulated in FP64 (the hardware
 accumulates 32 exact products in FP32, so results agree to ~1e-7 relative),
 MX-quantised twiddles multiplied in FP32.  Uses the oracle's element rounding
@@ -53,10 +54,17 @@ def dft16_matrix(sgn, fmt):
     return Fq, sF
 
 
-def dft16_mx(V, fmt, sgn):
-    """V: complex64 [..., 16] -> complex64 [..., 16]."""
+def dft16_mx(V, fmt, sgn, g=1, vec_axes=1):
+    """V: complex64 [..., vectors, 16] -> complex64 [..., vectors, 16].  With
+    k = 32 g one MX block is g consecutive vectors of a transform (the last
+    vec_axes axes before the element axis, flattened in order)."""
     r = np.stack([V.real, V.imag], -1).reshape(V.shape[:-1] + (32,)).astype(np.float32)
-    sv = _scale_exp(np.abs(r).max(-1), EMAX[fmt])
+    amax = np.abs(r).max(-1)
+    if g > 1:
+        lead = amax.shape[:amax.ndim - vec_axes]
+        a = amax.reshape(lead + (-1, g)).max(-1, keepdims=True)
+        amax = np.broadcast_to(a, lead + (a.shape[-2], g)).reshape(amax.shape)
+    sv = _scale_exp(amax, EMAX[fmt])
     q = _q(r * np.exp2(-sv)[..., None].astype(np.float32), fmt)
     Fq, sF = dft16_matrix(sgn, fmt)
     D = (q @ Fq.T).astype(np.float32)                    # exact products, FP32 result
@@ -71,22 +79,22 @@ def cmul32(w, y):
     return ((wr * yr - wi * yi) + 1j * (wr * yi + wi * yr)).astype(np.complex64)
 
 
-def fft1d(x, fmt, sgn):
+def fft1d(x, fmt, sgn, g=1):
     """x: complex64 [..., n], n in {256, 512}; transforms the last axis."""
     n = x.shape[-1]
     r = n // 256
     M = 16 * r
     X = x.reshape(x.shape[:-1] + (16, M))                # [j1][j2]
     V = np.swapaxes(X, -1, -2)                          # [j2][j1]
-    Y = dft16_mx(V, fmt, sgn)                           # [j2][k1]
+    Y = dft16_mx(V, fmt, sgn, g)                        # [j2][k1]
     TA = np.stack([twiddle_block(j2, n, sgn, fmt) for j2 in range(M)])  # [j2][k1]
     Y = cmul32(TA, Y)
     Y = np.swapaxes(Y, -1, -2)                          # [k1][j2]
     if r == 1:
-        Z = dft16_mx(Y, fmt, sgn)                       # [k1][k2]
+        Z = dft16_mx(Y, fmt, sgn, g)                    # [k1][k2]
         return np.swapaxes(Z, -1, -2).reshape(x.shape)  # X[k1 + 16 k2]
     Yr = Y.reshape(Y.shape[:-1] + (16, r))              # [k1][j21][j22]
-    U = dft16_mx(np.swapaxes(Yr, -1, -2), fmt, sgn)     # [k1][j22][k21]
+    U = dft16_mx(np.swapaxes(Yr, -1, -2), fmt, sgn, g, 2)   # [k1][j22][k21]
     TC = np.stack([twiddle_block(j22, M, sgn, fmt) for j22 in range(r)])   # [j22][k21]
     U = cmul32(TC, U)
     a, b = U[..., 0, :], U[..., 1, :]                   # [k1][k21]
@@ -96,28 +104,30 @@ def fft1d(x, fmt, sgn):
     return np.swapaxes(out, -1, -3).reshape(x.shape)    # [k22][k21][k1]: k = k1 + 16 (k21 + 16 k22)
 
 
-def mxfft2d(x, fmt="e4m3", op="forward"):
-    """Batch [..., n0, n1] complex64; same prescale (Alg. 1) as the library."""
+def mxfft2d(x, fmt="e4m3", op="forward", k=32):
+    """Batch [..., n0, n1] complex64; same prescale (Alg. 1) as the library;
+    k in {32, 64, 128} (blocks of k / 32 consecutive vectors)."""
+    g = k // 32
     x = np.asarray(x, np.complex64)
     out = np.empty_like(x)
     flat = x.reshape((-1,) + x.shape[-2:])
     res = out.reshape(flat.shape)
     for i, s in enumerate(flat):
         def transform(z, sgn):
-            k, _ = oracle.prescale_k(z, fmt)
-            zs = (z * np.float32(2.0 ** k)).astype(np.complex64)
-            zs = fft1d(zs, fmt, sgn)                                         # rows
-            zs = np.swapaxes(fft1d(np.swapaxes(zs, 0, 1).copy(), fmt, sgn), 0, 1)   # columns
-            return zs, k
+            ke, _ = oracle.prescale_k(z, fmt)
+            zs = (z * np.float32(2.0 ** ke)).astype(np.complex64)
+            zs = fft1d(zs, fmt, sgn, g)                                      # rows
+            zs = np.swapaxes(fft1d(np.swapaxes(zs, 0, 1).copy(), fmt, sgn, g), 0, 1)   # columns
+            return zs, ke
         if op == "forward":
-            y, k = transform(s, -1)
-            res[i] = y * np.float32(2.0 ** -k)
+            y, ke = transform(s, -1)
+            res[i] = y * np.float32(2.0 ** -ke)
         elif op == "inverse":
-            y, k = transform(s, +1)
-            res[i] = y * np.float32(2.0 ** -k)
+            y, ke = transform(s, +1)
+            res[i] = y * np.float32(2.0 ** -ke)
         else:
-            y, k = transform(s, -1)
-            y = (y * np.float32(2.0 ** -k)).astype(np.complex64)
+            y, ke = transform(s, -1)
+            y = (y * np.float32(2.0 ** -ke)).astype(np.complex64)
             z, ki = transform(y, +1)
             lg = int(np.log2(s.shape[0] * s.shape[1]))
             res[i] = z * np.float32(2.0 ** (-ki - lg))

@@ -19,12 +19,12 @@ import tc16_ref  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def run_tc16(x, fmt, op):
+def run_tc16(x, fmt, op, k=32):
     import torch
 
     from paper_2512_04317_gb300 import mxfft
     xt = torch.from_numpy(np.ascontiguousarray(x, np.complex64)).cuda()
-    with mxfft.Plan(x.shape[-2], x.shape[-1], fmt, 32, path="tc16") as p:
+    with mxfft.Plan(x.shape[-2], x.shape[-1], fmt, k, path="tc16") as p:
         y = getattr(p, op)(xt)
         torch.cuda.synchronize()
         st, flags, _ = p.status()
@@ -49,16 +49,31 @@ def test_tc16_matches_emulation(n0, n1, fmt, op, cuda_device):
     assert nrmse(got, want.astype(np.complex128)) < 1e-4
 
 
+@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512)])
+@pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
+@pytest.mark.parametrize("k", [64, 128])
+def test_tc16_shared_block_scales_match_emulation(n0, n1, fmt, k, cuda_device):
+    # k = 64 / 128: one scale for 2 / 4 consecutive vectors, across warps on
+    # the columns pass
+    for op in ("forward", "roundtrip"):
+        x = phantom.mri_batch(n0, n1, 2, 1, config_id=35, domain="image" if op == "roundtrip" else "kspace")
+        got = run_tc16(x, fmt, op, k)
+        want = tc16_ref.mxfft2d(x, fmt, op, k)
+        assert np.isfinite(got).all()
+        assert nrmse(got, want.astype(np.complex128)) < 1e-4
+
+
 @pytest.mark.parametrize("n", [256, 512])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
-def test_tc16_within_stated_tolerance(n, fmt, cuda_device):
+@pytest.mark.parametrize("k", [32, 64, 128])
+def test_tc16_within_stated_tolerance(n, fmt, k, cuda_device):
     ksp = phantom.mri_batch(n, n, 4, 1, config_id=32)
     img = phantom.mri_batch(n, n, 4, 1, config_id=32, domain="image")
     ref = np.fft.fft2(ksp.astype(np.complex128))
-    r2f = nrmse(oracle.mxfft2d(ksp, fmt, 32)[0], ref)
-    r2r = nrmse(oracle.mxfft2d(img, fmt, 32, op="roundtrip")[0], img.astype(np.complex128))
-    tcf = nrmse(run_tc16(ksp, fmt, "forward"), ref)
-    tcr = nrmse(run_tc16(img, fmt, "roundtrip"), img.astype(np.complex128))
+    r2f = nrmse(oracle.mxfft2d(ksp, fmt, k)[0], ref)
+    r2r = nrmse(oracle.mxfft2d(img, fmt, k, op="roundtrip")[0], img.astype(np.complex128))
+    tcf = nrmse(run_tc16(ksp, fmt, "forward", k), ref)
+    tcr = nrmse(run_tc16(img, fmt, "roundtrip", k), img.astype(np.complex128))
     assert tcf <= 1.10 * r2f, (tcf, r2f)
     assert tcr <= 1.10 * r2r, (tcr, r2r)
 

@@ -66,6 +66,8 @@ def parse():
                     help="engine: one batch-executor run per step, replayed as a CUDA graph; "
                          "plan: mxfft_forward + mxfft_roundtrip calls")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-tuning", action="store_true",
+                    help="ignore the autotuned launch geometries shipped with the package")
     ap.add_argument("--slices", type=int, default=0,
                     help="smaller case of a workload (profiling): about this many slices")
     ap.add_argument("--serving-requests", type=int, default=2000)
@@ -515,6 +517,11 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    tuning = None
+    tfile = os.path.join(ROOT, "paper_2512_04317_gb300", "tuning", "gb300_sm103a.json")
+    if not args.no_tuning and os.path.exists(tfile):
+        mxfft.mxfft_tune_load(tfile)     # launch geometries measured by mxfft_tune
+        tuning = os.path.relpath(tfile, ROOT)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
@@ -728,7 +735,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "path": args.path,
-                       "api": args.api,
+                       "api": args.api, "tuning": tuning,
                        "n0": n0, "n1": n1,
                        "batch_per_gpu": batch, "format": w["fmt"], "k": w["k"],
                        "transforms_per_step": TRANSFORMS_PER_STEP,

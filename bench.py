@@ -170,7 +170,8 @@ def recorded_traffic(kernel, workload, pts_per_launch):
         return None
     for ent in rec.get("entries", []):
         if (ent.get("kernel") == kernel and ent.get("workload") == workload and
-                ent.get("source_digest") == source_digest(kernel)):
+                ent.get("source_digest") == source_digest(kernel) and
+                ent.get("dram_bytes_per_point_per_launch") is not None):
             return float(ent["dram_bytes_per_point_per_launch"]) * pts_per_launch
     return None
 

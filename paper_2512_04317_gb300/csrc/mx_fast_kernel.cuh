@@ -207,8 +207,14 @@ cudaError_t launch_fast_dim(const FastArgs& fa, int logm, int blocks, int thread
         case 4: k = fast_pass_kernel<FMT, 4, DIM>; break;
         default: return cudaErrorNotSupported;
     }
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // raise the opt-in limit only (never lower it): launches captured earlier
+    // in a graph may need more than this one
+    static size_t smem_limit[5] = {0, 0, 0, 0, 0};
+    if (smem > smem_limit[logm]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_limit[logm] = smem;
+    }
     k<<<blocks, threads, smem, s>>>(fa);
     return cudaGetLastError();
 }

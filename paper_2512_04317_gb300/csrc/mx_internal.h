@@ -89,7 +89,7 @@ struct Tc16Args {
     const float2* in;
     float2* out;
     const SliceRef* ref;              // as in PassArgs
-    int n0, n1, dim, n, r;            // n = 256 r
+    int n0, n1, dim, n, r;            // n = 256 r, r in {1, 2, 4}
     int batch;                        // slices (set by launch_tc16_pass)
     const uint8_t* bmat;              // B operand: 32 x 32 element codes, core-matrix layout (1 KB)
     const float2* twA;                // [j2 < 16 r][k1 < 16] twiddle element values x 2^s
@@ -100,6 +100,7 @@ struct Tc16Args {
     int* err;                         // set when a bounded wait gives up
     int stall;                        // test hook: issue no matrix product
     int g;                            // vectors per MX block: k / 32 (1, 2, 4)
+    int inv;                          // 1: inverse transform (sign of the radix-4 stage)
 };
 
 // One slice of a ragged statistics launch (slices of different sizes and
@@ -149,7 +150,7 @@ void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng,
 // The register-resident pass with ng groups per CTA (ng = 0: tuned or default).
 cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                                 int ng, cudaStream_t s);
-// Tensor-core radix-16 pass: n in {256, 512}, 8-bit formats, other a multiple
+// Tensor-core radix-16 pass: n in {256, 512, 1024}, 8-bit formats, other a multiple
 // of 4096 / n.
 bool tc16_supported(int n, int other, int fmt);
 cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s);

@@ -1,13 +1,14 @@
 // Tensor-core variant of the MX pass: radix-16 sub-DFTs as MXFP8 matrix
 // products on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulation
-// in tensor memory), for transform lengths n = 256 r, r in {1, 2}.
+// in tensor memory), for transform lengths n = 256 r, r in {1, 2, 4}.
 //
 // Decomposition (four-step, rows of a transform viewed as 16 x M, M = 16 r):
 //   j = M j1 + j2, k = k1 + 16 k2
 //   A : Y[k1][j2] = W_n^(j2 k1) * DFT16_j1(x[M j1 + j2])[k1]
 //   C1: for each k1, 16-point DFTs over j21 of Y[k1][r j21 + j22] (j22 < r),
 //       times W_M^(j22 k21) when r > 1
-//   C2: r-point DFT over j22 (r = 2: a sum and a difference, FP32)
+//   C2: r-point DFT over j22 (r = 2: a sum and a difference; r = 4: radix 4
+//       with W_4 = -+i; FP32, every twiddle of this stage exact)
 //   X[k1 + 16 (k21 + 16 k22)]
 // Every 16-point input vector (32 reals) is one MX block for k = 32 (for k =
 // 64 / 128 a block is 2 / 4 consecutive vectors of a transform): shared
@@ -50,9 +51,9 @@ constexpr uint64_t kWaitNs = 100000000;   // bound of one completion wait: 100 m
 // reads of 8 consecutive rows hit distinct banks), then the two tile buffers.
 constexpr int kTwRow = 18;
 constexpr int kOffB = 8192;
-constexpr int kOffTwA = kOffB + 1024;                  // up to 32 rows
-constexpr int kOffTwC = kOffTwA + 32 * kTwRow * 8;     // up to 2 rows
-constexpr int kOffBuf = kOffTwC + 2 * kTwRow * 8;
+constexpr int kOffTwA = kOffB + 1024;                  // up to 64 rows
+constexpr int kOffTwC = kOffTwA + 64 * kTwRow * 8;     // up to 4 rows
+constexpr int kOffBuf = kOffTwC + 4 * kTwRow * 8;
 static_assert(kOffBuf % 16 == 0, "16-byte aligned cp.async destinations");
 
 using Args = Tc16Args;
@@ -61,16 +62,18 @@ using Args = Tc16Args;
 template <int LOGN>
 struct Geo {
     static constexpr int n = 1 << LOGN;
-    static constexpr int r = n / 256;
+    static constexpr int r = n / 256;               // 1, 2, 4
+    static constexpr int LGR = r == 1 ? 0 : (r == 2 ? 1 : 2);
     static constexpr int M = 16 * r;
-    static constexpr int LGM = r == 1 ? 4 : 5;
-    static constexpr int T = kTilePts / n;          // transforms per tile (16 or 8)
-    static constexpr int LGT = T == 16 ? 4 : 3;
-    // rows pass: [t][e], 2 pad slots after every M elements
-    static constexpr int TS = n + 2 * (n / M);
+    static constexpr int LGM = 4 + LGR;
+    static constexpr int T = kTilePts / n;          // transforms per tile (16, 8, 4)
+    static constexpr int LGT = T == 16 ? 4 : (T == 8 ? 3 : 2);
+    // rows pass: [t][e], PADR pad slots after every M elements
+    static constexpr int PADR = r == 4 ? 4 : 2;
+    static constexpr int TS = n + PADR * (n / M);
     static constexpr int ROW_SLOTS = T * TS;
-    // columns pass: [e][t]; with T = 8, 8 pad slots after every 16 elements
-    static constexpr int COL_SLOTS = n * T + (T == 8 ? 8 * (n / 16) : 0);
+    // columns pass: [e][t]; with T < 16, T pad slots after every 16 elements
+    static constexpr int COL_SLOTS = n * T + (T < 16 ? T * (n / 16) : 0);
     static constexpr int BUF_SLOTS = ROW_SLOTS > COL_SLOTS ? ROW_SLOTS : COL_SLOTS;
     static_assert(T * M == kThreads, "one vector per thread per stage");
 };
@@ -78,19 +81,20 @@ struct Geo {
 // Slot (8 bytes) of element e of transform t.  Rows pass: round A reads 16
 // consecutive elements per half-warp; round C1 reads each thread's own group
 // of M elements as 16-byte pairs (r = 1: chunks 9 k1 + c, distinct mod 8 over
-// a quarter-warp) or 8-byte elements (r = 2: slots 34 k1 + 2 j + j22, distinct
-// mod 16 over a half-warp).  Columns pass: a half-warp spans 16 transforms
-// (T = 16) or 8 transforms x two elements 16 apart (T = 8, the pad puts them
-// in opposite bank halves).
+// a quarter-warp) or 8-byte elements (r = 2: slots 34 k1 + 2 j + j22; r = 4:
+// 68 k1 + 4 j + j22; distinct mod 16 over a half-warp).  Columns pass: a
+// half-warp spans 16 transforms (T = 16) or T transforms x 16 / T elements
+// whose pads put them in distinct bank groups (T = 8, 4).  Every pattern was
+// checked for bank conflicts by enumerating its addresses.
 template <int LOGN>
 __device__ __forceinline__ int slot_row(int t, int e) {
     using G = Geo<LOGN>;
-    return t * G::TS + e + 2 * (e >> G::LGM);
+    return t * G::TS + e + G::PADR * (e >> G::LGM);
 }
 template <int LOGN>
 __device__ __forceinline__ int slot_col(int t, int e) {
     using G = Geo<LOGN>;
-    return e * G::T + (G::T == 8 ? 8 * (e >> 4) : 0) + t;
+    return e * G::T + (G::T < 16 ? G::T * (e >> 4) : 0) + t;
 }
 template <int LOGN, int DIM>
 __device__ __forceinline__ int slot(int t, int e) {
@@ -456,8 +460,8 @@ tc16_pass_kernel(const Args a) {
             int t, rem;
             if (DIM == 1) { t = v >> G::LGM; rem = v & (M - 1); }
             else { t = v & (T - 1); rem = v >> G::LGT; }
-            const int k1 = r == 1 ? rem : rem >> 1;
-            const int j22 = r == 1 ? 0 : rem & 1;
+            const int k1 = rem >> G::LGR;
+            const int j22 = rem & (r - 1);
             float2 x[16], y[16];
             if (DIM == 1 && r == 1) {
                 // own group of 16 consecutive elements, as 16-byte pairs
@@ -502,6 +506,55 @@ tc16_pass_kernel(const Args a) {
         }
         __syncthreads();
 
+        if (r == 4) {
+            // ---- C2: radix-4 over j22 (W_4 = -+i exact): X[k1 + 16 (k21 + 16 k22)]
+            const float sg = a.inv ? 1.0f : -1.0f;         // W_4 = sg i
+#pragma unroll 2
+            for (int i = 0; i < 4; i++) {
+                const int u = tid + i * kThreads;       // (t, k1, k21), T x 16 x 16
+                int t, k1, k21;
+                if (DIM == 1) { k1 = u & 15; k21 = (u >> 4) & 15; t = u >> 8; }
+                else { t = u & 3; k21 = 4 * ((u >> 2) & 3) + (u >> 8); k1 = (u >> 4) & 15; }
+                const int e = M * k1 + 4 * k21;
+                float2 U0, U1, U2, U3;
+                if (DIM == 1) {
+                    // two 16-byte reads; lanes with k1 bit 2 set read the upper
+                    // pair first, so a quarter-warp covers 8 distinct chunks
+                    const float4* q = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, e));
+                    const int par = (k1 >> 2) & 1;
+                    const float4 f0 = q[par], f1 = q[par ^ 1];
+                    const float4 lo = par ? f1 : f0, hi = par ? f0 : f1;
+                    U0 = make_float2(lo.x, lo.y);
+                    U1 = make_float2(lo.z, lo.w);
+                    U2 = make_float2(hi.x, hi.y);
+                    U3 = make_float2(hi.z, hi.w);
+                } else {
+                    U0 = d[slot_col<LOGN>(t, e)];
+                    U1 = d[slot_col<LOGN>(t, e + 1)];
+                    U2 = d[slot_col<LOGN>(t, e + 2)];
+                    U3 = d[slot_col<LOGN>(t, e + 3)];
+                }
+                const float2 a0 = make_float2(__fadd_rn(U0.x, U2.x), __fadd_rn(U0.y, U2.y));
+                const float2 a1 = make_float2(__fsub_rn(U0.x, U2.x), __fsub_rn(U0.y, U2.y));
+                const float2 b0 = make_float2(__fadd_rn(U1.x, U3.x), __fadd_rn(U1.y, U3.y));
+                const float2 b1 = make_float2(__fsub_rn(U1.x, U3.x), __fsub_rn(U1.y, U3.y));
+                const float2 wb = make_float2(-sg * b1.y, sg * b1.x);     // W_4 b1, exact
+                float2 X[4];
+                X[0] = make_float2(__fadd_rn(a0.x, b0.x), __fadd_rn(a0.y, b0.y));
+                X[1] = make_float2(__fadd_rn(a1.x, wb.x), __fadd_rn(a1.y, wb.y));
+                X[2] = make_float2(__fsub_rn(a0.x, b0.x), __fsub_rn(a0.y, b0.y));
+                X[3] = make_float2(__fsub_rn(a1.x, wb.x), __fsub_rn(a1.y, wb.y));
+#pragma unroll
+                for (int k22 = 0; k22 < 4; k22++) {
+                    const float2 val = scale_out ? scale2(X[k22], post) : X[k22];
+                    const int eo = k1 + 16 * k21 + 256 * k22;
+                    if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + eo] = val;
+                    else out[(size_t)eo * a.n1 + t0 + t] = val;
+                }
+            }
+            // the buffer is refilled by the next iteration's prefetch
+            if (__syncthreads_or(!mm.ok)) break;
+        }
         if (r == 2) {
             // ---- C2: radix-2 over j22: X[k1 + 16 (k21 + 16 k22)] ----------
 #pragma unroll 2
@@ -583,14 +636,15 @@ cudaError_t launch_one(const Args& a, cudaStream_t s) {
 template <int FMT>
 cudaError_t launch_fmt(const Args& a, cudaStream_t s) {
     if (a.n == 256) return a.dim == 1 ? launch_one<FMT, 1, 8>(a, s) : launch_one<FMT, 0, 8>(a, s);
-    return a.dim == 1 ? launch_one<FMT, 1, 9>(a, s) : launch_one<FMT, 0, 9>(a, s);
+    if (a.n == 512) return a.dim == 1 ? launch_one<FMT, 1, 9>(a, s) : launch_one<FMT, 0, 9>(a, s);
+    return a.dim == 1 ? launch_one<FMT, 1, 10>(a, s) : launch_one<FMT, 0, 10>(a, s);
 }
 
 }  // namespace tc16
 
 bool tc16_supported(int n, int other, int fmt) {
-    // n = 256 r (r = 1, 2), 8-bit element formats, whole tiles of 4096 / n transforms
-    if (n != 256 && n != 512) return false;
+    // n = 256 r (r = 1, 2, 4), 8-bit element formats, whole tiles of 4096 / n transforms
+    if (n != 256 && n != 512 && n != 1024) return false;
     const int T = tc16::kTilePts / n;
     return other >= T && other % T == 0 && (fmt == 0 || fmt == 1);
 }

@@ -423,6 +423,7 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
         t.err = p->d_err;
         t.stall = p->test_stall;
         t.g = p->kblk / 32;
+        t.inv = dir;
         ProfRec* r = prof_begin(p, 3, s);
         cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
         prof_end(r, s);

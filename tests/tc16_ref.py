@@ -80,7 +80,7 @@ def cmul32(w, y):
 
 
 def fft1d(x, fmt, sgn, g=1):
-    """x: complex64 [..., n], n in {256, 512}; transforms the last axis."""
+    """x: complex64 [..., n], n in {256, 512, 1024}; transforms the last axis."""
     n = x.shape[-1]
     r = n // 256
     M = 16 * r
@@ -97,10 +97,19 @@ def fft1d(x, fmt, sgn, g=1):
     U = dft16_mx(np.swapaxes(Yr, -1, -2), fmt, sgn, g, 2)   # [k1][j22][k21]
     TC = np.stack([twiddle_block(j22, M, sgn, fmt) for j22 in range(r)])   # [j22][k21]
     U = cmul32(TC, U)
-    a, b = U[..., 0, :], U[..., 1, :]                   # [k1][k21]
-    s0 = (a + b).astype(np.complex64)
-    s1 = (a - b).astype(np.complex64)
-    out = np.stack([s0, s1], -1)                        # [k1][k21][k22]
+    if r == 2:
+        a, b = U[..., 0, :], U[..., 1, :]               # [k1][k21]
+        s0 = (a + b).astype(np.complex64)
+        s1 = (a - b).astype(np.complex64)
+        out = np.stack([s0, s1], -1)                    # [k1][k21][k22]
+    else:
+        # radix 4 in FP32 with W_4 = sgn i (exact): the same additions in the
+        # same order as the kernel
+        U0, U1, U2, U3 = (U[..., j, :] for j in range(4))
+        a0, a1 = (U0 + U2).astype(np.complex64), (U0 - U2).astype(np.complex64)
+        b0, b1 = (U1 + U3).astype(np.complex64), (U1 - U3).astype(np.complex64)
+        wb = (np.float32(-sgn) * b1.imag + 1j * (np.float32(sgn) * b1.real)).astype(np.complex64)
+        out = np.stack([a0 + b0, a1 + wb, a0 - b0, a1 - wb], -1).astype(np.complex64)
     return np.swapaxes(out, -1, -3).reshape(x.shape)    # [k22][k21][k1]: k = k1 + 16 (k21 + 16 k22)
 
 

@@ -8,6 +8,7 @@ import json
 import numpy as np
 import pytest
 
+import oracle
 from paper_2512_04317_gb300 import phantom
 
 pytestmark = pytest.mark.gpu
@@ -156,3 +157,60 @@ def test_tuned_geometries_give_the_same_bits(cuda_device, tmp_path):
             np.testing.assert_array_equal(p.roundtrip(x).cpu().numpy().view(np.uint32),
                                           want.view(np.uint32))
     mxfft.mxfft_tune_clear()
+
+
+def test_engine_many_groups_beyond_fork_streams(cuda_device):
+    # 12 (plan, direction) groups share 8 fork streams; round trips of several
+    # plans run as the second stage
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    shapes = [(32, 64), (64, 32), (16, 16), (128, 64)]
+    fmts = [("e4m3", 32), ("e5m2", 16), ("e2m3", 8)]
+    work, want = [], []
+    for i, (n0, n1) in enumerate(shapes):
+        for j, (fmt, k) in enumerate(fmts):
+            op = ["forward", "inverse", "roundtrip"][(i + j) % 3]
+            x = phantom.random_complex((1 + (i + j) % 3, n0, n1), seed=500 + 10 * i + j, scale=5.0)
+            xt = torch.from_numpy(x).cuda()
+            work.append((op, xt, torch.empty_like(xt), fmt, k))
+            want.append(oracle.mxfft2d(x, fmt, k, op=op)[0])
+    with mxfft.Engine(graphs=True) as eng:
+        for rep in range(2):
+            eng.run(work)
+            torch.cuda.synchronize()
+            assert eng.status()[0] == 0
+            for (op, xt, y, fmt, k), w in zip(work, want):
+                assert_same([y.cpu().numpy()], [w])
+
+
+def test_engine_hundreds_of_small_items(cuda_device):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = phantom.random_complex((300, 8, 16), seed=77, scale=3.0)
+    want = oracle.mxfft2d(x, "e4m3", 8, op="roundtrip")[0]
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    work = [("roundtrip", xt[i:i + 1], yt[i:i + 1], "e4m3", 8) for i in range(300)]
+    with mxfft.Engine(graphs=False) as eng:
+        eng.run(work)
+        torch.cuda.synchronize()
+    assert_same([yt.cpu().numpy()], [want])
+
+
+def test_engine_graph_cache_eviction(cuda_device):
+    # more signatures than the cache holds: the cache is cleared and rebuilt,
+    # results stay exact
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = phantom.random_complex((70, 16, 16), seed=78, scale=2.0)
+    want = oracle.mxfft2d(x, "e4m3", 16)[0]
+    xt = torch.from_numpy(x).cuda()
+    yt = torch.empty_like(xt)
+    with mxfft.Engine(graphs=True) as eng:
+        for b in range(1, 71):          # 70 different slice counts = 70 signatures
+            eng.run([("forward", xt[:b], yt[:b], "e4m3", 16)])
+        torch.cuda.synchronize()
+    assert_same([yt.cpu().numpy()], [want])

@@ -36,7 +36,8 @@ def nrmse(a, ref):
     return float(np.linalg.norm(a.astype(np.complex128) - ref) / np.linalg.norm(ref))
 
 
-@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (512, 256)])
+@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (512, 256), (1024, 1024),
+                                   (256, 1024), (1024, 512)])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("op", ["forward", "inverse", "roundtrip"])
 def test_tc16_matches_emulation(n0, n1, fmt, op, cuda_device):
@@ -49,7 +50,7 @@ def test_tc16_matches_emulation(n0, n1, fmt, op, cuda_device):
     assert nrmse(got, want.astype(np.complex128)) < 1e-4
 
 
-@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512)])
+@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (1024, 256)])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("k", [64, 128])
 def test_tc16_shared_block_scales_match_emulation(n0, n1, fmt, k, cuda_device):
@@ -63,7 +64,7 @@ def test_tc16_shared_block_scales_match_emulation(n0, n1, fmt, k, cuda_device):
         assert nrmse(got, want.astype(np.complex128)) < 1e-4
 
 
-@pytest.mark.parametrize("n", [256, 512])
+@pytest.mark.parametrize("n", [256, 512, 1024])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("k", [32, 64, 128])
 def test_tc16_within_stated_tolerance(n, fmt, k, cuda_device):
@@ -90,7 +91,8 @@ def test_tc16_option_validation(cuda_device):
     p.close()
 
 
-@pytest.mark.parametrize("n0,n1,batch", [(256, 256, 40), (512, 512, 6), (512, 256, 11)])
+@pytest.mark.parametrize("n0,n1,batch", [(256, 256, 40), (512, 512, 6), (512, 256, 11),
+                                         (1024, 1024, 3), (1024, 256, 5)])
 def test_tc16_many_tiles_per_cta(n0, n1, batch, cuda_device):
     # more 4096-point tiles than resident CTAs: every CTA walks several tiles,
     # an uneven number each, through both shared buffers

@@ -41,6 +41,9 @@ WORKLOADS = {
     "multicoil_16x32_512x512": dict(n0=512, n1=512, nslices=32, ncoils=16, fmt="e4m3", k=32,
                                     config_id=3, desc="16 coils x 32 slices 512x512, MXFP8 e4m3, "
                                                       "k=32; forward + round trip"),
+    "multicoil_16x4_1024x1024": dict(n0=1024, n1=1024, nslices=4, ncoils=16, fmt="e4m3", k=32,
+                                     config_id=7, desc="16 coils x 4 slices 1024x1024, MXFP8 e4m3, "
+                                                       "k=32; forward + round trip"),
     "large_8_2048x2048": dict(n0=2048, n1=2048, nslices=8, ncoils=1, fmt="e4m3", k=32,
                               config_id=5, desc="8 x 2048x2048 phantoms, MXFP8 e4m3, k=32; "
                                                 "forward + round trip"),

@@ -194,7 +194,9 @@ __device__ __forceinline__ void stage_a(float2 (&r)[32], const TwA& tw, const Fm
 }
 
 // Phase B: one stage on 8 butterflies u = Ru[i], v = Rv[i], j = jb + i, with
-// twiddles at twh[j] / tws[j] (already offset to stage h: index h - 1 + j).
+// twiddles at twh[j] / tws[j] (already offset to stage h: the f16x2 table at
+// index h + j, 32-byte aligned runs of 8 since jb is a multiple of 8; the
+// exponents at h - 1 + j).
 template <int FMT, int LOGM>
 __device__ __forceinline__ void stage_b8(float2 (&Ru)[8], float2 (&Rv)[8],
                                          const uint32_t* __restrict__ twh,
@@ -202,6 +204,9 @@ __device__ __forceinline__ void stage_b8(float2 (&Ru)[8], float2 (&Rv)[8],
                                          const FmtParams& fp) {
     constexpr int M = 1 << LOGM;
     constexpr int ML = M < 8 ? M : 8;  // butterflies of a block held by this thread
+    const uint4* t4 = reinterpret_cast<const uint4*>(twh + jb);
+    const uint4 wa = __ldg(t4), wb = __ldg(t4 + 1);
+    const uint32_t w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
     for (int b0 = 0; b0 < 8; b0 += ML) {
         float2* U[ML];
@@ -211,7 +216,7 @@ __device__ __forceinline__ void stage_b8(float2 (&Ru)[8], float2 (&Rv)[8],
         for (int q = 0; q < ML; q++) {
             U[q] = &Ru[b0 + q];
             V[q] = &Rv[b0 + q];
-            W[q] = __ldg(twh + jb + b0 + q);
+            W[q] = w8[b0 + q];
         }
         mx_block<FMT, ML>(U, V, W, __ldg(tws + jb + b0), M > 8 ? red : 0u, fp);
     }
@@ -225,7 +230,7 @@ __host__ __device__ constexpr int rev5(int t) {
 struct FastArgs {
     PassArgs a;
     TwA twa;
-    const uint32_t* twh;   // f16x2 twiddle element values, index h - 1 + j
+    const uint32_t* twh;   // f16x2 twiddle element values, index h + j (entry 0 unused)
     int TG;                // transforms per group (16, or 8 for n = 2048)
     int lgTG;              // log2(TG)
     int S;                 // shared row stride (complex) of a group: TG or TG + 1

@@ -131,11 +131,11 @@ fast_pass_kernel(const FastArgs fa) {
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i++) R[q][i] = Gs[(e0[q] + i) * S + tau];
-        stage_b8<FMT, LOGM>(R[0], R[1], fa.twh + h - 1, a.tws + h - 1, jA, red, fp);
-        stage_b8<FMT, LOGM>(R[2], R[3], fa.twh + h - 1, a.tws + h - 1, jB, red, fp);
+        stage_b8<FMT, LOGM>(R[0], R[1], fa.twh + h, a.tws + h - 1, jA, red, fp);
+        stage_b8<FMT, LOGM>(R[2], R[3], fa.twh + h, a.tws + h - 1, jB, red, fp);
         if (two) {
-            stage_b8<FMT, LOGM>(R[0], R[2], fa.twh + 2 * h - 1, a.tws + 2 * h - 1, jC, red, fp);
-            stage_b8<FMT, LOGM>(R[1], R[3], fa.twh + 2 * h - 1, a.tws + 2 * h - 1, jD, red, fp);
+            stage_b8<FMT, LOGM>(R[0], R[2], fa.twh + 2 * h, a.tws + 2 * h - 1, jC, red, fp);
+            stage_b8<FMT, LOGM>(R[1], R[3], fa.twh + 2 * h, a.tws + 2 * h - 1, jD, red, fp);
         }
         ast += two ? 2 : 1;
         if (ast >= L) break;

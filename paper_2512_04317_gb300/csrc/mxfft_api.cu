@@ -505,9 +505,13 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
                 p->twa[axis][d].h2[i] = i < (int)h2.size() ? h2[i] : 0u;
                 p->twa[axis][d].sw[i] = i < (int)sw.size() ? sw[i] : (int8_t)0;
             }
-            rc = cuda_status(cudaMalloc(&p->d_twh[axis][d], sizeof(uint32_t) * h2.size()));
+            // device copy shifted by one entry (stage h at index h + j): every run
+            // of 8 twiddles the register pass loads starts 32-byte aligned
+            std::vector<uint32_t> h2s(h2.size() + 1, 0u);
+            std::copy(h2.begin(), h2.end(), h2s.begin() + 1);
+            rc = cuda_status(cudaMalloc(&p->d_twh[axis][d], sizeof(uint32_t) * h2s.size()));
             if (rc == MXFFT_OK)
-                rc = cuda_status(cudaMemcpy(p->d_twh[axis][d], h2.data(), sizeof(uint32_t) * h2.size(),
+                rc = cuda_status(cudaMemcpy(p->d_twh[axis][d], h2s.data(), sizeof(uint32_t) * h2s.size(),
                                             cudaMemcpyHostToDevice));
         }
         if (rc == MXFFT_OK) rc = cuda_status(cudaMalloc(&p->d_tws[axis], sw.size()));

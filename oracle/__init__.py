@@ -9,7 +9,9 @@ operation order, ``-ffp-contract=off``); this module compiles it with gcc and
 wraps it with ctypes over numpy arrays.
 
 Functions and the passages they follow:
-  * ``mxfft2d``         Alg. 1 + Alg. 2 inside a radix-2 DIT 2D FFT; Eq. (1)
+  * ``mxfft2d``         Alg. 1 + Alg. 2 inside a radix-2 DIT 2D FFT; Eq. (1);
+                        op "roundtrip_fused": the fused encode -> F -> F^-1 ->
+                        decode round trip of Sec. 4.3 (reading C17)
   * ``prescale_k``      Alg. 1 (Sec. 2.1)
   * ``magnitude``       |x| as used by Alg. 1 (reading C3)
   * ``quantize``        the OCP element rounding used by EncodeBlockMX (Sec. 2.2)
@@ -35,7 +37,7 @@ FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
 # the FP6/FP4 formats, where the paper gives none.
 TAU_MIN_DEFAULT = {"e4m3": 2.0**-10, "e5m2": 2.0**-12, "e2m3": 2.0**-10,
                    "e3m2": 2.0**-10, "e2m1": 2.0**-10, "fp16": 2.0**-24}
-OP = {"forward": 0, "inverse": 1, "roundtrip": 2}
+OP = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}
 
 _lock = threading.Lock()
 _lib = None
@@ -124,8 +126,8 @@ def mxfft2d(x: np.ndarray, fmt="e4m3", k: int = 32, tau: float = 1e-3,
 
     Returns ``(out, kexp, flags)``: ``out`` complex64 with the shape of ``x``;
     ``kexp`` the prescale exponents, shape ``[batch]`` (``[batch, 2]`` for the
-    round trip: forward k, inverse k); ``flags`` nonzero where a prescale saw a
-    non-finite magnitude.
+    round trip: forward k, inverse k; the fused round trip has one k per
+    slice); ``flags`` nonzero where a prescale saw a non-finite magnitude.
     """
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.complex64)

@@ -17,6 +17,8 @@
  *     re-encode the product as a fresh MX block, decode, then u +/- wv in FP32.
  *   - Inverse: conjugate twiddles, its own prescale, no 1/N factor (Eq. 1 puts
  *     1/N^2 outside); round trip = (1/(n0 n1)) F^-1{F{x}} (Eq. 1).
+ *   - The fused encode -> F -> F^-1 -> decode round trip of Sec. 4.3 as a
+ *     declared variant (reading C17).
  *   - An FP64 "exact" mode with the same dataflow and no quantisation, used only
  *     to pin the dataflow (bit reversal, stage indexing, twiddles) to a DFT.
  *   - The root-sum-of-squares coil combine of Eq. (1) (oracle_rss).
@@ -49,6 +51,16 @@
  *       butterfly the
  *       twiddle (rounded from FP64) and v are binary16, the complex product is
  *       formed with binary16 operations (each rounded once), u +- wv stays FP32.
+ *   C17 the fused round trip encodes once and decodes once: Alg. 1's prescale
+ *       of the input, the forward transform (rows, then columns), then the
+ *       inverse applied directly to the forward result at the input's scale
+ *       (no unscale, no second prescale, no re-encode of the forward output),
+ *       columns first and then rows (the mirror order, so that both column
+ *       transforms of a tile can run back to back), and one decode by
+ *       2^(-k - log2(n0 n1)).  Its MX blocks are those of the separate
+ *       transforms; only the inverse's axis order and the missing second
+ *       prescale change the result.  Not defined for the FP16 control (its
+ *       binary16 products would overflow at the unscaled intermediate size).
  *
  * Floating-point contract: compile with -ffp-contract=off and without
  * fast-math.  Every FP32 result below is one IEEE operation on FP32 operands.
@@ -458,16 +470,16 @@ static int prescale_k(const float *x, long cnt, const prescale_params *p,
 /* 2D driver.                                                                 */
 /* ------------------------------------------------------------------------- */
 
-/* op: 0 forward, 1 inverse, 2 round trip.  in/out: [batch][n0][n1] complex64
- * interleaved (in == out allowed).  k_out: [batch] prescale exponents (for the
- * round trip, k_out[2b] = forward k and k_out[2b+1] = inverse k), flags_out:
- * [batch] nonzero when a prescale saw a non-finite magnitude.
- * Returns 0, or -1 on bad arguments / allocation failure. */
-static void transform_slice(float *S, int n0, int n1, int kblk, int inverse,
-                            const elem_fmt *f, const bf_opts *o, fft_ws *ws)
+static void rows_mx(float *S, int n0, int n1, int kblk, int inverse,
+                    const elem_fmt *f, const bf_opts *o, fft_ws *ws)
 {
     for (int r = 0; r < n0; r++)
         fft1d_mx(S + 2L * r * n1, n1, kblk, inverse, f, o, ws);
+}
+
+static void cols_mx(float *S, int n0, int n1, int kblk, int inverse,
+                    const elem_fmt *f, const bf_opts *o, fft_ws *ws)
+{
     float *col = malloc(sizeof(float) * 2 * n0);
     for (int c = 0; c < n1; c++) {
         for (int r = 0; r < n0; r++) {
@@ -483,8 +495,22 @@ static void transform_slice(float *S, int n0, int n1, int kblk, int inverse,
     free(col);
 }
 
+/* One 2D transform: rows (length n1) first, then columns (reading C12). */
+static void transform_slice(float *S, int n0, int n1, int kblk, int inverse,
+                            const elem_fmt *f, const bf_opts *o, fft_ws *ws)
+{
+    rows_mx(S, n0, n1, kblk, inverse, f, o, ws);
+    cols_mx(S, n0, n1, kblk, inverse, f, o, ws);
+}
+
 static int valid_pow2(int n) { return n >= 2 && n <= 4096 && (n & (n - 1)) == 0; }
 
+/* op: 0 forward, 1 inverse, 2 round trip, 3 fused round trip (reading C17).
+ * in/out: [batch][n0][n1] complex64 interleaved (in == out allowed).  k_out:
+ * [batch] prescale exponents (for the round trip, k_out[2b] = forward k and
+ * k_out[2b+1] = inverse k), flags_out: [batch] nonzero when a prescale saw a
+ * non-finite magnitude.  Returns 0, or -1 on bad arguments (op 3 with the FP16
+ * control) / allocation failure. */
 int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
                    int fmt, int kblk, float tau, double target, double tau_min,
                    int kmin, int kmax, int op, int renorm, int direct_enc,
@@ -492,7 +518,7 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
 {
     elem_fmt f;
     if (get_fmt(fmt, &f) || !valid_pow2(n0) || !valid_pow2(n1) || batch < 0 ||
-        kblk < 2 || (kblk & (kblk - 1)) || op < 0 || op > 2)
+        kblk < 2 || (kblk & (kblk - 1)) || op < 0 || op > 3 || (op == 3 && f.fp16))
         return -1;
     bf_opts o = {renorm, direct_enc};
     prescale_params pp = {tau, target, tau_min, kmin, kmax};
@@ -534,6 +560,16 @@ int oracle_mxfft2d(const float *in, float *out, int batch, int n0, int n1,
             if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -kinv - lg);
             if (k_out) k_out[2 * s + 1] = kinv;
+        } else if (op == 3) {
+            /* fused round trip: the forward result A stays at the input's
+             * scale (no unscale, no second prescale); the inverse runs
+             * columns first, then rows; one combined decode by
+             * 2^(-k - log2(n0 n1)) */
+            cols_mx(S, n0, n1, kblk, 1, &f, &o, &ws);
+            rows_mx(S, n0, n1, kblk, 1, &f, &o, &ws);
+            int lg = ilog2i(n0) + ilog2i(n1);
+            for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k - lg);
+            if (k_out) k_out[s] = k;
         } else {
             if (q16) for (long i = 0; i < 2 * npts; i++) S[i] = (float)q_fp16(S[i]);
             for (long i = 0; i < 2 * npts; i++) S[i] = ldexpf(S[i], -k);
@@ -645,10 +681,31 @@ static void fft1d_f64(double *A, int n, int inverse, double *tmp)
     }
 }
 
-/* op: 0 forward, 1 inverse (unnormalised), 2 round trip (with 1/(n0 n1)). */
+static void rows_f64(double *S, int n0, int n1, int inv, double *tmp)
+{
+    for (int r = 0; r < n0; r++) fft1d_f64(S + 2L * r * n1, n1, inv, tmp);
+}
+
+static void cols_f64(double *S, int n0, int n1, int inv, double *tmp, double *col)
+{
+    for (int c = 0; c < n1; c++) {
+        for (int r = 0; r < n0; r++) {
+            col[2 * r] = S[2L * ((long)r * n1 + c)];
+            col[2 * r + 1] = S[2L * ((long)r * n1 + c) + 1];
+        }
+        fft1d_f64(col, n0, inv, tmp);
+        for (int r = 0; r < n0; r++) {
+            S[2L * ((long)r * n1 + c)] = col[2 * r];
+            S[2L * ((long)r * n1 + c) + 1] = col[2 * r + 1];
+        }
+    }
+}
+
+/* op: 0 forward, 1 inverse (unnormalised), 2 round trip (with 1/(n0 n1)),
+ * 3 fused round trip (inverse columns first, then rows; with 1/(n0 n1)). */
 int oracle_fft2d_exact(const double *in, double *out, int batch, int n0, int n1, int op)
 {
-    if (!valid_pow2(n0) || !valid_pow2(n1) || batch < 0 || op < 0 || op > 2) return -1;
+    if (!valid_pow2(n0) || !valid_pow2(n1) || batch < 0 || op < 0 || op > 3) return -1;
     long npts = (long)n0 * n1;
     int nmax = n0 > n1 ? n0 : n1;
     double *tmp = malloc(sizeof(double) * 2 * nmax);
@@ -656,23 +713,16 @@ int oracle_fft2d_exact(const double *in, double *out, int batch, int n0, int n1,
     for (int s = 0; s < batch; s++) {
         double *S = out + 2 * npts * s;
         memmove(S, in + 2 * npts * s, sizeof(double) * 2 * npts);
-        int passes = op == 2 ? 2 : 1;
-        for (int p = 0; p < passes; p++) {
-            int inv = (op == 1) || (p == 1);
-            for (int r = 0; r < n0; r++) fft1d_f64(S + 2L * r * n1, n1, inv, tmp);
-            for (int c = 0; c < n1; c++) {
-                for (int r = 0; r < n0; r++) {
-                    col[2 * r] = S[2L * ((long)r * n1 + c)];
-                    col[2 * r + 1] = S[2L * ((long)r * n1 + c) + 1];
-                }
-                fft1d_f64(col, n0, inv, tmp);
-                for (int r = 0; r < n0; r++) {
-                    S[2L * ((long)r * n1 + c)] = col[2 * r];
-                    S[2L * ((long)r * n1 + c) + 1] = col[2 * r + 1];
-                }
-            }
+        rows_f64(S, n0, n1, op == 1, tmp);
+        cols_f64(S, n0, n1, op == 1, tmp, col);
+        if (op == 2) {
+            rows_f64(S, n0, n1, 1, tmp);
+            cols_f64(S, n0, n1, 1, tmp, col);
+        } else if (op == 3) {
+            cols_f64(S, n0, n1, 1, tmp, col);
+            rows_f64(S, n0, n1, 1, tmp);
         }
-        if (op == 2)
+        if (op >= 2)
             for (long i = 0; i < 2 * npts; i++) S[i] /= (double)npts;
     }
     free(tmp);

@@ -244,14 +244,22 @@ def prescale_k(S, tau32: Fr, target: Fr, tau_min: Fr, kmin=-126, kmax=126) -> in
     return min(max(max(k1, k2), kmin), kmax)
 
 
-def _transform2d(S, kblk, fmt, inverse):
+def _rows(S, kblk, fmt, inverse):
+    return [fft1d(list(row), kblk, fmt, inverse) for row in S]
+
+
+def _cols(S, kblk, fmt, inverse):
     n0, n1 = len(S), len(S[0])
-    S = [fft1d(list(row), kblk, fmt, inverse) for row in S]
+    S = [list(row) for row in S]
     for c in range(n1):
         col = fft1d([S[r][c] for r in range(n0)], kblk, fmt, inverse)
         for r in range(n0):
             S[r][c] = col[r]
     return S
+
+
+def _transform2d(S, kblk, fmt, inverse):
+    return _cols(_rows(S, kblk, fmt, inverse), kblk, fmt, inverse)
 
 
 def mxfft2d(x: np.ndarray, fmt: str, kblk: int, op: str = "forward", tau=1e-3,
@@ -264,13 +272,20 @@ def mxfft2d(x: np.ndarray, fmt: str, kblk: int, op: str = "forward", tau=1e-3,
     k = prescale_k(S, tau32, Fr(target), Fr(tau_min), kmin, kmax)
     S = [[(ldexp32(a, k), ldexp32(b, k)) for (a, b) in row] for row in S]
     S = _transform2d(S, kblk, fmt, inverse=(op == "inverse"))
+    lg = (len(S).bit_length() - 1) + (len(S[0]).bit_length() - 1)
+    if op == "roundtrip_fused":
+        # encode once, F, then F^-1 columns first on the undecoded result,
+        # decode once
+        S = _rows(_cols(S, kblk, fmt, True), kblk, fmt, True)
+        S = [[(ldexp32(a, -k - lg), ldexp32(b, -k - lg)) for (a, b) in row] for row in S]
+        out = np.array([[complex(float(a), float(b)) for (a, b) in row] for row in S])
+        return out, k
     S = [[(ldexp32(a, -k), ldexp32(b, -k)) for (a, b) in row] for row in S]
     kout = k
     if op == "roundtrip":
         kinv = prescale_k(S, tau32, Fr(target), Fr(tau_min), kmin, kmax)
         S = [[(ldexp32(a, kinv), ldexp32(b, kinv)) for (a, b) in row] for row in S]
         S = _transform2d(S, kblk, fmt, inverse=True)
-        lg = (len(S).bit_length() - 1) + (len(S[0]).bit_length() - 1)
         S = [[(ldexp32(a, -kinv - lg), ldexp32(b, -kinv - lg)) for (a, b) in row] for row in S]
         kout = (k, kinv)
     out = np.array([[complex(float(a), float(b)) for (a, b) in row] for row in S])

@@ -145,13 +145,31 @@ int mxfft_roundtrip(mxfft_plan_t plan, const void *in, void *out, int batch,
                     void *stream);
 
 /*
+ * mxfft_roundtrip_fused -- the fused encode -> F -> F^-1 -> decode round trip
+ * of Sec. 4.3, a declared variant of mxfft_roundtrip: one prescale k of the
+ * input (Alg. 1), the forward transform (rows, then columns), the inverse
+ * applied directly to the forward result A (no unscale, no second prescale),
+ * columns first and then rows, and one scaling by 2^(-k - log2(n0 n1)).  Both
+ * column transforms of a tile run in one kernel on chip where the
+ * register-resident pass applies, so the call makes one statistics pass and
+ * three passes over the slice instead of two and four.  Same MX blocks as the
+ * separate transforms; the result differs from mxfft_roundtrip only through
+ * the inverse's axis order and the missing second prescale.  Arguments as for
+ * mxfft_roundtrip.  MXFFT_ERR_UNSUPPORTED for the FP16 control (its binary16
+ * products would overflow at the unscaled intermediate size).  k_out of
+ * mxfft_get_status: [batch], the one prescale exponent per slice.
+ */
+int mxfft_roundtrip_fused(mxfft_plan_t plan, const void *in, void *out, int batch,
+                          void *stream);
+
+/*
  * mxfft_get_status -- after the stream of the last call has been synchronised
  * (this function synchronises it), report what the device saw in that call.
  *   device_flags  nullable; receives bit 0 = some slice had a non-finite
  *                 magnitude (its k was forced to 0, its output is undefined).
  *   k_out         nullable; receives the prescale exponents of the last call:
- *                 [batch] for forward/inverse, [batch][2] (forward k, inverse
- *                 k) for the round trip.
+ *                 [batch] for forward / inverse / fused round trip,
+ *                 [batch][2] (forward k, inverse k) for the round trip.
  *                 bit 1 = a bounded wait of the tensor-core path gave up (its
  *                 output is undefined).
  * Returns MXFFT_ERR_NONFINITE when bit 0 is set, MXFFT_ERR_TIMEOUT when bit 1
@@ -223,7 +241,8 @@ int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, 
 typedef enum {
     MXFFT_OP_FORWARD = 0,
     MXFFT_OP_INVERSE = 1,
-    MXFFT_OP_ROUNDTRIP = 2
+    MXFFT_OP_ROUNDTRIP = 2,
+    MXFFT_OP_ROUNDTRIP_FUSED = 3   /* mxfft_roundtrip_fused */
 } mxfft_op;
 
 /* One work item: `slices` independent [n0][n1] slices (slices x coils of an

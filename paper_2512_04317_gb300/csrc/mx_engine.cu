@@ -9,8 +9,8 @@
 // table in device memory (SliceRef), so a group is one launch whatever the
 // addresses, and a captured graph stays valid when a later call passes other
 // buffers: only the table content changes.  Per slice the arithmetic is that
-// of mxfft_forward / mxfft_inverse / mxfft_roundtrip, so results are
-// bit-identical to them.
+// of mxfft_forward / mxfft_inverse / mxfft_roundtrip / mxfft_roundtrip_fused,
+// so results are bit-identical to them.
 #include <algorithm>
 #include <cstddef>
 #include <cstdio>
@@ -38,6 +38,7 @@ struct PassLaunch {
     int dim, dir, prologue, epilogue;
     int ref0, count;      // slice references [ref0, ref0 + count)
     int branch;           // fork branch within its stage
+    int fused = 0;        // 1: forward + inverse columns of the fused round trip
 };
 
 // Host image of one run: the device tables and the launches that read them.
@@ -132,7 +133,7 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb) {
 }
 
 bool item_ok(const mxfft_item& it) {
-    if (it.slices < 0 || it.op < 0 || it.op > 2 || it.reserved != 0) return false;
+    if (it.slices < 0 || it.op < 0 || it.op > 3 || it.reserved != 0) return false;
     if (it.slices == 0) return true;
     if (!it.in || !it.out || ((uintptr_t)it.in & 15u) || ((uintptr_t)it.out & 15u)) return false;
     const size_t bytes = (size_t)it.slices * it.n0 * it.n1 * sizeof(float2);
@@ -190,6 +191,8 @@ int build_layout(mxfft_engine_s* e, const mxfft_item* items, int n, Layout& L,
     std::string sig;
     for (int i = 0; i < n; i++) {
         if (items[i].slices == 0) continue;
+        if (items[i].op == MXFFT_OP_ROUNDTRIP_FUSED && items[i].format == MXFFT_FP16)
+            return MXFFT_ERR_UNSUPPORTED;
         int rc = get_plan(e, items[i], &item_plan[i]);
         if (rc) return rc;
         char b[128];
@@ -247,20 +250,25 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
                       kparams(item_plan[i]));
     }
     L.ncta1 = (int)L.ctas.size();
-    // stage 1 groups: (plan, direction) in order of first appearance
+    // stage 1 groups: (plan, kind) in order of first appearance; kind 0 forward
+    // (also the first half of a round trip), 1 inverse, 2 fused round trip
+    auto kind_of = [](int op) {
+        return op == MXFFT_OP_INVERSE ? 1 : (op == MXFFT_OP_ROUNDTRIP_FUSED ? 2 : 0);
+    };
     std::vector<std::pair<mxfft_plan_s*, int>> groups;
     for (int i = 0; i < n; i++) {
         if (items[i].slices == 0) continue;
-        const std::pair<mxfft_plan_s*, int> key(item_plan[i], items[i].op == MXFFT_OP_INVERSE ? 1 : 0);
+        const std::pair<mxfft_plan_s*, int> key(item_plan[i], kind_of(items[i].op));
         if (std::find(groups.begin(), groups.end(), key) == groups.end()) groups.push_back(key);
     }
     for (size_t gi = 0; gi < groups.size(); gi++) {
         mxfft_plan_s* p = groups[gi].first;
-        const int dir = groups[gi].second;
+        const int kind = groups[gi].second;
+        const int dir = kind == 1 ? 1 : 0;
         const int np = p->n0 * p->n1;
         const int rows0 = (int)L.refs.size();
         for (int i = 0; i < n; i++) {
-            if (item_plan[i] != p || (items[i].op == MXFFT_OP_INVERSE ? 1 : 0) != dir) continue;
+            if (item_plan[i] != p || kind_of(items[i].op) != kind) continue;
             for (int s = 0; s < items[i].slices; s++)
                 L.refs.push_back(SliceRef{(const float2*)items[i].in + (size_t)s * np,
                                           (float2*)items[i].out + (size_t)s * np,
@@ -274,7 +282,14 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
             L.refs.push_back(c);
         }
         L.stage1.push_back(PassLaunch{p, 1, dir, PRO_PRESCALE, EPI_RAW, rows0, count, (int)gi});
-        L.stage1.push_back(PassLaunch{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, (int)gi});
+        if (kind == 2) {
+            // fused round trip: columns forward + inverse, then the inverse rows
+            // with the one decode (2^(-k - log2(n0 n1)), k of the input)
+            L.stage1.push_back(PassLaunch{p, 0, 0, PRO_NONE, EPI_RAW, cols0, count, (int)gi, 1});
+            L.stage1.push_back(PassLaunch{p, 1, 1, PRO_NONE, EPI_RT_FINAL, cols0, count, (int)gi});
+        } else {
+            L.stage1.push_back(PassLaunch{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, (int)gi});
+        }
     }
     L.nbranch1 = (int)groups.size();
     // round trips: statistics of the forward outputs, then the inverse passes
@@ -346,7 +361,8 @@ cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, i
         a.ref = d_refs + pl.ref0;
         a.prologue = pl.prologue;
         a.epilogue = pl.epilogue;
-        err = timed_pass(pl.p, a, pl.count, nf > 1 ? e->fork[pl.branch % nf] : s);
+        cudaStream_t bs = nf > 1 ? e->fork[pl.branch % nf] : s;
+        err = pl.fused ? fused_cols_pass(pl.p, a, pl.count, bs) : timed_pass(pl.p, a, pl.count, bs);
     }
     if (nf > 1) {
         // join

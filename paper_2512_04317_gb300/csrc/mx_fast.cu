@@ -1,5 +1,6 @@
 // Dispatch of the register-resident MX pass by element format and block size.
 #include <algorithm>
+#include <cstring>
 
 #include "mx_fast_kernel.cuh"
 
@@ -43,13 +44,20 @@ int fast_ng_candidates(int n, int other, int* out, int max) {
     return c;
 }
 
-cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
-                                int ng, cudaStream_t s) {
+namespace {
+cudaError_t launch_fast(const PassArgs& a, const uint32_t* twh, const TwA& twa,
+                        const uint32_t* twh2, const TwA* twa2, int batch, int ng, cudaStream_t s) {
     if (!fast_pass_supported(a)) return cudaErrorNotSupported;
     fast::FastArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
     fa.a = a;
     fa.twa = twa;
     fa.twh = twh;
+    if (twa2) {
+        fa.fused = 1;
+        fa.twa2 = *twa2;
+        fa.twh2 = twh2;
+    }
     int threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
     fast::fast_geometry(a.n, other, &fa.TG, &fa.S, &fa.NG, &threads);
@@ -71,10 +79,23 @@ cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const Tw
         default: return cudaErrorNotSupported;
     }
 }
+}  // namespace
+
+cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
+                                int ng, cudaStream_t s) {
+    return launch_fast(a, twh, twa, nullptr, nullptr, batch, ng, s);
+}
 
 cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                              cudaStream_t s) {
-    return launch_fast_pass_ng(a, twh, twa, batch, 0, s);
+    return launch_fast(a, twh, twa, nullptr, nullptr, batch, 0, s);
+}
+
+cudaError_t launch_fast_pass_fused(const PassArgs& a, const uint32_t* twh, const TwA& twa,
+                                   const uint32_t* twh_inv, const TwA& twa_inv, int batch,
+                                   cudaStream_t s) {
+    if (a.dim != 0) return cudaErrorInvalidValue;
+    return launch_fast(a, twh, twa, twh_inv, &twa_inv, batch, 0, s);
 }
 
 }  // namespace mxfft

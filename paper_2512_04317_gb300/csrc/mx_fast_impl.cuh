@@ -235,6 +235,9 @@ struct FastArgs {
     int lgTG;              // log2(TG)
     int S;                 // shared row stride (complex) of a group: TG or TG + 1
     int NG;                // groups per CTA
+    int fused;             // 1: columns forward then inverse (fused round trip)
+    TwA twa2;              // inverse twiddles of the fused launch (as twa / twh)
+    const uint32_t* twh2;
 };
 
 }  // namespace fast

@@ -17,7 +17,73 @@ __device__ __forceinline__ float2 epi_value(float2 v, int mode, float post) {
     return v;
 }
 
-template <int FMT, int LOGM, int DIM>
+// All stages of one transform per thread slot: phase A on the 32 elements in
+// r (bit-reversed chunk order), then phase B through shared memory.  Returns
+// with the last stage's results in R, element e0[q] + i in R[q][i] (natural
+// order), and the group's shared rows holding an earlier stage.
+template <int FMT, int LOGM>
+__device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], int (&e0)[4],
+                                           float2* __restrict__ Gs, const TwA& twa,
+                                           const uint32_t* __restrict__ twh,
+                                           const int8_t* __restrict__ tws, int L, int S, int TG,
+                                           int sigma, int tau, int s, const FmtParams& fp) {
+    // ---- phase A: stages h = 1..16 inside the chunk -------------------------
+    stage_a<FMT, LOGM, 1>(r, twa, fp);
+    stage_a<FMT, LOGM, 2>(r, twa, fp);
+    stage_a<FMT, LOGM, 4>(r, twa, fp);
+    stage_a<FMT, LOGM, 8>(r, twa, fp);
+    stage_a<FMT, LOGM, 16>(r, twa, fp);
+#pragma unroll
+    for (int t = 0; t < 32; t++) Gs[(32 * sigma + t) * S + tau] = r[t];
+    __syncthreads();
+
+    // ---- phase B: stage pairs (h, 2h), an odd last stage alone ---------------
+    const unsigned red = (unsigned)TG;           // lane of the partner run (slot ^ 1)
+    int ast = 5;
+    while (true) {
+        const int h = 1 << ast;
+        const bool two = ast + 1 < L;
+        int jA, jB, jC, jD;
+        if (two) {
+            const int Gi = sigma >> (ast - 3), rr = sigma & ((h >> 3) - 1);
+            const int base = 4 * h * Gi + 8 * rr;
+#pragma unroll
+            for (int q = 0; q < 4; q++) e0[q] = base + q * h;
+            jA = jB = 8 * rr;
+            jC = 8 * rr;
+            jD = h + 8 * rr;
+        } else {
+            e0[0] = 8 * sigma;
+            e0[1] = 8 * sigma + h;
+            e0[2] = 8 * (sigma + s);
+            e0[3] = 8 * (sigma + s) + h;
+            jA = 8 * sigma;
+            jB = 8 * (sigma + s);
+            jC = jD = 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) R[q][i] = Gs[(e0[q] + i) * S + tau];
+        stage_b8<FMT, LOGM>(R[0], R[1], twh + h, tws + h - 1, jA, red, fp);
+        stage_b8<FMT, LOGM>(R[2], R[3], twh + h, tws + h - 1, jB, red, fp);
+        if (two) {
+            stage_b8<FMT, LOGM>(R[0], R[2], twh + 2 * h, tws + 2 * h - 1, jC, red, fp);
+            stage_b8<FMT, LOGM>(R[1], R[3], twh + 2 * h, tws + 2 * h - 1, jD, red, fp);
+        }
+        ast += two ? 2 : 1;
+        if (ast >= L) break;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
+        __syncthreads();
+    }
+}
+
+// FUSED (columns only): forward, then inverse columns of the fused round trip
+// (reading C17) in one launch.
+template <int FMT, int LOGM, int DIM, bool FUSED>
 __global__ void __launch_bounds__(kMaxThreads)
 fast_pass_kernel(const FastArgs fa) {
     extern __shared__ float2 sm[];
@@ -91,59 +157,22 @@ fast_pass_kernel(const FastArgs fa) {
         __syncthreads();
     }
 
-    // ---- phase A: stages h = 1..16 inside the chunk -------------------------
-    stage_a<FMT, LOGM, 1>(r, fa.twa, fp);
-    stage_a<FMT, LOGM, 2>(r, fa.twa, fp);
-    stage_a<FMT, LOGM, 4>(r, fa.twa, fp);
-    stage_a<FMT, LOGM, 8>(r, fa.twa, fp);
-    stage_a<FMT, LOGM, 16>(r, fa.twa, fp);
-#pragma unroll
-    for (int t = 0; t < 32; t++) Gs[(32 * sigma + t) * S + tau] = r[t];
-    __syncthreads();
-
-    // ---- phase B: stage pairs (h, 2h), an odd last stage alone ---------------
-    const unsigned red = (unsigned)TG;           // lane of the partner run (slot ^ 1)
     float2 R[4][8];
     int e0[4];
-    int ast = 5;
-    while (true) {
-        const int h = 1 << ast;
-        const bool two = ast + 1 < L;
-        int jA, jB, jC, jD;
-        if (two) {
-            const int Gi = sigma >> (ast - 3), rr = sigma & ((h >> 3) - 1);
-            const int base = 4 * h * Gi + 8 * rr;
-#pragma unroll
-            for (int q = 0; q < 4; q++) e0[q] = base + q * h;
-            jA = jB = 8 * rr;
-            jC = 8 * rr;
-            jD = h + 8 * rr;
-        } else {
-            e0[0] = 8 * sigma;
-            e0[1] = 8 * sigma + h;
-            e0[2] = 8 * (sigma + s);
-            e0[3] = 8 * (sigma + s) + h;
-            jA = 8 * sigma;
-            jB = 8 * (sigma + s);
-            jC = jD = 0;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-#pragma unroll
-            for (int i = 0; i < 8; i++) R[q][i] = Gs[(e0[q] + i) * S + tau];
-        stage_b8<FMT, LOGM>(R[0], R[1], fa.twh + h, a.tws + h - 1, jA, red, fp);
-        stage_b8<FMT, LOGM>(R[2], R[3], fa.twh + h, a.tws + h - 1, jB, red, fp);
-        if (two) {
-            stage_b8<FMT, LOGM>(R[0], R[2], fa.twh + 2 * h, a.tws + 2 * h - 1, jC, red, fp);
-            stage_b8<FMT, LOGM>(R[1], R[3], fa.twh + 2 * h, a.tws + 2 * h - 1, jD, red, fp);
-        }
-        ast += two ? 2 : 1;
-        if (ast >= L) break;
+    all_stages<FMT, LOGM>(r, R, e0, Gs, fa.twa, fa.twh, a.tws, L, S, TG, sigma, tau, s, fp);
+    if (FUSED) {
+        // the fused round trip's inverse columns on the same tile: the forward
+        // result back to shared memory, gathered in bit-reversed chunk order
+        // (as the row load does), then every stage with the inverse twiddles
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
         __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 32; j++) r[rev5(j)] = Gs[(rc + j * s) * S + tau];
+        __syncthreads();
+        all_stages<FMT, LOGM>(r, R, e0, Gs, fa.twa2, fa.twh2, a.tws, L, S, TG, sigma, tau, s, fp);
     }
 
     // ---- output in natural order ---------------------------------------------
@@ -195,16 +224,16 @@ inline bool fast_geometry(int n, int other, int* TG, int* S, int* NG, int* threa
     return *threads <= kMaxThreads;
 }
 
-template <int FMT, int DIM>
+template <int FMT, int DIM, bool FUSED>
 cudaError_t launch_fast_dim(const FastArgs& fa, int logm, int blocks, int threads, size_t smem,
                             cudaStream_t s) {
     void (*k)(const FastArgs) = nullptr;
     switch (logm) {
-        case 0: k = fast_pass_kernel<FMT, 0, DIM>; break;
-        case 1: k = fast_pass_kernel<FMT, 1, DIM>; break;
-        case 2: k = fast_pass_kernel<FMT, 2, DIM>; break;
-        case 3: k = fast_pass_kernel<FMT, 3, DIM>; break;
-        case 4: k = fast_pass_kernel<FMT, 4, DIM>; break;
+        case 0: k = fast_pass_kernel<FMT, 0, DIM, FUSED>; break;
+        case 1: k = fast_pass_kernel<FMT, 1, DIM, FUSED>; break;
+        case 2: k = fast_pass_kernel<FMT, 2, DIM, FUSED>; break;
+        case 3: k = fast_pass_kernel<FMT, 3, DIM, FUSED>; break;
+        case 4: k = fast_pass_kernel<FMT, 4, DIM, FUSED>; break;
         default: return cudaErrorNotSupported;
     }
     // raise the opt-in limit only (never lower it): launches captured earlier
@@ -226,8 +255,12 @@ cudaError_t launch_fast_fmt(const FastArgs& fa, int logm, int batch, cudaStream_
     const int threads = fa.TG * (a.n / 32) * fa.NG;
     const int blocks = batch * (other / (fa.TG * fa.NG));
     const size_t smem = (size_t)fa.NG * a.n * fa.S * sizeof(float2);
-    return a.dim == 1 ? launch_fast_dim<FMT, 1>(fa, logm, blocks, threads, smem, s)
-                      : launch_fast_dim<FMT, 0>(fa, logm, blocks, threads, smem, s);
+    if (fa.fused) {
+        if (a.dim != 0) return cudaErrorInvalidValue;
+        return launch_fast_dim<FMT, 0, true>(fa, logm, blocks, threads, smem, s);
+    }
+    return a.dim == 1 ? launch_fast_dim<FMT, 1, false>(fa, logm, blocks, threads, smem, s)
+                      : launch_fast_dim<FMT, 0, false>(fa, logm, blocks, threads, smem, s);
 }
 
 }  // namespace fast

@@ -127,6 +127,11 @@ cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s);
 bool fast_pass_supported(const PassArgs& a);
 cudaError_t launch_fast_pass(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                              cudaStream_t s);
+// Forward then inverse columns of the fused round trip in one launch (dim 0,
+// forward twiddles in twh / twa, inverse in twh_inv / twa_inv).
+cudaError_t launch_fast_pass_fused(const PassArgs& a, const uint32_t* twh, const TwA& twa,
+                                   const uint32_t* twh_inv, const TwA& twa_inv, int batch,
+                                   cudaStream_t s);
 // The root-sum-of-squares coil combine of one item: images x coils consecutive
 // complex slices of npts points -> images real slices (mx_rss.cu).
 struct RssRef {

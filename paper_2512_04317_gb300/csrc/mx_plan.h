@@ -55,6 +55,7 @@ KParams kparams(const mxfft_plan_s* p);
 PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out);
 // Launch one pass over batch slices with the plan's kernel choice.
 cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s);
+cudaError_t fused_cols_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s);
 // Copy the per-slice "non-finite input" flags of an engine's last run to
 // pinned host memory, asynchronously on s (mx_engine.cu).
 cudaError_t engine_flags_async(mxfft_engine_t e, uint32_t* h_flags, cudaStream_t s);

@@ -290,10 +290,11 @@ int mxfft_server_create(const mxfft_server_config* cfg, mxfft_server_t* out) {
 int mxfft_server_submit(mxfft_server_t S, const mxfft_request* r) {
     if (!S || !r) return MXFFT_ERR_INVALID;
     if (!pow2_in(r->n0, 2, 2048) || !pow2_in(r->n1, 2, 2048) || r->format < 0 || r->format > MXFFT_FP16 ||
-        !pow2_in(r->k, 2, 128) || r->op < 0 || r->op > 2 || r->slices < 1 || !r->host_in ||
+        !pow2_in(r->k, 2, 128) || r->op < 0 || r->op > 3 || r->slices < 1 || !r->host_in ||
         r->reserved != 0 || (!r->host_out && !r->host_rss))
         return MXFFT_ERR_INVALID;
     if (r->host_rss && (r->coils < 1 || r->slices % r->coils)) return MXFFT_ERR_INVALID;
+    if (r->op == MXFFT_OP_ROUNDTRIP_FUSED && r->format == MXFFT_FP16) return MXFFT_ERR_UNSUPPORTED;
     SReq q;
     q.r = *r;
     q.bytes = (size_t)r->slices * r->n0 * r->n1 * sizeof(float2);

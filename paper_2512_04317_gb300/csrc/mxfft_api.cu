@@ -290,9 +290,10 @@ void prof_clear(mxfft_plan_s* p) {
     p->recs->clear();
 }
 
-// op: 0 forward, 1 inverse, 2 round trip
+// op: 0 forward, 1 inverse, 2 round trip, 3 fused round trip
 int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int op) {
     if (!p || batch < 0) return MXFFT_ERR_INVALID;
+    if (op == 3 && p->fmt == MXFFT_FP16) return MXFFT_ERR_UNSUPPORTED;
     if (batch == 0) return MXFFT_OK;
     if (!in || !out || !aligned16(in) || !aligned16(out)) return MXFFT_ERR_INVALID;
     const size_t bytes = (size_t)batch * p->n0 * p->n1 * sizeof(float2);
@@ -326,8 +327,19 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
     PassArgs cols = pass_args(p, 0, dir0, y, y);
     cols.st = st_f;
     cols.prologue = PRO_NONE;
-    cols.epilogue = EPI_UNSCALE;
-    if ((e = timed_pass(p, cols, batch, s)) != cudaSuccess) return cuda_status(e);
+    cols.epilogue = op == 3 ? EPI_RAW : EPI_UNSCALE;
+    if (op == 3) {
+        // fused round trip (reading C17): forward and inverse columns on the
+        // undecoded forward result, then the inverse rows with the one decode
+        if ((e = fused_cols_pass(p, cols, batch, s)) != cudaSuccess) return cuda_status(e);
+        PassArgs r2 = pass_args(p, 1, 1, y, y);
+        r2.st = st_f;
+        r2.prologue = PRO_NONE;
+        r2.epilogue = EPI_RT_FINAL;
+        if ((e = timed_pass(p, r2, batch, s)) != cudaSuccess) return cuda_status(e);
+    } else if ((e = timed_pass(p, cols, batch, s)) != cudaSuccess) {
+        return cuda_status(e);
+    }
     if (op == 2) {
         // the inverse's own prescale statistics, on the forward output y
         ProfRec* rs = prof_begin(p, 0, s);
@@ -435,6 +447,25 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
                          : launch_pass(a, batch, s);
     prof_end(r, s);
     return e;
+}
+
+// Forward then inverse column transforms of the fused round trip on the same
+// slices (a: columns, forward twiddles, no prologue, raw epilogue): one
+// register-resident launch that keeps each tile on chip between the two where
+// that kernel applies, else the two passes one after the other (same results).
+cudaError_t fused_cols_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
+    if (p->path != 1 && !p->force_generic && fast_pass_supported(a)) {
+        ProfRec* r = prof_begin(p, 2, s);
+        cudaError_t e = launch_fast_pass_fused(a, p->d_twh[0][0], p->twa[0][0], p->d_twh[0][1],
+                                               p->twa[0][1], batch, s);
+        prof_end(r, s);
+        return e;
+    }
+    cudaError_t e = timed_pass(p, a, batch, s);
+    if (e != cudaSuccess) return e;
+    PassArgs b = a;
+    b.tw = p->d_tw[0][1];
+    return timed_pass(p, b, batch, s);
 }
 
 }  // namespace mxfft
@@ -580,6 +611,10 @@ int mxfft_inverse(mxfft_plan_t p, const void* in, void* out, int batch, void* st
 
 int mxfft_roundtrip(mxfft_plan_t p, const void* in, void* out, int batch, void* stream) {
     return run(p, in, out, batch, stream, 2);
+}
+
+int mxfft_roundtrip_fused(mxfft_plan_t p, const void* in, void* out, int batch, void* stream) {
+    return run(p, in, out, batch, stream, 3);
 }
 
 int mxfft_get_status(mxfft_plan_t p, int* device_flags, int32_t* k_out) {

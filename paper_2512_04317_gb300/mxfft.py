@@ -24,12 +24,12 @@ MXFFT_ERR_TIMEOUT = 6
 FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
 OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL = 0, 1, 2, 3, 4, 5
 
-OPS = {"forward": 0, "inverse": 1, "roundtrip": 2}
+OPS = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}
 ENGINE_GRAPHS, ENGINE_TC16 = 1, 2
 
 # every symbol include/mxfft.h declares
 EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
-           "mxfft_roundtrip", "mxfft_get_status", "mxfft_destroy", "mxfft_profile",
+           "mxfft_roundtrip", "mxfft_roundtrip_fused", "mxfft_get_status", "mxfft_destroy", "mxfft_profile",
            "mxfft_profile_read", "mxfft_prescale_exponents_noalloc",
            "mxfft_engine_create", "mxfft_engine_run", "mxfft_engine_get_status",
            "mxfft_engine_destroy", "mxfft_tune", "mxfft_tune_save", "mxfft_tune_load",
@@ -96,7 +96,7 @@ def load(path: str | None = None):
         P, I, F, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
         lib.mxfft_plan.argtypes = [I, I, I, I, F, F, ctypes.POINTER(P)]
         lib.mxfft_set_option.argtypes = [P, I, D]
-        for name in ("mxfft_forward", "mxfft_inverse", "mxfft_roundtrip"):
+        for name in ("mxfft_forward", "mxfft_inverse", "mxfft_roundtrip", "mxfft_roundtrip_fused"):
             getattr(lib, name).argtypes = [P, P, P, I, P]
         lib.mxfft_get_status.argtypes = [P, P, P]
         lib.mxfft_destroy.argtypes = [P]
@@ -167,6 +167,10 @@ def mxfft_inverse(plan, in_ptr, out_ptr, batch, stream=None):
 
 def mxfft_roundtrip(plan, in_ptr, out_ptr, batch, stream=None):
     _call("mxfft_roundtrip", plan, in_ptr, out_ptr, batch, stream)
+
+
+def mxfft_roundtrip_fused(plan, in_ptr, out_ptr, batch, stream=None):
+    _call("mxfft_roundtrip_fused", plan, in_ptr, out_ptr, batch, stream)
 
 
 def mxfft_get_status(plan, k_count: int = 0):
@@ -389,6 +393,10 @@ class Plan:
 
     def roundtrip(self, x, out=None):
         return self._run("mxfft_roundtrip", x, out)
+
+    def roundtrip_fused(self, x, out=None):
+        """The fused encode -> F -> F^-1 -> decode round trip (one prescale)."""
+        return self._run("mxfft_roundtrip_fused", x, out)
 
     def status(self):
         """(status, device_flags, k) of the last call; k is [batch] or [batch][2]."""

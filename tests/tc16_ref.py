@@ -134,6 +134,14 @@ def mxfft2d(x, fmt="e4m3", op="forward", k=32):
         elif op == "inverse":
             y, ke = transform(s, +1)
             res[i] = y * np.float32(2.0 ** -ke)
+        elif op == "roundtrip_fused":
+            # one prescale; the inverse on the undecoded forward result,
+            # columns first, then rows; one decode
+            y, ke = transform(s, -1)
+            z = np.swapaxes(fft1d(np.swapaxes(y, 0, 1).copy(), fmt, +1, g), 0, 1)
+            z = fft1d(z, fmt, +1, g)
+            lg = int(np.log2(s.shape[0] * s.shape[1]))
+            res[i] = z * np.float32(2.0 ** (-ke - lg))
         else:
             y, ke = transform(s, -1)
             y = (y * np.float32(2.0 ** -ke)).astype(np.complex64)

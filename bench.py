@@ -495,8 +495,13 @@ def accuracy(plan, xk, xi, torch):
         rms = float(torch.sqrt(torch.mean(err ** 2)))
         return 20.0 * float(torch.log10(r.abs().max() / rms))
     xi64 = xi.to(torch.complex128)
-    return {"forward_nrmse": nrmse(y, ref), "forward_psnr_db": psnr(y, ref),
-            "roundtrip_nrmse": nrmse(z, xi64), "roundtrip_psnr_db": psnr(z, xi64)}
+    out = {"forward_nrmse": nrmse(y, ref), "forward_psnr_db": psnr(y, ref),
+           "roundtrip_nrmse": nrmse(z, xi64), "roundtrip_psnr_db": psnr(z, xi64)}
+    if plan.fmt != "fp16":
+        f = plan.roundtrip_fused(xi)
+        out.update({"roundtrip_fused_nrmse": nrmse(f, xi64),
+                    "roundtrip_fused_psnr_db": psnr(f, xi64)})
+    return out
 
 
 def main():
@@ -584,6 +589,34 @@ def main():
     t_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evs), world, dist, dev)
     ms_per_step = t_ms / args.steps
     value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, t_ms)
+
+    # ---- the same step with the fused round trip (Sec. 4.3 variant: one
+    # prescale, both column transforms of a tile in one launch, no second
+    # statistics pass), timed the same way -----------------------------------
+    fused = None
+    if engine is not None and w["fmt"] != "fp16":
+        yf = torch.empty_like(xi)
+        work_f = [("forward", xk, yk, w["fmt"], w["k"]),
+                  ("roundtrip_fused", xi, yf, w["fmt"], w["k"])]
+        for _ in range(args.warmup):
+            engine.run(work_f)
+        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        barrier()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            evf[i][0].record(stream)
+            engine.run(work_f)
+            evf[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        tf_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evf), world, dist, dev)
+        fused = {"value": job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, tf_ms),
+                 "unit": "Mpts/s", "ms_per_step": tf_ms / args.steps,
+                 "speedup_vs_separate_round_trip": ms_per_step / (tf_ms / args.steps),
+                 "launches_per_step": 6,
+                 "step": "forward of the k-space batch + fused round trip of the image batch"}
 
     # ---- per-kernel device time (event pairs around each launch on the launch
     # stream; the same kernels through the plan calls, since launches inside a
@@ -759,6 +792,7 @@ def main():
             "clocks": clk,
             "wall_s_timed_region": wall,
             "engine_equals_plan_calls": same,
+            "fused_roundtrip_variant": fused,
             "rss_image_accuracy_vs_fp64": rss_acc,
             "serving": serving,
         }

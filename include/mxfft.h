@@ -81,7 +81,7 @@ typedef enum {
                                block of 2 / 4 consecutive vectors of a transform; other k
                                MXFFT_ERR_UNSUPPORTED), MX-quantised twiddles between the
                                radix-16 stages; approximate, not bit-exact.
-                               Needs n0, n1 in {256, 512, 1024} and format E4M3 or E5M2, else
+                               Needs n0, n1 in {256, 512, 1024, 2048} and format E4M3 or E5M2, else
                                MXFFT_ERR_UNSUPPORTED. */,
     MXFFT_OPT_TEST_STALL = 5  /* test hook of the bounded wait, 0 or 1; default 0.  1: the
                                tensor-core pass withholds its matrix products, so every CTA's

@@ -1,14 +1,16 @@
 // Tensor-core variant of the MX pass: radix-16 sub-DFTs as MXFP8 matrix
 // products on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulation
-// in tensor memory), for transform lengths n = 256 r, r in {1, 2, 4}.
+// in tensor memory), for transform lengths n = 256 r, r in {1, 2, 4, 8}.
 //
 // Decomposition (four-step, rows of a transform viewed as 16 x M, M = 16 r):
 //   j = M j1 + j2, k = k1 + 16 k2
 //   A : Y[k1][j2] = W_n^(j2 k1) * DFT16_j1(x[M j1 + j2])[k1]
 //   C1: for each k1, 16-point DFTs over j21 of Y[k1][r j21 + j22] (j22 < r),
 //       times W_M^(j22 k21) when r > 1
-//   C2: r-point DFT over j22 (r = 2: a sum and a difference; r = 4: radix 4
-//       with W_4 = -+i; FP32, every twiddle of this stage exact)
+//   C2: r-point DFT over j22 in FP32 (r = 2: a sum and a difference; r = 4:
+//       radix 4 with W_4 = -+i, exact; r = 8: radix 2 x radix 4, the odd
+//       half times W_8^k, whose (1 -+ i) / sqrt(2) factors use sqrt(1/2)
+//       rounded to FP32)
 //   X[k1 + 16 (k21 + 16 k22)]
 // Every 16-point input vector (32 reals) is one MX block for k = 32 (for k =
 // 64 / 128 a block is 2 / 4 consecutive vectors of a transform): shared
@@ -51,9 +53,9 @@ constexpr uint64_t kWaitNs = 100000000;   // bound of one completion wait: 100 m
 // reads of 8 consecutive rows hit distinct banks), then the two tile buffers.
 constexpr int kTwRow = 18;
 constexpr int kOffB = 8192;
-constexpr int kOffTwA = kOffB + 1024;                  // up to 64 rows
-constexpr int kOffTwC = kOffTwA + 64 * kTwRow * 8;     // up to 4 rows
-constexpr int kOffBuf = kOffTwC + 4 * kTwRow * 8;
+constexpr int kOffTwA = kOffB + 1024;                  // up to 128 rows
+constexpr int kOffTwC = kOffTwA + 128 * kTwRow * 8;    // up to 8 rows
+constexpr int kOffBuf = kOffTwC + 8 * kTwRow * 8;
 static_assert(kOffBuf % 16 == 0, "16-byte aligned cp.async destinations");
 
 using Args = Tc16Args;
@@ -62,14 +64,14 @@ using Args = Tc16Args;
 template <int LOGN>
 struct Geo {
     static constexpr int n = 1 << LOGN;
-    static constexpr int r = n / 256;               // 1, 2, 4
-    static constexpr int LGR = r == 1 ? 0 : (r == 2 ? 1 : 2);
+    static constexpr int r = n / 256;               // 1, 2, 4, 8
+    static constexpr int LGR = r == 1 ? 0 : (r == 2 ? 1 : (r == 4 ? 2 : 3));
     static constexpr int M = 16 * r;
     static constexpr int LGM = 4 + LGR;
-    static constexpr int T = kTilePts / n;          // transforms per tile (16, 8, 4)
-    static constexpr int LGT = T == 16 ? 4 : (T == 8 ? 3 : 2);
+    static constexpr int T = kTilePts / n;          // transforms per tile (16, 8, 4, 2)
+    static constexpr int LGT = T == 16 ? 4 : (T == 8 ? 3 : (T == 4 ? 2 : 1));
     // rows pass: [t][e], PADR pad slots after every M elements
-    static constexpr int PADR = r == 4 ? 4 : 2;
+    static constexpr int PADR = r == 8 ? 8 : (r == 4 ? 4 : 2);
     static constexpr int TS = n + PADR * (n / M);
     static constexpr int ROW_SLOTS = T * TS;
     // columns pass: [e][t]; with T < 16, T pad slots after every 16 elements
@@ -82,9 +84,10 @@ struct Geo {
 // consecutive elements per half-warp; round C1 reads each thread's own group
 // of M elements as 16-byte pairs (r = 1: chunks 9 k1 + c, distinct mod 8 over
 // a quarter-warp) or 8-byte elements (r = 2: slots 34 k1 + 2 j + j22; r = 4:
-// 68 k1 + 4 j + j22; distinct mod 16 over a half-warp).  Columns pass: a
-// half-warp spans 16 transforms (T = 16) or T transforms x 16 / T elements
-// whose pads put them in distinct bank groups (T = 8, 4).  Every pattern was
+// 68 k1 + 4 j + j22; r = 8: 136 k1 + 8 j + j22; distinct mod 16 over a
+// half-warp).  Columns pass: a half-warp spans 16 transforms (T = 16) or T
+// transforms x 16 / T elements whose pads put them in distinct bank groups
+// (T = 8, 4, 2).  Every pattern was
 // checked for bank conflicts by enumerating its addresses.
 template <int LOGN>
 __device__ __forceinline__ int slot_row(int t, int e) {
@@ -555,6 +558,83 @@ tc16_pass_kernel(const Args a) {
             // the buffer is refilled by the next iteration's prefetch
             if (__syncthreads_or(!mm.ok)) break;
         }
+        if (r == 8) {
+            // ---- C2: radix 8 over j22 = radix 4 on the even and the odd
+            // inputs, then X[k] = E[k] + W_8^k O[k], X[k + 4] = E[k] - W_8^k O[k]
+            const float sg = a.inv ? 1.0f : -1.0f;         // W_8 = (1 + sg i) / sqrt(2)
+            const float c8 = 0.70710678118654752f;          // sqrt(1/2), rounded to FP32
+#pragma unroll 1
+            for (int i = 0; i < 2; i++) {
+                const int u = tid + i * kThreads;       // (t, k1, k21), T x 16 x 16
+                int t, k1, k21;
+                if (DIM == 1) { k1 = u & 15; k21 = (u >> 4) & 15; t = u >> 8; }
+                else { t = u & 1; k21 = 2 * ((u >> 1) & 7) + (u >> 8); k1 = (u >> 4) & 15; }
+                const int e = M * k1 + 8 * k21;
+                float2 U[8];
+                if (DIM == 1) {
+                    // four 16-byte reads; a lane reads its chunks in the order
+                    // c ^ x, x = (k1 >> 1) & 3, so a quarter-warp covers 8
+                    // distinct chunks, then undoes the permutation
+                    const float4* q = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, e));
+                    const int x = (k1 >> 1) & 3;
+                    float4 f[4];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) f[c] = q[c ^ x];
+                    if (x & 1) {
+                        float4 s0 = f[0]; f[0] = f[1]; f[1] = s0;
+                        float4 s2 = f[2]; f[2] = f[3]; f[3] = s2;
+                    }
+                    if (x & 2) {
+                        float4 s0 = f[0]; f[0] = f[2]; f[2] = s0;
+                        float4 s1 = f[1]; f[1] = f[3]; f[3] = s1;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        U[2 * c] = make_float2(f[c].x, f[c].y);
+                        U[2 * c + 1] = make_float2(f[c].z, f[c].w);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; j++) U[j] = d[slot_col<LOGN>(t, e + j)];
+                }
+                float2 E[4], O[4];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const float2 x0 = U[h], x1 = U[h + 2], x2 = U[h + 4], x3 = U[h + 6];
+                    const float2 a0 = make_float2(__fadd_rn(x0.x, x2.x), __fadd_rn(x0.y, x2.y));
+                    const float2 a1 = make_float2(__fsub_rn(x0.x, x2.x), __fsub_rn(x0.y, x2.y));
+                    const float2 b0 = make_float2(__fadd_rn(x1.x, x3.x), __fadd_rn(x1.y, x3.y));
+                    const float2 b1 = make_float2(__fsub_rn(x1.x, x3.x), __fsub_rn(x1.y, x3.y));
+                    const float2 wb = make_float2(-sg * b1.y, sg * b1.x);     // W_4 b1, exact
+                    float2* R = h == 0 ? E : O;
+                    R[0] = make_float2(__fadd_rn(a0.x, b0.x), __fadd_rn(a0.y, b0.y));
+                    R[1] = make_float2(__fadd_rn(a1.x, wb.x), __fadd_rn(a1.y, wb.y));
+                    R[2] = make_float2(__fsub_rn(a0.x, b0.x), __fsub_rn(a0.y, b0.y));
+                    R[3] = make_float2(__fsub_rn(a1.x, wb.x), __fsub_rn(a1.y, wb.y));
+                }
+                // W_8^k O[k]: k = 1 (1 + sg i) / sqrt 2, k = 2 sg i (exact),
+                // k = 3 (-1 + sg i) / sqrt 2
+                float2 P[4];
+                P[0] = O[0];
+                P[1] = make_float2(__fmul_rn(__fsub_rn(O[1].x, sg * O[1].y), c8),
+                                   __fmul_rn(__fadd_rn(O[1].y, sg * O[1].x), c8));
+                P[2] = make_float2(-sg * O[2].y, sg * O[2].x);
+                P[3] = make_float2(-__fmul_rn(__fadd_rn(O[3].x, sg * O[3].y), c8),
+                                   __fmul_rn(__fsub_rn(sg * O[3].x, O[3].y), c8));
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const int k4 = k & 3;
+                    float2 X = k < 4 ? make_float2(__fadd_rn(E[k4].x, P[k4].x), __fadd_rn(E[k4].y, P[k4].y))
+                                     : make_float2(__fsub_rn(E[k4].x, P[k4].x), __fsub_rn(E[k4].y, P[k4].y));
+                    if (scale_out) X = scale2(X, post);
+                    const int eo = k1 + 16 * k21 + 256 * k;
+                    if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + eo] = X;
+                    else out[(size_t)eo * a.n1 + t0 + t] = X;
+                }
+            }
+            // the buffer is refilled by the next iteration's prefetch
+            if (__syncthreads_or(!mm.ok)) break;
+        }
         if (r == 2) {
             // ---- C2: radix-2 over j22: X[k1 + 16 (k21 + 16 k22)] ----------
 #pragma unroll 2
@@ -637,14 +717,15 @@ template <int FMT>
 cudaError_t launch_fmt(const Args& a, cudaStream_t s) {
     if (a.n == 256) return a.dim == 1 ? launch_one<FMT, 1, 8>(a, s) : launch_one<FMT, 0, 8>(a, s);
     if (a.n == 512) return a.dim == 1 ? launch_one<FMT, 1, 9>(a, s) : launch_one<FMT, 0, 9>(a, s);
-    return a.dim == 1 ? launch_one<FMT, 1, 10>(a, s) : launch_one<FMT, 0, 10>(a, s);
+    if (a.n == 1024) return a.dim == 1 ? launch_one<FMT, 1, 10>(a, s) : launch_one<FMT, 0, 10>(a, s);
+    return a.dim == 1 ? launch_one<FMT, 1, 11>(a, s) : launch_one<FMT, 0, 11>(a, s);
 }
 
 }  // namespace tc16
 
 bool tc16_supported(int n, int other, int fmt) {
-    // n = 256 r (r = 1, 2, 4), 8-bit element formats, whole tiles of 4096 / n transforms
-    if (n != 256 && n != 512 && n != 1024) return false;
+    // n = 256 r (r = 1, 2, 4, 8), 8-bit element formats, whole tiles of 4096 / n transforms
+    if (n != 256 && n != 512 && n != 1024 && n != 2048) return false;
     const int T = tc16::kTilePts / n;
     return other >= T && other % T == 0 && (fmt == 0 || fmt == 1);
 }

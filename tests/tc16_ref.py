@@ -80,7 +80,7 @@ def cmul32(w, y):
 
 
 def fft1d(x, fmt, sgn, g=1):
-    """x: complex64 [..., n], n in {256, 512, 1024}; transforms the last axis."""
+    """x: complex64 [..., n], n in {256, 512, 1024, 2048}; transforms the last axis."""
     n = x.shape[-1]
     r = n // 256
     M = 16 * r
@@ -97,6 +97,31 @@ def fft1d(x, fmt, sgn, g=1):
     U = dft16_mx(np.swapaxes(Yr, -1, -2), fmt, sgn, g, 2)   # [k1][j22][k21]
     TC = np.stack([twiddle_block(j22, M, sgn, fmt) for j22 in range(r)])   # [j22][k21]
     U = cmul32(TC, U)
+    if r == 8:
+        # radix 4 on the even and the odd j22, then the odd half times W_8^k
+        # (sqrt(1/2) rounded to FP32); the same operations as the kernel
+        f32 = np.float32
+        sg = f32(sgn)
+
+        def radix4(x0, x1, x2, x3):
+            a0, a1 = (x0 + x2).astype(np.complex64), (x0 - x2).astype(np.complex64)
+            b0, b1 = (x1 + x3).astype(np.complex64), (x1 - x3).astype(np.complex64)
+            wb = (-sg * b1.imag + 1j * (sg * b1.real)).astype(np.complex64)
+            return [(a0 + b0).astype(np.complex64), (a1 + wb).astype(np.complex64),
+                    (a0 - b0).astype(np.complex64), (a1 - wb).astype(np.complex64)]
+        Uj = [U[..., j, :] for j in range(8)]
+        E = radix4(Uj[0], Uj[2], Uj[4], Uj[6])
+        O = radix4(Uj[1], Uj[3], Uj[5], Uj[7])
+        c8 = f32(0.70710678118654752)
+        o1r, o1i, o3r, o3i = O[1].real, O[1].imag, O[3].real, O[3].imag
+        P = [O[0],
+             ((o1r - sg * o1i) * c8 + 1j * ((o1i + sg * o1r) * c8)).astype(np.complex64),
+             (-sg * O[2].imag + 1j * (sg * O[2].real)).astype(np.complex64),
+             (-((o3r + sg * o3i) * c8) + 1j * ((sg * o3r - o3i) * c8)).astype(np.complex64)]
+        X = [(E[k] + P[k]).astype(np.complex64) for k in range(4)] + \
+            [(E[k] - P[k]).astype(np.complex64) for k in range(4)]
+        out = np.stack(X, -1)                           # [k1][k21][k22]
+        return np.swapaxes(out, -1, -3).reshape(x.shape)
     if r == 2:
         a, b = U[..., 0, :], U[..., 1, :]               # [k1][k21]
         s0 = (a + b).astype(np.complex64)

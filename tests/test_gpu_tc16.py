@@ -1,7 +1,7 @@
 """Tensor-core radix-16 variant (MXFFT_OPT_PATH = 1): radix-16 sub-DFTs as
-MXFP8 tcgen05 matrix products.  Not bit-exact with the radix-2 oracle by
-design; checked (1) against a numpy emulation of the same algorithm to FP32
-accumulation-order level, and (2) against FP64 with the stated tolerance:
+MXFP8 tcgen05 matrix products, n in {256, 512, 1024, 2048}.  Not bit-exact
+with the radix-2 oracle by design; checked (1) against a numpy emulation of
+the same algorithm to FP32 accumulation-order level, and (2) against FP64 with the stated tolerance:
 NRMSE <= 1.10 x the radix-2 oracle's NRMSE on the same input."""
 import os
 import sys
@@ -50,7 +50,22 @@ def test_tc16_matches_emulation(n0, n1, fmt, op, cuda_device):
     assert nrmse(got, want.astype(np.complex128)) < 1e-4
 
 
-@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (1024, 256)])
+@pytest.mark.parametrize("n0,n1,fmt,op", [(2048, 2048, "e4m3", "forward"),
+                                           (2048, 2048, "e5m2", "roundtrip"),
+                                           (2048, 512, "e4m3", "inverse"),
+                                           (256, 2048, "e5m2", "forward"),
+                                           (2048, 256, "e4m3", "roundtrip_fused")])
+def test_tc16_2048_matches_emulation(n0, n1, fmt, op, cuda_device):
+    # n = 2048 = 16 x 16 x 8: the last stage is a radix-8 DFT in FP32
+    img = op in ("roundtrip", "roundtrip_fused")
+    x = phantom.mri_batch(n0, n1, 1, 1, config_id=36, domain="image" if img else "kspace")
+    got = run_tc16(x, fmt, op)
+    want = tc16_ref.mxfft2d(x, fmt, op)
+    assert np.isfinite(got).all()
+    assert nrmse(got, want.astype(np.complex128)) < 1e-4
+
+
+@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (1024, 256), (2048, 256)])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("k", [64, 128])
 def test_tc16_shared_block_scales_match_emulation(n0, n1, fmt, k, cuda_device):
@@ -79,6 +94,15 @@ def test_tc16_within_stated_tolerance(n, fmt, k, cuda_device):
     assert tcr <= 1.10 * r2r, (tcr, r2r)
 
 
+@pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
+def test_tc16_2048_within_stated_tolerance(fmt, cuda_device):
+    ksp = phantom.mri_batch(2048, 2048, 1, 1, config_id=37)
+    ref = np.fft.fft2(ksp.astype(np.complex128))
+    r2f = nrmse(oracle.mxfft2d(ksp, fmt, 32)[0], ref)
+    tcf = nrmse(run_tc16(ksp, fmt, "forward", 32), ref)
+    assert tcf <= 1.10 * r2f, (tcf, r2f)
+
+
 def test_tc16_option_validation(cuda_device):
     from paper_2512_04317_gb300 import mxfft
     for args in [(128, 256, "e4m3", 32), (256, 256, "e2m3", 32), (256, 256, "e4m3", 16)]:
@@ -92,7 +116,8 @@ def test_tc16_option_validation(cuda_device):
 
 
 @pytest.mark.parametrize("n0,n1,batch", [(256, 256, 40), (512, 512, 6), (512, 256, 11),
-                                         (1024, 1024, 3), (1024, 256, 5)])
+                                         (1024, 1024, 3), (1024, 256, 5), (2048, 2048, 2),
+                                         (2048, 256, 9)])
 def test_tc16_many_tiles_per_cta(n0, n1, batch, cuda_device):
     # more 4096-point tiles than resident CTAs: every CTA walks several tiles,
     # an uneven number each, through both shared buffers

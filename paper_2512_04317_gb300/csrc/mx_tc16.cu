@@ -27,7 +27,8 @@
 // threads runs each stage as one round of two MMAs (rows 0-127 and 128-255,
 // accumulators in tensor-memory columns 0-31 and 32-63); thread i owns
 // vector i.  CTAs are persistent: each walks a contiguous range of tiles
-// (mostly of one slice, whose buffers and exponent it resolves once) and
+// (mostly of one slice, whose buffers and exponent it resolves once; the
+// columns pass of n = 2048 walks every grid-th tile instead) and
 // copies the next tile into its second shared buffer (cp.async, 16 B per
 // thread and copy) while it transforms the current one, so that HBM reads
 // overlap the MMA rounds.  The shared layouts are padded so that every
@@ -377,13 +378,23 @@ tc16_pass_kernel(const Args a) {
     for (int i = tid; i < M * 16; i += kThreads) sTwA[(i >> 4) * kTwRow + (i & 15)] = __ldg(a.twA + i);
     if (r > 1 && tid < r * 16) sTwC[(tid >> 4) * kTwRow + (tid & 15)] = __ldg(a.twC + tid);
     // CTA b takes the contiguous tiles [tile_begin, tile_end), shares equal to
-    // within one tile
+    // within one tile.  Exception: the columns pass of n = 2048, whose tiles
+    // are 2 columns (16 bytes of each row): there CTA b takes the tiles b, b +
+    // grid, ..., so that the CTAs working at the same time read and write
+    // adjacent columns and share every DRAM sector (a contiguous range would
+    // leave each sector's other half to the same CTA's next tile, after the
+    // sector has left L2).
+    constexpr bool kStrided = DIM == 0 && T == 2;
     const int share = ntiles / (int)gridDim.x, extra = ntiles % (int)gridDim.x;
-    const int tile_begin = (int)blockIdx.x * share + min((int)blockIdx.x, extra);
-    const int tile_end = tile_begin + share + ((int)blockIdx.x < extra ? 1 : 0);
+    const int tile_begin = kStrided ? (int)blockIdx.x
+                                    : (int)blockIdx.x * share + min((int)blockIdx.x, extra);
+    const int tile_step = kStrided ? (int)gridDim.x : 1;
+    const int my_tiles = kStrided
+        ? ((int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0)
+        : share + ((int)blockIdx.x < extra ? 1 : 0);
     const bool with_k = a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW;
     SliceCache ld, cs;   // slices of the tile being loaded and of the current tile
-    if (tile_begin < tile_end) {
+    if (my_tiles > 0) {
         const int sl = tile_begin / per_slice;
         resolve(a, sl, false, ld);
         load_tile<LOGN, DIM>(a, ld.in, (tile_begin - sl * per_slice) * T, buf_u32);
@@ -403,11 +414,12 @@ tc16_pass_kernel(const Args a) {
     mm.ok = true;
 
     int cur = 0;
-    for (int tile = tile_begin; tile < tile_end; tile++, cur ^= 1) {
+    for (int it = 0; it < my_tiles; it++, cur ^= 1) {
+        const int tile = tile_begin + it * tile_step;
         // prefetch the next tile into the other buffer (free since the last
         // barrier of the previous iteration), then wait for this one
-        const int next = tile + 1;
-        if (next < tile_end) {
+        const int next = tile + tile_step;
+        if (it + 1 < my_tiles) {
             const int sl = next / per_slice;
             resolve(a, sl, false, ld);
             load_tile<LOGN, DIM>(a, ld.in, (next - sl * per_slice) * T,

@@ -161,6 +161,8 @@ __device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams
 // registers and the CTA's shared histogram.  When the whole warp executes the
 // call, lanes that hit the same bin are merged first (__match_any_sync), so a
 // bin shared by many lanes costs one shared atomic instead of one per lane.
+// add<true> is for call sites that every lane of the warp reaches (a loop with
+// a warp-uniform trip count); add<false> checks the active mask first.
 struct StatAcc {
     uint32_t amax_bits = 0;   // max |x| (mag_c3) over points outside the fast range
     uint32_t smax_bits = 0;   // max re^2 + im^2 over points inside it
@@ -174,6 +176,7 @@ struct StatAcc {
     // 2^(j+1)) exactly when s is in [2^(2j), 2^(2j+2)).  Hence the bin
     // floor(log2 |x|) is floor(floor(log2 s) / 2), and max |x| = fl(sqrt(max s))
     // because the rounded square root is monotone: no square root per point.
+    template <bool kConverged = false>
     __device__ __forceinline__ void add(float re, float im, uint32_t* sh_hist) {
         const uint32_t br = __float_as_uint(re) & 0x7fffffffu;
         const uint32_t bi = __float_as_uint(im) & 0x7fffffffu;
@@ -199,9 +202,11 @@ struct StatAcc {
                 bin = ilogb_bits(mb) + 149;
             }
         }
-        if (__activemask() == 0xffffffffu) {
+        if (kConverged || __activemask() == 0xffffffffu) {
             const unsigned same = __match_any_sync(0xffffffffu, bin);
-            if (bin >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1)
+            // the lowest lane of its group adds the group's count
+            const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
+            if (bin >= 0 && (same & below) == 0u)
                 atomicAdd(&sh_hist[bin], (uint32_t)__popc(same));
         } else if (bin >= 0) {
             atomicAdd(&sh_hist[bin], 1u);

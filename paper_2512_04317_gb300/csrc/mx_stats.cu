@@ -22,16 +22,18 @@ __device__ __forceinline__ void stats_cta(const float2* __restrict__ x, int npts
     const int begin = chunk * kStatsPtsPerCta;
     const int end = min(begin + kStatsPtsPerCta, npts);
     StatAcc acc;
-    // two 16-byte loads in flight per thread before their arithmetic
+    // two 16-byte loads in flight per thread before their arithmetic; the
+    // trip count is the same for every thread of the CTA, so every lane of a
+    // warp reaches each add
     for (int base = begin; base < end; base += 4 * blockDim.x) {
         const int p0 = base + 2 * tid, p1 = p0 + 2 * blockDim.x;
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);   // zeros do not count
         const float4 v0 = p0 < end ? __ldg(xs + (p0 >> 1)) : zero;
         const float4 v1 = p1 < end ? __ldg(xs + (p1 >> 1)) : zero;
-        acc.add(v0.x, v0.y, sh_hist);
-        acc.add(v0.z, v0.w, sh_hist);
-        acc.add(v1.x, v1.y, sh_hist);
-        acc.add(v1.z, v1.w, sh_hist);
+        acc.add<true>(v0.x, v0.y, sh_hist);
+        acc.add<true>(v0.z, v0.w, sh_hist);
+        acc.add<true>(v1.x, v1.y, sh_hist);
+        acc.add<true>(v1.z, v1.w, sh_hist);
     }
     __syncthreads();
     stats_flush_and_select(acc, sh_hist, sh_misc, st, ctas, kp);

@@ -23,8 +23,10 @@
 //     even, saturating, signed zeros and subnormals kept), the element-space
 //     product uses fma.rn.f32.f16 on the exact f16 element values (a product
 //     of two element values is exact, so the only rounding is the add, as in
-//     Alg. 2), and u +- c 2^s^ is one FFMA each because c 2^s^ is always an
-//     exact FP32 value (s^ >= -127 and the element grid step is >= 2^-16).
+//     Alg. 2), and u +- c 2^s^ is one FMA per component because c 2^s^ is
+//     always an exact FP32 value (s^ >= -127 and the element grid step is >=
+//     2^-16).  The scalings and these FMAs run as packed FP32 pairs
+//     (__fmul2_rn / __ffma2_rn: each component rounded as its scalar form).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -142,10 +144,12 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
     const bool bad = !(A <= 3.402823466e38f);
     const int sv = scale_of(A, fp.emax);
     const float inv = exp2i(-sv);
+    const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
     for (int t = 0; t < NB; t++) {
-        const float2 v = *V[t];
-        const uint32_t y = Cvt<FMT>::q2(__fmul_rn(v.x, inv), __fmul_rn(v.y, inv));
+        // packed FP32 pairs (each component rounded as its scalar operation)
+        const float2 vs = __fmul2_rn(*V[t], inv2);
+        const uint32_t y = Cvt<FMT>::q2(vs.x, vs.y);
         const uint32_t w = W[t];
         const float pr = fma_ll(w, y, -fma_hh(w, y, -0.0f));
         const float pi = fma_hl(w, y, fma_lh(w, y, -0.0f));
@@ -159,15 +163,17 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
     const int sh = Pb ? min(max(so + ilogb_bits(Pb) - fp.emax, -127), 127) : so;
     const float f = exp2i(so - sh);
     const float d = bad ? __int_as_float(0x7fffffff) : exp2i(sh);
+    const float2 f2 = make_float2(f, f), d2 = make_float2(d, d);
 #pragma unroll
     for (int t = 0; t < NB; t++) {
-        const float2 p = *V[t];
-        const uint32_t c = Cvt<FMT>::q2(__fmul_rn(p.x, f), __fmul_rn(p.y, f));
+        const float2 ps = __fmul2_rn(*V[t], f2);
+        const uint32_t c = Cvt<FMT>::q2(ps.x, ps.y);
         const __half2 ch = *reinterpret_cast<const __half2*>(&c);
         const float cr = __low2float(ch), ci = __high2float(ch);
         const float2 u = *U[t];
-        *U[t] = make_float2(__fmaf_rn(cr, d, u.x), __fmaf_rn(ci, d, u.y));
-        *V[t] = make_float2(__fmaf_rn(-cr, d, u.x), __fmaf_rn(-ci, d, u.y));
+        // u +- c 2^s^ as packed FP32 pairs (each component rounded as __fmaf_rn)
+        *U[t] = __ffma2_rn(make_float2(cr, ci), d2, u);
+        *V[t] = __ffma2_rn(make_float2(-cr, -ci), d2, u);
     }
 }
 

@@ -170,7 +170,7 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
     const int sh = Pb ? min(max(so + ilogb_bits(Pb) - fp.emax, -127), 127) : so;
     const float f = exp2i(so - sh);
     const float d = bad ? __int_as_float(0x7fffffff) : exp2i(sh);
-    const float2 f2 = make_float2(f, f), d2 = make_float2(d, d);
+    const float2 f2 = make_float2(f, f), d2 = make_float2(d, d), nd2 = make_float2(-d, -d);
 #pragma unroll
     for (int t = 0; t < NB; t++) {
         const float2 ps = __fmul2_rn(*V[t], f2);
@@ -180,7 +180,7 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
         const float2 u = *U[t];
         // u +- c 2^s^ as packed FP32 pairs (each component rounded as __fmaf_rn)
         *U[t] = __ffma2_rn(make_float2(cr, ci), d2, u);
-        *V[t] = __ffma2_rn(make_float2(-cr, -ci), d2, u);
+        *V[t] = __ffma2_rn(make_float2(cr, ci), nd2, u);
     }
 }
 

@@ -124,32 +124,29 @@ fast_pass_kernel(const FastArgs fa) {
         }
     } else {
         // stage the CTA's rows as [e][tau]: lanes run over rows, two lanes per
-        // 16-byte pair, so each row contributes a full 32-byte sector per load
-        // total is a multiple of 8 * nthr (NG * TG * n / 2 = 16 * threads)
-        const int total = fa.NG << (lgTG + L - 1);
-        for (int u0 = tid; u0 < total; u0 += 8 * nthr) {
-            float4 v[8];
+        // 16-byte pair, so each row contributes a full 32-byte sector per load.
+        // The CTA's rows are NG * TG * n / 2 = 16 * threads float4: 16 per
+        // thread, all in flight before the first store; the row of a thread's
+        // float4 is fixed (threads is a multiple of TG)
+        const int tc = tid & (TG - 1);
+        const int r0 = tid >> lgTG, dr = nthr >> lgTG;
+        float4 v[16];
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const int u = u0 + b * nthr;
-                const int tc = u & (TG - 1);
-                const int rest = u >> lgTG;
-                const int p = rest & ((n >> 1) - 1);
-                const int g = rest >> (L - 1);
-                v[b] = __ldg(reinterpret_cast<const float4*>(
-                    in + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p));
-            }
+        for (int b = 0; b < 16; b++) {
+            const int rest = r0 + b * dr;
+            const int p = rest & ((n >> 1) - 1);
+            const int g = rest >> (L - 1);
+            v[b] = __ldg(reinterpret_cast<const float4*>(
+                in + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p));
+        }
 #pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const int u = u0 + b * nthr;
-                const int tc = u & (TG - 1);
-                const int rest = u >> lgTG;
-                const int p = rest & ((n >> 1) - 1);
-                const int g = rest >> (L - 1);
-                float2* Gg = sm + (size_t)g * n * S;
-                Gg[(2 * p) * S + tc] = make_float2(__fmul_rn(v[b].x, pre), __fmul_rn(v[b].y, pre));
-                Gg[(2 * p + 1) * S + tc] = make_float2(__fmul_rn(v[b].z, pre), __fmul_rn(v[b].w, pre));
-            }
+        for (int b = 0; b < 16; b++) {
+            const int rest = r0 + b * dr;
+            const int p = rest & ((n >> 1) - 1);
+            const int g = rest >> (L - 1);
+            float2* Gg = sm + (size_t)g * n * S;
+            Gg[(2 * p) * S + tc] = make_float2(__fmul_rn(v[b].x, pre), __fmul_rn(v[b].y, pre));
+            Gg[(2 * p + 1) * S + tc] = make_float2(__fmul_rn(v[b].z, pre), __fmul_rn(v[b].w, pre));
         }
         __syncthreads();
 #pragma unroll

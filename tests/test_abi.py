@@ -56,6 +56,7 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.mxfft_forward(None, None, None, 1, None) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_inverse(None, None, None, 1, None) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_roundtrip(None, None, None, 1, None) == mxfft.MXFFT_ERR_INVALID
+    assert lib.mxfft_roundtrip_fused(None, None, None, 1, None) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_set_option(None, 0, 2.0 ** -10) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_get_status(None, None, None) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_profile(None, 1) == mxfft.MXFFT_ERR_INVALID

@@ -27,13 +27,13 @@ bool fast_pass_supported(const PassArgs& a) {
     int TG, S, NG, threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
     const int logm = log2_exact(a.m);
-    return a.fmt <= 4 && logm >= 0 && logm <= 4 && a.fp.mbits > 0 &&
-           fast::fast_geometry(a.n, other, &TG, &S, &NG, &threads);
+    return a.fmt <= 4 && logm >= 0 && logm <= 5 && a.fp.mbits > 0 &&
+           fast::fast_geometry(a.n, other, a.m, &TG, &S, &NG, &threads);
 }
 
-int fast_ng_candidates(int n, int other, int* out, int max) {
+int fast_ng_candidates(int n, int other, int m, int* out, int max) {
     int TG, S, NG, threads;
-    if (!fast::fast_geometry(n, other, &TG, &S, &NG, &threads)) return 0;
+    if (!fast::fast_geometry(n, other, m, &TG, &S, &NG, &threads)) return 0;
     const int per_group = TG * (n / 32);
     int c = 0;
     for (int ng = 1; per_group * ng <= fast::kMaxThreads && c < max; ng <<= 1) {
@@ -60,12 +60,12 @@ cudaError_t launch_fast(const PassArgs& a, const uint32_t* twh, const TwA& twa,
     }
     int threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
-    fast::fast_geometry(a.n, other, &fa.TG, &fa.S, &fa.NG, &threads);
+    fast::fast_geometry(a.n, other, a.m, &fa.TG, &fa.S, &fa.NG, &threads);
     fa.lgTG = fa.TG == 16 ? 4 : 3;
     if (ng == 0) ng = fast_ng_tuned(a.n, other, a.dim, a.fmt, a.m, batch);
     if (ng > 0) {
         int cand[16];
-        const int nc = fast_ng_candidates(a.n, other, cand, 16);
+        const int nc = fast_ng_candidates(a.n, other, a.m, cand, 16);
         if (std::find(cand, cand + nc, ng) == cand + nc) return cudaErrorInvalidValue;
         fa.NG = ng;
     }

@@ -1,5 +1,6 @@
 // Register-resident MX radix-2 pass for transform lengths n = 64..2048 and
-// MX blocks of m <= 16 butterflies (k <= 32 real elements).
+// MX blocks of m <= 16 butterflies (k <= 32 real elements), and m = 32 (k =
+// 64) for n >= 128 with groups of 8 transforms.
 //
 // Data layout and work split:
 //   * A CTA owns NG groups of TG transforms (rows or columns) of one slice.
@@ -17,7 +18,9 @@
 //     holds the 8-element runs P + 8r + q h, q = 0..3, P = 4hG, which carry
 //     whole butterfly groups of both stages.  An MX block of m = 16 spans the
 //     runs r and r^1, held by the lanes sigma and sigma^1 (lane ^ TG): one
-//     xor shuffle.  An odd last stage h = n/2 pairs runs sigma and sigma+n/32.
+//     xor shuffle (m = 32: runs r .. r^3, two shuffles, TG = 8 so that the
+//     four slots share a warp; in phase A its two chunks, one shuffle).  An
+//     odd last stage h = n/2 pairs runs sigma and sigma+n/32.
 //   * Element quantisation uses the sm_100-family conversions
 //     cvt.rn.satfinite.<fmt>x2.f32 and cvt.rn.f16x2.<fmt>x2 (round to nearest
 //     even, saturating, signed zeros and subnormals kept), the element-space
@@ -141,14 +144,16 @@ __device__ __forceinline__ float block_max_abs(float2* const (&X)[NB]) {
 // Steps: block max of v -> s_v; y = Q(v 2^-s_v); p = x y (exact products, one
 // rounding each), written over v, which is dead by then; block max of p -> s^;
 // c = Q(p 2^(s_w + s_v - s^)); u +- c 2^s^.  A block holding Inf/NaN decodes
-// to NaN (OCP MX NaN scale).  `red` != 0 also reduces the two block maxima
-// with the lane `red` apart.
-template <int FMT, int NB>
+// to NaN (OCP MX NaN scale).  A block of NB butterflies per lane spread over
+// 2^NRED lanes (lane ^ red << i, i < NRED) also reduces the two block maxima
+// over those lanes.
+template <int FMT, int NB, int NRED>
 __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (&V)[NB],
                                          const uint32_t (&W)[NB], int sw, unsigned red,
                                          const FmtParams& fp) {
     float A = block_max_abs<NB>(V);
-    if (red) A = fmax_nan(A, __shfl_xor_sync(0xffffffffu, A, red));
+#pragma unroll
+    for (int i = 0; i < NRED; i++) A = fmax_nan(A, __shfl_xor_sync(0xffffffffu, A, red << i));
     const bool bad = !(A <= 3.402823466e38f);
     const int sv = scale_of(A, fp.emax);
     const float inv = exp2i(-sv);
@@ -164,7 +169,8 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
         *V[t] = make_float2(pr, pi);
     }
     float P = block_max_abs<NB>(V);
-    if (red) P = fmaxf(P, __shfl_xor_sync(0xffffffffu, P, red));
+#pragma unroll
+    for (int i = 0; i < NRED; i++) P = fmaxf(P, __shfl_xor_sync(0xffffffffu, P, red << i));
     const int so = sw + sv;
     const uint32_t Pb = __float_as_uint(P);
     const int sh = Pb ? min(max(so + ilogb_bits(Pb) - fp.emax, -127), 127) : so;
@@ -185,24 +191,29 @@ __device__ __forceinline__ void mx_block(float2* const (&U)[NB], float2* const (
 }
 
 // Phase A stage H on a 32-element chunk r[] (chunk-local butterfly t = 0..15:
-// group t / H, index j = t % H).
+// group t / H, index j = t % H).  Chunk sigma holds the stage's butterflies
+// 16 sigma .. 16 sigma + 15, so a block of m = 32 is the chunks sigma and
+// sigma ^ 1, held by the lanes tg apart.
 template <int FMT, int LOGM, int H>
-__device__ __forceinline__ void stage_a(float2 (&r)[32], const TwA& tw, const FmtParams& fp) {
+__device__ __forceinline__ void stage_a(float2 (&r)[32], const TwA& tw, const FmtParams& fp,
+                                        unsigned tg) {
     constexpr int M = 1 << LOGM;
+    constexpr int MB = M < 16 ? M : 16;        // butterflies of a block held by this thread
+    constexpr int NRED = M > 16 ? LOGM - 4 : 0;
 #pragma unroll
-    for (int b0 = 0; b0 < 16; b0 += M) {
-        float2* U[M];
-        float2* V[M];
-        uint32_t W[M];
+    for (int b0 = 0; b0 < 16; b0 += MB) {
+        float2* U[MB];
+        float2* V[MB];
+        uint32_t W[MB];
 #pragma unroll
-        for (int q = 0; q < M; q++) {
+        for (int q = 0; q < MB; q++) {
             const int t = b0 + q;
             const int iu = 2 * H * (t / H) + (t % H);
             U[q] = &r[iu];
             V[q] = &r[iu + H];
             W[q] = tw.h2[H - 1 + (t % H)];
         }
-        mx_block<FMT, M>(U, V, W, tw.sw[H - 1 + (b0 % H)], 0u, fp);
+        mx_block<FMT, MB, NRED>(U, V, W, tw.sw[H - 1 + (b0 % H)], tg, fp);
     }
 }
 
@@ -231,7 +242,7 @@ __device__ __forceinline__ void stage_b8(float2 (&Ru)[8], float2 (&Rv)[8],
             V[q] = &Rv[b0 + q];
             W[q] = w8[b0 + q];
         }
-        mx_block<FMT, ML>(U, V, W, __ldg(tws + jb + b0), M > 8 ? red : 0u, fp);
+        mx_block<FMT, ML, (M > 8 ? LOGM - 3 : 0)>(U, V, W, __ldg(tws + jb + b0), red, fp);
     }
 }
 

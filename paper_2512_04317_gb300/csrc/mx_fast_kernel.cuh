@@ -28,17 +28,17 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
                                            const int8_t* __restrict__ tws, int L, int S, int TG,
                                            int sigma, int tau, int s, const FmtParams& fp) {
     // ---- phase A: stages h = 1..16 inside the chunk -------------------------
-    stage_a<FMT, LOGM, 1>(r, twa, fp);
-    stage_a<FMT, LOGM, 2>(r, twa, fp);
-    stage_a<FMT, LOGM, 4>(r, twa, fp);
-    stage_a<FMT, LOGM, 8>(r, twa, fp);
-    stage_a<FMT, LOGM, 16>(r, twa, fp);
+    stage_a<FMT, LOGM, 1>(r, twa, fp, (unsigned)TG);
+    stage_a<FMT, LOGM, 2>(r, twa, fp, (unsigned)TG);
+    stage_a<FMT, LOGM, 4>(r, twa, fp, (unsigned)TG);
+    stage_a<FMT, LOGM, 8>(r, twa, fp, (unsigned)TG);
+    stage_a<FMT, LOGM, 16>(r, twa, fp, (unsigned)TG);
 #pragma unroll
     for (int t = 0; t < 32; t++) Gs[(32 * sigma + t) * S + tau] = r[t];
     __syncthreads();
 
     // ---- phase B: stage pairs (h, 2h), an odd last stage alone ---------------
-    const unsigned red = (unsigned)TG;           // lane of the partner run (slot ^ 1)
+    const unsigned red = (unsigned)TG;           // lane offset of the partner run (slot ^ 1)
     int ast = 5;
     while (true) {
         const int h = 1 << ast;
@@ -198,14 +198,16 @@ fast_pass_kernel(const FastArgs fa) {
 }
 
 // Launch geometry: TG transforms per group (8 for n = 2048 so a group fits in
-// shared memory, with a padded stride), NG groups per CTA so that a CTA has
-// at least 128 threads (a group of n = 512 has 256, of n >= 1024 has 512).
-// Small CTAs let four of them share an SM and drift apart, so one CTA's loads
-// overlap another's arithmetic.
-inline bool fast_geometry(int n, int other, int* TG, int* S, int* NG, int* threads) {
-    if (n < 64 || n > 2048) return false;
-    *TG = n == 2048 ? 8 : 16;
-    *S = n == 2048 ? 9 : 16;
+// shared memory, and for m = 32 so that the four lanes of a block share a
+// warp; a padded stride then), NG groups per CTA so that a CTA has at least
+// 128 threads (a group of n = 512 has 256, of n >= 1024 has 512, with TG =
+// 16).  Small CTAs let four of them share an SM and drift apart, so one CTA's
+// loads overlap another's arithmetic.  m = 32 needs n >= 128 (for n = 64 the
+// last stage's block spans both of a lane's run pairs).
+inline bool fast_geometry(int n, int other, int m, int* TG, int* S, int* NG, int* threads) {
+    if (n < 64 || n > 2048 || m > 32 || (m == 32 && n < 128)) return false;
+    *TG = (n == 2048 || m == 32) ? 8 : 16;
+    *S = *TG == 8 ? 9 : 16;
     const int per_group = *TG * (n / 32);
     int ng = per_group >= 128 ? 1 : 128 / per_group;
     while (ng > 1 && (*TG * ng > other || other % (*TG * ng) != 0)) ng >>= 1;
@@ -225,11 +227,12 @@ cudaError_t launch_fast_dim(const FastArgs& fa, int logm, int blocks, int thread
         case 2: k = fast_pass_kernel<FMT, 2, DIM, FUSED>; break;
         case 3: k = fast_pass_kernel<FMT, 3, DIM, FUSED>; break;
         case 4: k = fast_pass_kernel<FMT, 4, DIM, FUSED>; break;
+        case 5: k = fast_pass_kernel<FMT, 5, DIM, FUSED>; break;
         default: return cudaErrorNotSupported;
     }
     // raise the opt-in limit only (never lower it): launches captured earlier
     // in a graph may need more than this one
-    static size_t smem_limit[5] = {0, 0, 0, 0, 0};
+    static size_t smem_limit[6] = {0, 0, 0, 0, 0, 0};
     if (smem > smem_limit[logm]) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

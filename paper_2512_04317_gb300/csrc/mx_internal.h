@@ -149,7 +149,7 @@ cudaError_t launch_rss(const RssRef& val, const RssRef* dev, long long images, l
 // Groups of TG transforms per CTA of the register-resident pass: valid values
 // for (n, other), the tuned value for a launch (0 if none), and the table the
 // autotuner fills (mx_tune.cu).
-int fast_ng_candidates(int n, int other, int* out, int max);
+int fast_ng_candidates(int n, int other, int m, int* out, int max);
 int fast_ng_tuned(int n, int other, int dim, int fmt, int m, int batch);
 void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng, double us);
 // The register-resident pass with ng groups per CTA (ng = 0: tuned or default).

@@ -138,7 +138,7 @@ int mxfft_tune(mxfft_plan_t p, int batch, void* stream, int* n_measured) {
         if (!fast_pass_supported(a)) continue;
         const int other = dim == 1 ? p->n0 : p->n1;
         int cand[16];
-        const int nc = fast_ng_candidates(a.n, other, cand, 16);
+        const int nc = fast_ng_candidates(a.n, other, a.m, cand, 16);
         if (nc < 2) continue;
         int best = 0;
         double best_us = 0.0;
@@ -206,7 +206,7 @@ int mxfft_tune_load(const char* path) {
             !json_int(obj, "batch_class", &bc) || !json_int(obj, "ng", &ng))
             return MXFFT_ERR_INVALID;
         int cand[16];
-        const int nc = fast_ng_candidates((int)n, (int)other, cand, 16);
+        const int nc = fast_ng_candidates((int)n, (int)other, (int)m, cand, 16);
         bool valid = false;
         for (int i = 0; i < nc; i++) valid = valid || cand[i] == ng;
         if (!valid || (dim != 0 && dim != 1) || bc < 0 || bc > 30) return MXFFT_ERR_INVALID;

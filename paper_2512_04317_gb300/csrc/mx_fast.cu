@@ -27,7 +27,7 @@ bool fast_pass_supported(const PassArgs& a) {
     int TG, S, NG, threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
     const int logm = log2_exact(a.m);
-    return a.fmt <= 4 && logm >= 0 && logm <= 5 && a.fp.mbits > 0 &&
+    return a.fmt <= 4 && logm >= 0 && logm <= 6 && a.fp.mbits > 0 &&
            fast::fast_geometry(a.n, other, a.m, &TG, &S, &NG, &threads);
 }
 
@@ -61,7 +61,7 @@ cudaError_t launch_fast(const PassArgs& a, const uint32_t* twh, const TwA& twa,
     int threads;
     const int other = a.dim == 1 ? a.n0 : a.n1;
     fast::fast_geometry(a.n, other, a.m, &fa.TG, &fa.S, &fa.NG, &threads);
-    fa.lgTG = fa.TG == 16 ? 4 : 3;
+    fa.lgTG = fa.TG == 16 ? 4 : (fa.TG == 8 ? 3 : 2);
     if (ng == 0) ng = fast_ng_tuned(a.n, other, a.dim, a.fmt, a.m, batch);
     if (ng > 0) {
         int cand[16];

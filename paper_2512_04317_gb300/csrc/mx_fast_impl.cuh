@@ -1,6 +1,7 @@
 // Register-resident MX radix-2 pass for transform lengths n = 64..2048 and
-// MX blocks of m <= 16 butterflies (k <= 32 real elements), and m = 32 (k =
-// 64) for n >= 128 with groups of 8 transforms.
+// MX blocks of m <= 16 butterflies (k <= 32 real elements), m = 32 (k = 64)
+// for n >= 128 with groups of 8 transforms and m = 64 (k = 128) for n >= 128
+// with groups of 4.
 //
 // Data layout and work split:
 //   * A CTA owns NG groups of TG transforms (rows or columns) of one slice.
@@ -19,8 +20,11 @@
 //     whole butterfly groups of both stages.  An MX block of m = 16 spans the
 //     runs r and r^1, held by the lanes sigma and sigma^1 (lane ^ TG): one
 //     xor shuffle (m = 32: runs r .. r^3, two shuffles, TG = 8 so that the
-//     four slots share a warp; in phase A its two chunks, one shuffle).  An
-//     odd last stage h = n/2 pairs runs sigma and sigma+n/32.
+//     four slots share a warp; in phase A its two chunks, one shuffle; m = 64:
+//     8 runs and three shuffles, TG = 4, in phase A four chunks, and at the
+//     first stage pair (h = 32, 64), where a block spans both run pairs of a
+//     slot, 16 butterflies per lane over 4 lanes).  An odd last stage h = n/2
+//     pairs runs sigma and sigma+n/32.
 //   * Element quantisation uses the sm_100-family conversions
 //     cvt.rn.satfinite.<fmt>x2.f32 and cvt.rn.f16x2.<fmt>x2 (round to nearest
 //     even, saturating, signed zeros and subnormals kept), the element-space
@@ -244,6 +248,33 @@ __device__ __forceinline__ void stage_b8(float2 (&Ru)[8], float2 (&Rv)[8],
         }
         mx_block<FMT, ML, (M > 8 ? LOGM - 3 : 0)>(U, V, W, __ldg(tws + jb + b0), red, fp);
     }
+}
+
+// Phase B with m = 64 at the first stage pair (stage 32, and its second stage
+// 64): one MX block covers 8 butterflies of each of two run pairs per lane (u =
+// RuA[i], v = RvA[i], j = jbA + i, and u = RuB[i], v = RvB[i], j = jbB + i),
+// over 4 lanes.
+template <int FMT>
+__device__ __forceinline__ void stage_b_dual(float2 (&RuA)[8], float2 (&RvA)[8],
+                                             float2 (&RuB)[8], float2 (&RvB)[8],
+                                             const uint32_t* __restrict__ twh,
+                                             const int8_t* __restrict__ tws, int jbA, int jbB,
+                                             unsigned red, const FmtParams& fp) {
+    const uint4* ta = reinterpret_cast<const uint4*>(twh + jbA);
+    const uint4* tb = reinterpret_cast<const uint4*>(twh + jbB);
+    const uint4 a0 = __ldg(ta), a1 = __ldg(ta + 1), b0 = __ldg(tb), b1 = __ldg(tb + 1);
+    const uint32_t W[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
+                            b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float2* U[16];
+    float2* V[16];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        U[i] = &RuA[i];
+        V[i] = &RvA[i];
+        U[8 + i] = &RuB[i];
+        V[8 + i] = &RvB[i];
+    }
+    mx_block<FMT, 16, 2>(U, V, W, __ldg(tws + jbA), red, fp);
 }
 
 // Compile-time 5-bit reversal of the chunk position.

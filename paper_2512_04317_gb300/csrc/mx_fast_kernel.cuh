@@ -65,11 +65,18 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i++) R[q][i] = Gs[(e0[q] + i) * S + tau];
-        stage_b8<FMT, LOGM>(R[0], R[1], twh + h, tws + h - 1, jA, red, fp);
-        stage_b8<FMT, LOGM>(R[2], R[3], twh + h, tws + h - 1, jB, red, fp);
-        if (two) {
-            stage_b8<FMT, LOGM>(R[0], R[2], twh + 2 * h, tws + 2 * h - 1, jC, red, fp);
-            stage_b8<FMT, LOGM>(R[1], R[3], twh + 2 * h, tws + 2 * h - 1, jD, red, fp);
+        if (LOGM == 6 && h == 32) {
+            // m = 64 > h: a block of stage 32 is both groups of the slot's runs,
+            // a block of stage 64 the whole group (always a stage pair: n >= 128)
+            stage_b_dual<FMT>(R[0], R[1], R[2], R[3], twh + h, tws + h - 1, jA, jB, red, fp);
+            stage_b_dual<FMT>(R[0], R[2], R[1], R[3], twh + 2 * h, tws + 2 * h - 1, jC, jD, red, fp);
+        } else {
+            stage_b8<FMT, LOGM>(R[0], R[1], twh + h, tws + h - 1, jA, red, fp);
+            stage_b8<FMT, LOGM>(R[2], R[3], twh + h, tws + h - 1, jB, red, fp);
+            if (two) {
+                stage_b8<FMT, LOGM>(R[0], R[2], twh + 2 * h, tws + 2 * h - 1, jC, red, fp);
+                stage_b8<FMT, LOGM>(R[1], R[3], twh + 2 * h, tws + 2 * h - 1, jD, red, fp);
+            }
         }
         ast += two ? 2 : 1;
         if (ast >= L) break;
@@ -199,15 +206,16 @@ fast_pass_kernel(const FastArgs fa) {
 
 // Launch geometry: TG transforms per group (8 for n = 2048 so a group fits in
 // shared memory, and for m = 32 so that the four lanes of a block share a
-// warp; a padded stride then), NG groups per CTA so that a CTA has at least
-// 128 threads (a group of n = 512 has 256, of n >= 1024 has 512, with TG =
-// 16).  Small CTAs let four of them share an SM and drift apart, so one CTA's
-// loads overlap another's arithmetic.  m = 32 needs n >= 128 (for n = 64 the
-// last stage's block spans both of a lane's run pairs).
+// warp; 4 for m = 64, eight lanes; a padded stride then), NG groups per CTA so
+// that a CTA has at least 128 threads (a group of n = 512 has 256, of n >=
+// 1024 has 512, with TG = 16).  Small CTAs let four of them share an SM and
+// drift apart, so one CTA's loads overlap another's arithmetic.  m = 32 needs
+// n >= 128 (for n = 64 the last stage's block spans both of a lane's run
+// pairs).
 inline bool fast_geometry(int n, int other, int m, int* TG, int* S, int* NG, int* threads) {
-    if (n < 64 || n > 2048 || m > 32 || (m == 32 && n < 128)) return false;
-    *TG = (n == 2048 || m == 32) ? 8 : 16;
-    *S = *TG == 8 ? 9 : 16;
+    if (n < 64 || n > 2048 || m > 64 || (m == 32 && n < 128)) return false;
+    *TG = m == 64 ? 4 : ((n == 2048 || m == 32) ? 8 : 16);
+    *S = *TG == 16 ? 16 : *TG + 1;
     const int per_group = *TG * (n / 32);
     int ng = per_group >= 128 ? 1 : 128 / per_group;
     while (ng > 1 && (*TG * ng > other || other % (*TG * ng) != 0)) ng >>= 1;
@@ -228,11 +236,12 @@ cudaError_t launch_fast_dim(const FastArgs& fa, int logm, int blocks, int thread
         case 3: k = fast_pass_kernel<FMT, 3, DIM, FUSED>; break;
         case 4: k = fast_pass_kernel<FMT, 4, DIM, FUSED>; break;
         case 5: k = fast_pass_kernel<FMT, 5, DIM, FUSED>; break;
+        case 6: k = fast_pass_kernel<FMT, 6, DIM, FUSED>; break;
         default: return cudaErrorNotSupported;
     }
     // raise the opt-in limit only (never lower it): launches captured earlier
     // in a graph may need more than this one
-    static size_t smem_limit[6] = {0, 0, 0, 0, 0, 0};
+    static size_t smem_limit[7] = {0, 0, 0, 0, 0, 0, 0};
     if (smem > smem_limit[logm]) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

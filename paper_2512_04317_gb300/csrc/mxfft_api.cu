@@ -409,8 +409,8 @@ PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, fl
 }
 
 // The tensor-core pass when that path is selected, else the register-resident
-// kernel where it applies (n in [64, 2048], m <= 16), else the generic
-// shared-memory kernel.
+// kernel where it applies (n in [64, 2048], m <= 16; m = 32, 64 for n >= 128),
+// else the generic shared-memory kernel.
 cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
     const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
     if (p->path == 1) {

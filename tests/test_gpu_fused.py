@@ -42,10 +42,13 @@ def test_small_and_generic_sizes(n0, n1, cuda_device):
 
 
 @pytest.mark.parametrize("k", [64, 128])
-def test_large_blocks_two_column_passes(k, cuda_device):
-    # m = k / 2 > 16: the register-resident kernel does not apply
+def test_large_blocks(k, cuda_device):
+    # m = k / 2 = 32, 64: blocks over 4 / 8 lanes (groups of 8 / 4 transforms)
     x = phantom.random_complex((2, 256, 128), seed=k)
     check(x, "e4m3", k, OP)
+    # columns of 64 with m = 32: the generic kernel's two column passes
+    y = phantom.random_complex((2, 64, 128), seed=k + 1)
+    check(y, "e5m2", 64, OP)
 
 
 def test_generic_kernel_gives_the_same_bits(cuda_device):

@@ -18,6 +18,7 @@ host cores instead.  Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -74,6 +75,10 @@ def parse():
     ap.add_argument("--slices", type=int, default=0,
                     help="smaller case of a workload (profiling): about this many slices")
     ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--fmt", choices=["e4m3", "e5m2", "e2m3", "e3m2", "e2m1", "fp16"], default=None,
+                    help="element format instead of the workload's (format / block-size sweeps)")
+    ap.add_argument("--k", type=int, default=0,
+                    help="MX block size k instead of the workload's (power of two, 2..128)")
     return ap.parse_args()
 
 
@@ -410,6 +415,10 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
                      else "the complex coil images",
            "server": f"{slots} slots, batches of at most {batch_slices} slices and "
                      f"{batch_mb} MiB, memory budget 80% of free"}
+    # no garbage-collector pauses in the submitting loop while it keeps time
+    gc.collect()
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
     wall, lat, batches = run_mx(0.0)
     sat = n_req / wall
     out["saturated"] = {"req_per_s": sat, "mpts_per_s": pts_total / wall / 1e6,
@@ -433,6 +442,8 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
             ent["fp32_per_slice"] = {"p50_ms": f50, "p99_ms": f99,
                                      "mpts_per_s": pts_total / fw / 1e6}
         out["poisson"].append(ent)
+    if gc_was_enabled:
+        gc.enable()
     del work
     return out
 
@@ -510,6 +521,10 @@ def main():
     if args.slices > 0:
         w["nslices"] = max(1, -(-args.slices // w["ncoils"]))
         w["desc"] += f" (reduced to {w['nslices'] * w['ncoils']} slices)"
+    if args.fmt or args.k:
+        w["fmt"] = args.fmt or w["fmt"]
+        w["k"] = args.k or w["k"]
+        w["desc"] += f" (run with format {w['fmt']}, k={w['k']})"
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, w, world, rank)

@@ -134,13 +134,15 @@ def test_engine_rejects_bad_items(cuda_device):
         mxfft.mxfft_engine_run(eng.handle, [], None)   # nothing to do
 
 
-def test_tuned_geometries_give_the_same_bits(cuda_device, tmp_path):
+@pytest.mark.parametrize("k", [32, 64, 128])
+def test_tuned_geometries_give_the_same_bits(k, cuda_device, tmp_path):
+    # groups of 16, 8 and 4 transforms (k = 32, 64, 128)
     import torch
 
     from paper_2512_04317_gb300 import mxfft
     x = torch.from_numpy(phantom.mri_batch(256, 256, 8, 1, config_id=42)).cuda()
     mxfft.mxfft_tune_clear()
-    with mxfft.Plan(256, 256, "e4m3", 32) as p:
+    with mxfft.Plan(256, 256, "e4m3", k) as p:
         want = p.roundtrip(x).cpu().numpy()
         n = mxfft.mxfft_tune(p.handle, 8)
         assert n >= 2

@@ -49,9 +49,11 @@ WORKLOADS = {
                               config_id=5, desc="8 x 2048x2048 phantoms, MXFP8 e4m3, k=32; "
                                                 "forward + round trip"),
 }
-DEFAULT_WORKLOAD = "batch64_256x256"
+DEFAULT_WORKLOAD = "multicoil_16x32_512x512"
 TRANSFORMS_PER_STEP = 3          # forward + (forward + inverse) of the round trip
 ALG_BYTES_PER_PT = 16            # read complex64 once + write once, per transform
+PASS_BYTES_PER_PT = 8            # a row or column pass launch: half a transform's bytes
+CPU_SUBSET_SLICES = 4            # fixed oracle sample for slices of 512x512 and more
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -125,6 +127,27 @@ def load_peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def dtype_label(fmt):
+    """The arithmetic the path computes in: MX element format + FP32."""
+    if fmt == "fp16":
+        return "fp16 products, f32 accumulate"
+    kind = {"e4m3": "mxfp8", "e5m2": "mxfp8", "e2m3": "mxfp6", "e3m2": "mxfp6",
+            "e2m1": "mxfp4"}[fmt]
+    return f"{kind}-{fmt} elements, e8m0 block scales, f32 accumulate"
+
+
+def oracle_sample_slices(w, cores):
+    """Slices of the oracle's bounded sample: the fixed 4-slice subset for
+    slices of 512x512 and more, else one slice per core."""
+    n = w["n0"] * w["n1"]
+    total = w["nslices"] * w["ncoils"]
+    if n >= 1 << 20:
+        return 1
+    if n >= 1 << 18:
+        return min(total, CPU_SUBSET_SLICES)
+    return min(total, max(cores, 1))
 
 
 # sources each kernel is compiled from (its own file(s) and the shared headers)
@@ -242,11 +265,9 @@ def run_reference(args, w, world, rank):
     import oracle
     from paper_2512_04317_gb300 import phantom
     oracle.build()
-    cores = oracle.num_threads()
-    ns = min(w["nslices"] * w["ncoils"], max(cores, 1))
+    ns = oracle_sample_slices(w, oracle.num_threads())
+    cores = min(oracle.num_threads(), ns)       # OpenMP runs over the sample's slices
     n0, n1 = w["n0"], w["n1"]
-    if n0 * n1 >= 1 << 20:
-        ns = 1
     ksp = phantom.mri_batch(n0, n1, ns, 1, config_id=w["config_id"])
     img = phantom.mri_batch(n0, n1, ns, 1, config_id=w["config_id"], domain="image")
     times = []
@@ -265,7 +286,8 @@ def run_reference(args, w, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpts/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(w["fmt"]),
+        "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "sample": sample},
         "cpu_baseline": {"value": value, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -276,12 +298,15 @@ def run_reference(args, w, world, rank):
 
 def cpu_baseline(w, ksp, img):
     import oracle
-    cores = oracle.num_threads()
-    ns = ksp.shape[0]
     n0, n1 = w["n0"], w["n1"]
-    # bounded sample: about 10-30 s of CPU work
-    per_slice_core_s = 0.3 * (n0 * n1) / 65536 * max(1.0, (n0 * n1) ** 0.5 / 256) ** 0.1
-    ns = int(max(1, min(ns, 25.0 / per_slice_core_s)))
+    if n0 * n1 >= 1 << 18:
+        # the fixed subset of the large configurations
+        ns = min(ksp.shape[0], CPU_SUBSET_SLICES)
+    else:
+        # bounded sample: about 10-30 s of CPU work
+        per_slice_core_s = 0.3 * (n0 * n1) / 65536 * max(1.0, (n0 * n1) ** 0.5 / 256) ** 0.1
+        ns = int(max(1, min(ksp.shape[0], 25.0 / per_slice_core_s)))
+    cores = min(oracle.num_threads(), ns)       # OpenMP runs over the sample's slices
     # whole passes over the sample until at least 10 s (at most ~30 s) of wall time
     t0 = time.perf_counter()
     reps = 0
@@ -419,29 +444,53 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
     gc.collect()
     gc_was_enabled = gc.isenabled()
     gc.disable()
+    run_mx(0.0)                      # warm-up phase (first use of kernels and plans), not reported
     wall, lat, batches = run_mx(0.0)
     sat = n_req / wall
     out["saturated"] = {"req_per_s": sat, "mpts_per_s": pts_total / wall / 1e6,
                         "batches": batches, "p50_ms": _pct(lat)[0], "p99_ms": _pct(lat)[1]}
+    fsat = None
     if fp32:
         fw, flat = run_fp32(0.0)
-        out["fp32_per_slice_saturated"] = {"req_per_s": n_req / fw,
+        fsat = n_req / fw
+        out["fp32_per_slice_saturated"] = {"req_per_s": fsat,
                                            "mpts_per_s": pts_total / fw / 1e6,
                                            "p50_ms": _pct(flat)[0], "p99_ms": _pct(flat)[1]}
+    # Poisson arrivals at fractions of the MX server's saturated rate, every
+    # phase run twice (repeat spread of p99); the FP32 path under the same
+    # arrivals is far past its own capacity there (queue growth)
     out["poisson"] = []
     for frac in (rates if rates else fractions):
         rate = frac if rates else frac * sat
-        wall, lat, batches = run_mx(rate)
-        p50, p99 = _pct(lat)
+        reps = []
+        for _ in range(2):
+            wall, lat, batches = run_mx(rate)
+            reps.append((_pct(lat), batches, pts_total / wall / 1e6))
+        p99s = [r[0][1] for r in reps]
         ent = {"load": frac, "req_per_s": rate,
-               "mx": {"p50_ms": p50, "p99_ms": p99, "batches": batches,
-                      "mpts_per_s": pts_total / wall / 1e6}}
+               "mx": {"p50_ms": reps[-1][0][0], "p99_ms": reps[-1][0][1],
+                      "p50_ms_repeats": [r[0][0] for r in reps], "p99_ms_repeats": p99s,
+                      "p99_spread": max(p99s) / max(min(p99s), 1e-9),
+                      "batches": reps[-1][1], "mpts_per_s": reps[-1][2]}}
         if fp32:
             fw, flat = run_fp32(rate)
             f50, f99 = _pct(flat)
             ent["fp32_per_slice"] = {"p50_ms": f50, "p99_ms": f99,
-                                     "mpts_per_s": pts_total / fw / 1e6}
+                                     "mpts_per_s": pts_total / fw / 1e6,
+                                     "note": "same arrivals: above the FP32 path's capacity"}
         out["poisson"].append(ent)
+    # like for like: arrivals at fractions of the FP32 path's own saturated
+    # rate, each path at the same arrival times
+    if fp32 and not rates:
+        out["poisson_at_fp32_load"] = []
+        for frac in fractions:
+            rate = frac * fsat
+            fw, flat = run_fp32(rate)
+            wall, lat, batches = run_mx(rate)
+            out["poisson_at_fp32_load"].append({
+                "load_of_fp32_capacity": frac, "req_per_s": rate,
+                "fp32_per_slice": {"p50_ms": _pct(flat)[0], "p99_ms": _pct(flat)[1]},
+                "mx": {"p50_ms": _pct(lat)[0], "p99_ms": _pct(lat)[1], "batches": batches}})
     if gc_was_enabled:
         gc.enable()
     del work
@@ -515,6 +564,24 @@ def accuracy(plan, xk, xi, torch):
     return out
 
 
+def timed_steps(torch, run, steps, flush, stream, world, dist, dev, barrier):
+    """Device time of `steps` calls of run(): CUDA events on the launch stream
+    around each step, L2 flushed between steps (outside the events), barrier
+    and synchronize on both sides, max over ranks.  Returns the job ms."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    barrier()
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        evs[i][0].record(stream)
+        run()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return job_time_ms(sum(a.elapsed_time(b) for a, b in evs), world, dist, dev)
+
+
 def main():
     args = parse()
     w = dict(WORKLOADS[args.workload])
@@ -586,22 +653,11 @@ def main():
     torch.cuda.synchronize()
 
     # ---- device-timed region: K steps, L2 flushed between them ----------------
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     clocks = ClockSampler(local, enabled=not args.no_clocks)
-    barrier()
-    torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(i & 0xff)
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    t_ms = timed_steps(torch, step, args.steps, flush, stream, world, dist, dev, barrier)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    t_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evs), world, dist, dev)
     ms_per_step = t_ms / args.steps
     value = job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, t_ms)
 
@@ -615,23 +671,37 @@ def main():
                   ("roundtrip_fused", xi, yf, w["fmt"], w["k"])]
         for _ in range(args.warmup):
             engine.run(work_f)
-        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        barrier()
-        for i in range(args.steps):
-            flush.fill_(i & 0xff)
-            evf[i][0].record(stream)
-            engine.run(work_f)
-            evf[i][1].record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        tf_ms = job_time_ms(sum(a.elapsed_time(b) for a, b in evf), world, dist, dev)
+        tf_ms = timed_steps(torch, lambda: engine.run(work_f), args.steps, flush, stream, world,
+                            dist, dev, barrier)
         fused = {"value": job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, tf_ms),
                  "unit": "Mpts/s", "ms_per_step": tf_ms / args.steps,
                  "speedup_vs_separate_round_trip": ms_per_step / (tf_ms / args.steps),
                  "launches_per_step": 6,
                  "step": "forward of the k-space batch + fused round trip of the image batch"}
+
+    # ---- the tensor-core radix-16 variant (Sec. 4.2 note; approximate, within
+    # the stated NRMSE) on the same workload and step, timed the same way ---
+    tc_leg = None
+    if args.path == "radix2" and engine is not None and mxfft.tc16_supported(n0, n1, w["fmt"], w["k"]):
+        eng_tc = mxfft.Engine(graphs=True, tc16=True)
+        ytk, yti = torch.empty_like(xk), torch.empty_like(xi)
+        work_tc = [("forward", xk, ytk, w["fmt"], w["k"]), ("roundtrip", xi, yti, w["fmt"], w["k"])]
+        for _ in range(args.warmup):
+            eng_tc.run(work_tc)
+        tt_ms = timed_steps(torch, lambda: eng_tc.run(work_tc), args.steps, flush, stream, world,
+                            dist, dev, barrier)
+        tt_step = tt_ms / args.steps
+        with mxfft.Plan(n0, n1, w["fmt"], w["k"], path="tc16") as ptc:
+            tc_acc = accuracy(ptc, xk, xi, torch)
+        tc_leg = {"value": job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, tt_ms),
+                  "unit": "Mpts/s", "ms_per_step": tt_step,
+                  "hbm_roofline_frac_per_transform":
+                      pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (tt_step * 1e-3) / 1e9
+                      / load_peaks()[0],
+                  "accuracy_vs_fp64": tc_acc,
+                  "launches_per_step": eng_tc.launches_per_run(),
+                  "step": "the same engine run (forward + round trip) on tensor-core plans"}
+        eng_tc.close()
 
     # ---- per-kernel device time (event pairs around each launch on the launch
     # stream; the same kernels through the plan calls, since launches inside a
@@ -647,16 +717,26 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
     avg_ms = dom_ms / max(dom_n, 1)
-    bytes_per_launch = 8 * pts if dom == "stats_kernel" else ALG_BYTES_PER_PT * pts
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
     peak, peak_src = load_peaks()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(dom, args.workload,
-                                                                      pts),
+    # the headline fraction counts 16 B per point per transform (read the
+    # complex64 input once, write the output once) over the step's device time
+    whole_gbs = pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (ms_per_step * 1e-3) / 1e9
+    # the dominant kernel per launch, at its own algorithmic bytes: 8 B per
+    # point for a statistics launch (read) and for a row or column pass
+    # (half a transform), 16 B per point for a whole-transform launch
+    dom_bpp = mxfft.KERNEL_ALG_BYTES_PER_PT.get(dom, PASS_BYTES_PER_PT)
+    dom_gbs = dom_bpp * pts / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": whole_gbs, "peak": peak, "unit": "GB/s",
+                "frac": whole_gbs / peak,
+                "traffic": recorded_traffic(dom, args.workload, pts),
+                "basis": f"{ALG_BYTES_PER_PT} B per point per transform x {pts} points x "
+                         f"{TRANSFORMS_PER_STEP} transforms / ms_per_step",
                 "kernel": dom, "avg_launch_ms": avg_ms, "peak_source": peak_src,
+                "dominant_kernel": {"kernel": dom, "avg_launch_ms": avg_ms, "launches": dom_n,
+                                    "alg_bytes_per_point_per_launch": dom_bpp,
+                                    "achieved": dom_gbs, "frac": dom_gbs / peak},
                 "kernel_share": {k: v[0] / max(sum(x[0] for x in prof.values()), 1e-12)
                                  for k, v in prof.items()}}
-    whole = pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (ms_per_step * 1e-3) / 1e9
     # instruction-issue roofline of the same kernel: one warp instruction per
     # scheduler and cycle, 4 schedulers of 32 lanes per SM, at the sampled clock
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -785,7 +865,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": dtype_label(w["fmt"]), "data": "synthetic",
             "config": {"workload": args.workload, "desc": w["desc"], "path": args.path,
                        "api": args.api, "tuning": tuning,
                        "n0": n0, "n1": n1,
@@ -793,13 +873,14 @@ def main():
                        "transforms_per_step": TRANSFORMS_PER_STEP,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "hbm_roofline_frac_whole_step": whole / peak,
             "roofline": roofline,
+            "tensor_core_variant": tc_leg,
             "roofline_alu": roofline_alu,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Mpts/s", "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io, "steps": e2e_steps, "mode": e2e_mode},
             "gpu_launches": launches_per_step * args.steps,
+            "launches_per_step": launches_per_step,
             "accuracy_vs_fp64": acc,
             "device_status": st,
             "fp32_cufft_comparator": {"per_slice_mpts_s": per_slice_fp32,

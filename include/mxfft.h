@@ -166,12 +166,12 @@ int mxfft_roundtrip_fused(mxfft_plan_t plan, const void *in, void *out, int batc
  * mxfft_get_status -- after the stream of the last call has been synchronised
  * (this function synchronises it), report what the device saw in that call.
  *   device_flags  nullable; receives bit 0 = some slice had a non-finite
- *                 magnitude (its k was forced to 0, its output is undefined).
+ *                 magnitude (its k was forced to 0, its output is undefined),
+ *                 bit 1 = a bounded wait of the tensor-core path gave up (its
+ *                 output is undefined).
  *   k_out         nullable; receives the prescale exponents of the last call:
  *                 [batch] for forward / inverse / fused round trip,
  *                 [batch][2] (forward k, inverse k) for the round trip.
- *                 bit 1 = a bounded wait of the tensor-core path gave up (its
- *                 output is undefined).
  * Returns MXFFT_ERR_NONFINITE when bit 0 is set, MXFFT_ERR_TIMEOUT when bit 1
  * is set, else MXFFT_OK (or a CUDA error).
  */
@@ -190,8 +190,9 @@ int mxfft_destroy(mxfft_plan_t plan);
  * and the launch count launches[i], and clears the records.  Kinds:
  * 0 = statistics kernel (Alg. 1), 1 = generic MX butterfly pass kernel,
  * 2 = register-resident MX butterfly pass kernel (rows and columns of
- * length 64..2048 with k <= 32), 3 = tensor-core radix-16 pass kernel.  Returns MXFFT_ERR_INVALID for a NULL plan
- * or nkinds < 1.
+ * length 64..2048 with k <= 32, and of length 128..2048 with k = 64 or 128),
+ * 3 = tensor-core radix-16 pass kernel.  Returns MXFFT_ERR_INVALID for a NULL
+ * plan or nkinds < 1.
  */
 int mxfft_profile(mxfft_plan_t plan, int enable);
 int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int nkinds);
@@ -204,9 +205,9 @@ int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int n
  * that runs inside another framework's fixed memory pool, a real-time
  * acquisition and reconstruction loop that must not reach the CUDA allocator,
  * or code that has already committed all free device memory.  It computes the
- * Alg. 1 prescale exponent k of each of `batch` slices (the statistics kernel
- * of the transforms) without a plan and without any cudaMalloc, cudaFree or
- * allocating library call.
+ * prescale exponent k of each of `batch` slices -- the same exponents that
+ * mxfft_forward selects for them, by the same statistics kernel -- without a
+ * plan and without any cudaMalloc, cudaFree or allocating library call.
  *   in      device pointer to [batch][n0][n1] complex64, 16-byte aligned.
  *   batch   0 .. MXFFT_NOALLOC_MAX_SLICES; a larger batch returns
  *           MXFFT_ERR_INVALID because the scratch is a fixed static array
@@ -217,14 +218,19 @@ int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int n
  *           written asynchronously on `stream`; a slice holding a non-finite
  *           magnitude gets 0, like the transforms.
  * Scratch: one file-scope device array of MXFFT_NOALLOC_MAX_SLICES per-slice
- * records (about 1.2 MB), which every GPU that loads this library keeps until
- * the process exits.  Every call uses it and it keeps the last call's
+ * records (about 1.2 MB).  Every call uses it and it keeps the last call's
  * contents; each call clears the records it needs first.  Calls that overlap
  * on the GPU (two streams, or two host threads without ordering) race on it:
  * serialise them.
- * Set-up: the first call on a device, made with that device current, looks up
- * the array's device address once (cudaGetSymbolAddress); make that first call
- * before any stream capture.
+ * Set-up: the CUDA runtime loads this library's device code, array included,
+ * lazily, on a device's first use of it; from then on the device holds the
+ * array until the process exits.  The first call on a device, made with that
+ * device current, looks up the array's device address (cudaGetSymbolAddress)
+ * and so may be the call that loads the module, which itself takes device
+ * memory.  Make that first call at initialisation time, while memory is still
+ * free and before any stream capture; later calls allocate nothing.  After a
+ * cudaDeviceReset the next call looks the address up again in the new
+ * context (and loads the module again).
  */
 #define MXFFT_NOALLOC_MAX_SLICES 1024
 int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, int format,
@@ -291,6 +297,10 @@ typedef struct mxfft_engine_s *mxfft_engine_t;
 int mxfft_engine_create(float tau, float target, int flags, mxfft_engine_t *out);
 int mxfft_engine_run(mxfft_engine_t e, const mxfft_item *items, int n_items, void *stream);
 int mxfft_engine_get_status(mxfft_engine_t e, int *device_flags, int32_t *k_out, int k_out_len);
+/* mxfft_engine_launches -- number of kernels the last mxfft_engine_run
+ *   enqueued (for a graph replay: the kernels of the captured graph); 0
+ *   before the first run.  MXFFT_ERR_INVALID for NULL arguments. */
+int mxfft_engine_launches(mxfft_engine_t e, int *launches);
 int mxfft_engine_destroy(mxfft_engine_t e);
 
 /* ======================================================================

@@ -73,6 +73,7 @@ struct RunBuffers {
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     RunBuffers buf;
+    int launches = 0;     // kernels in the captured graph
 };
 
 size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -163,6 +164,7 @@ struct mxfft_engine_s {
     int last_slices = 0;
     std::vector<char> last_rt;
     std::vector<mxfft_plan_s*> last_plans;
+    int last_launches = 0;                      // kernels the last run enqueued
 };
 
 namespace {
@@ -515,7 +517,12 @@ int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, voi
     // the tables go up (stream-ordered, from the pinned staging buffer) only
     // when they differ from the last upload into these buffers
     cudaError_t err = cudaSuccess;
-    if (changed) err = cudaMemcpyAsync(b->d_blob, b->h_blob, L.bytes, cudaMemcpyHostToDevice, s);
+    // an earlier run of these buffers may still be on another stream: it
+    // reads the same statistics records that this run clears first, so this
+    // stream waits for it on the device (no host synchronisation)
+    if (b->pending) err = cudaStreamWaitEvent(s, b->done, 0);
+    if (err == cudaSuccess && changed)
+        err = cudaMemcpyAsync(b->d_blob, b->h_blob, L.bytes, cudaMemcpyHostToDevice, s);
     if (err != cudaSuccess) return cuda_status(err);
     if (g) {
         if (!g->exec) {
@@ -524,7 +531,9 @@ int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, voi
             cudaGraph_t graph = nullptr;
             err = cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal);
             if (err == cudaSuccess) {
+                const long long n0 = g_kernel_launches.load();
                 cudaError_t e1 = enqueue(e, L, *b, e->capture);
+                g->launches = (int)(g_kernel_launches.load() - n0);
                 cudaError_t e2 = cudaStreamEndCapture(e->capture, &graph);
                 err = e1 != cudaSuccess ? e1 : e2;
             }
@@ -536,8 +545,11 @@ int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, voi
             }
         }
         err = cudaGraphLaunch(g->exec, s);
+        e->last_launches = g->launches;
     } else {
+        const long long n0 = g_kernel_launches.load();
         err = enqueue(e, L, *b, s);
+        e->last_launches = (int)(g_kernel_launches.load() - n0);
     }
     if (err == cudaSuccess) err = cudaEventRecord(b->done, s);
     if (err != cudaSuccess) return cuda_status(err);
@@ -549,6 +561,12 @@ int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, voi
     for (auto* p : item_plan)
         if (p && std::find(e->last_plans.begin(), e->last_plans.end(), p) == e->last_plans.end())
             e->last_plans.push_back(p);
+    return MXFFT_OK;
+}
+
+int mxfft_engine_launches(mxfft_engine_t e, int* launches) {
+    if (!e || !launches) return MXFFT_ERR_INVALID;
+    *launches = e->last_launches;
     return MXFFT_OK;
 }
 

@@ -248,6 +248,7 @@ cudaError_t launch_fast_dim(const FastArgs& fa, int logm, int blocks, int thread
         smem_limit[logm] = smem;
     }
     k<<<blocks, threads, smem, s>>>(fa);
+    note_launch();
     return cudaGetLastError();
 }
 

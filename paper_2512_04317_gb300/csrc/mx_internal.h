@@ -5,7 +5,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace mxfft {
+
+// Kernel launches made by this library in the process (each launcher adds
+// one per kernel it enqueues); the executor reports per-run differences.
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Element-format constants in the form the device quantiser uses.
 struct FmtParams {

@@ -1,14 +1,15 @@
-// Allocation-free variant of the prescale statistics kernel (Alg. 1).
+// Allocation-free variant of the prescale statistics kernel.
 //
 // Some callers cannot allocate device memory when they call in: a host
 // thread working inside another framework's fixed memory pool, a real-time
 // reconstruction loop that is not allowed to reach the CUDA allocator between
 // acquisitions, or code that has already committed every free byte of the GPU.
-// mxfft_prescale_exponents_noalloc serves them: it computes the Alg. 1 exponent
-// k of every slice with no cudaMalloc, cudaFree or allocating library call.
-// Its per-slice scratch (histogram, maxima, counters) lives in the file-scope
-// array below, which every GPU that loads this library holds until the
-// process exits.
+// mxfft_prescale_exponents_noalloc serves them: it computes the prescale
+// exponent k of every slice (the same exponents mxfft_forward uses) with no
+// cudaMalloc, cudaFree or allocating library call.  Its per-slice scratch
+// (histogram, maxima, counters) lives in the file-scope array below, which
+// every GPU that loads this library's device code holds until the process
+// exits.
 #include <cmath>
 #include <mutex>
 
@@ -52,20 +53,55 @@ stats_noalloc_kernel(const float2* __restrict__ x, int npts, SliceStats* __restr
     if (sh_misc[3] && tid == 0) k_out[slice] = st[slice].k;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device and
+// context.  The context's unique id (cuCtxGetId) is kept beside the address:
+// after the caller resets the device (cudaDeviceReset) the next call runs in
+// a new context, where the module and its array are loaded again, possibly
+// elsewhere, so the address is looked up again.  The two driver entry points
+// come through the runtime, so the library needs no link-time libcuda.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 SliceStats* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if unavailable).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int scratch_for_current_device(SliceStats** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MXFFT_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    // id 0: no context is current yet (the lookup below creates the primary one)
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         // the symbol's host-side name is not a device address; ask the runtime
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MXFFT_ERR_CUDA;
         g_scratch_ptr[dev] = static_cast<SliceStats*>(p);
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_ptr[dev];
     return MXFFT_OK;

@@ -252,6 +252,7 @@ cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s) {
         attr_set = true;
     }
     pass_kernel<<<batch * per_slice, kPassThreads, smem, s>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 

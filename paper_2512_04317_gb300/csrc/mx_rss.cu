@@ -47,6 +47,7 @@ cudaError_t launch_rss(const RssRef& val, const RssRef* dev, long long images, l
                        cudaStream_t s) {
     if (images <= 0 || npts <= 0) return cudaSuccess;
     rss_kernel<<<rss_grid(images, npts), kRssThreads, 0, s>>>(val, dev);
+    note_launch();
     return cudaGetLastError();
 }
 

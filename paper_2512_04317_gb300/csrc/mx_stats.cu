@@ -61,12 +61,14 @@ cudaError_t launch_stats(const float2* x, int batch, int n0, int n1, SliceStats*
     const uint32_t per = (uint32_t)((npts + kStatsPtsPerCta - 1) / kStatsPtsPerCta);
     dim3 grid(per, batch);
     stats_kernel<<<grid, kStatsThreads, 0, s>>>(x, npts, st, kp, per);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_stats_ref(const StatsRef* refs, const int2* cta_tab, int nctas, cudaStream_t s) {
     if (nctas <= 0) return cudaSuccess;
     stats_ref_kernel<<<nctas, kStatsThreads, 0, s>>>(refs, cta_tab);
+    note_launch();
     return cudaGetLastError();
 }
 

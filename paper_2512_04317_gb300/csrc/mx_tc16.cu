@@ -722,6 +722,7 @@ cudaError_t launch_one(const Args& a, cudaStream_t s) {
     const int ntiles = a.batch * (other / G::T);
     const int blocks = ntiles < resident ? ntiles : resident;
     k<<<blocks, kThreads, smem, s>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -367,6 +367,8 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
 
 namespace mxfft {
 
+std::atomic<long long> g_kernel_launches{0};
+
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return MXFFT_OK;
     if (e == cudaErrorMemoryAllocation) return MXFFT_ERR_NOMEM;

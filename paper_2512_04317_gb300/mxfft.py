@@ -32,7 +32,7 @@ EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
            "mxfft_roundtrip", "mxfft_roundtrip_fused", "mxfft_get_status", "mxfft_destroy", "mxfft_profile",
            "mxfft_profile_read", "mxfft_prescale_exponents_noalloc",
            "mxfft_engine_create", "mxfft_engine_run", "mxfft_engine_get_status",
-           "mxfft_engine_destroy", "mxfft_tune", "mxfft_tune_save", "mxfft_tune_load",
+           "mxfft_engine_launches", "mxfft_engine_destroy", "mxfft_tune", "mxfft_tune_save", "mxfft_tune_load",
            "mxfft_tune_clear", "mxfft_server_create", "mxfft_server_submit",
            "mxfft_server_poll", "mxfft_server_wait", "mxfft_server_stats",
            "mxfft_server_destroy", "mxfft_rss", "mxfft_status_string")
@@ -73,6 +73,21 @@ _lock = threading.Lock()
 _lib = None
 
 
+# algorithmic bytes per point of one launch of a kernel (profiling kinds of
+# mxfft_profile_read): a statistics launch reads the slice once; a row or
+# column pass moves half of a transform's 16 B per point
+KERNEL_ALG_BYTES_PER_PT = {"stats_kernel": 8, "pass_kernel": 8, "fast_pass_kernel": 8,
+                           "tc16_pass_kernel": 8}
+
+
+def tc16_supported(n0: int, n1: int, fmt, k: int) -> bool:
+    """Whether a plan of this shape, format and k can take the tensor-core
+    variant (MXFFT_OPT_PATH = 1)."""
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    return (n0 in (256, 512, 1024, 2048) and n1 in (256, 512, 1024, 2048) and f in (0, 1)
+            and k in (32, 64, 128))
+
+
 class MxfftError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -107,6 +122,7 @@ def load(path: str | None = None):
         lib.mxfft_engine_create.argtypes = [F, F, I, PP]
         lib.mxfft_engine_run.argtypes = [P, ctypes.POINTER(Item), I, P]
         lib.mxfft_engine_get_status.argtypes = [P, P, P, I]
+        lib.mxfft_engine_launches.argtypes = [P, P]
         lib.mxfft_engine_destroy.argtypes = [P]
         lib.mxfft_tune.argtypes = [P, I, P, P]
         lib.mxfft_tune_save.argtypes = [ctypes.c_char_p]
@@ -252,6 +268,13 @@ def mxfft_engine_get_status(engine, k_count: int = 0):
     _check(load().mxfft_engine_get_status(engine, ctypes.byref(flags), karr if k_count else None,
                                           int(k_count)), "mxfft_engine_get_status")
     return flags.value, list(karr)[:k_count]
+
+
+def mxfft_engine_launches(engine) -> int:
+    """Kernels the engine's last run enqueued (a graph replay: its kernels)."""
+    n = ctypes.c_int(0)
+    _check(load().mxfft_engine_launches(engine, ctypes.byref(n)), "mxfft_engine_launches")
+    return n.value
 
 
 def mxfft_engine_destroy(engine) -> None:
@@ -463,6 +486,10 @@ class Engine:
             stream = torch.cuda.current_stream(dev).cuda_stream
         mxfft_engine_run(self.handle, items, stream)
         self._slices = sum(it.slices for it in items)
+
+    def launches_per_run(self) -> int:
+        """Kernels the last run enqueued."""
+        return mxfft_engine_launches(self.handle)
 
     def status(self):
         """(device_flags, [[k, k_inverse] per slice]) of the last run."""

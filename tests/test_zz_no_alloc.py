@@ -51,6 +51,28 @@ def test_noalloc_exponents_equal_plan_path_on_two_calls_in_a_row(cuda_device):
         assert got == want, (fmt, got, want)
 
 
+def test_noalloc_calls_after_the_first_take_no_device_memory(cuda_device):
+    """After the set-up call (which may load the library's device code), a
+    call leaves both the device's free memory and torch's allocator as they
+    were: its scratch is the static array, nothing else."""
+    import torch
+    x = torch.from_numpy(phantom.mri_batch(128, 128, 6, 1, config_id=13)).to(cuda_device)
+    k = torch.zeros(6, dtype=torch.int32, device=cuda_device)
+    stream = torch.cuda.current_stream(cuda_device).cuda_stream
+    args = (x.data_ptr(), 6, 128, 128, "e4m3", 1e-3, 0.5, k.data_ptr(), stream)
+    assert mxfft.mxfft_prescale_exponents_noalloc(*args) == mxfft.MXFFT_OK   # set-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(cuda_device)
+    alloc0 = torch.cuda.memory_allocated(cuda_device)
+    for _ in range(3):
+        assert mxfft.mxfft_prescale_exponents_noalloc(*args) == mxfft.MXFFT_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(cuda_device)
+    assert free1 == free0
+    assert torch.cuda.memory_allocated(cuda_device) == alloc0
+    assert k.cpu().tolist() == plan_exponents(x, "e4m3")
+
+
 def test_noalloc_rejects_batches_beyond_its_scratch(cuda_device):
     import torch
     x = torch.zeros(2, 4, 4, dtype=torch.complex64, device=cuda_device)

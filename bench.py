@@ -154,7 +154,8 @@ def oracle_sample_slices(w, cores):
 KERNEL_SOURCES = {
     "fast_pass_kernel": ("mx_fast", "mx_device.cuh", "mx_internal.h"),
     "pass_kernel": ("mx_pass.cu", "mx_device.cuh", "mx_internal.h"),
-    "tc16_pass_kernel": ("mx_tc16.cu", "mx_device.cuh", "mx_internal.h"),
+    "tc16_pass_kernel": ("mx_tc16.cu", "mx_tcgen05.cuh", "mx_device.cuh", "mx_internal.h"),
+    "tc2d_kernel": ("mx_tc2d.cu", "mx_tcgen05.cuh", "mx_device.cuh", "mx_internal.h"),
     "stats_kernel": ("mx_stats.cu", "mx_device.cuh", "mx_internal.h"),
 }
 

@@ -83,12 +83,24 @@ typedef enum {
                                radix-16 stages; approximate, not bit-exact.
                                Needs n0, n1 in {256, 512, 1024, 2048} and format E4M3 or E5M2, else
                                MXFFT_ERR_UNSUPPORTED. */,
-    MXFFT_OPT_TEST_STALL = 5  /* test hook of the bounded wait, 0 or 1; default 0.  1: the
-                               tensor-core pass withholds its matrix products, so every CTA's
-                               wait for their completion runs out (after 100 ms), the CTA
-                               stops, and mxfft_get_status returns MXFFT_ERR_TIMEOUT (device
-                               flag bit 1); the outputs of such a call are undefined.  No
-                               effect on the radix-2 path. */
+    MXFFT_OPT_TEST_STALL = 5, /* test hook of the bounded wait, 0 or 1; default 0.  1: the
+                               tensor-core kernels withhold their matrix products, so every
+                               CTA's wait for their completion runs out (after 100 ms), the CTA
+                               stops issuing work, and mxfft_get_status returns
+                               MXFFT_ERR_TIMEOUT (device flag bit 1); the outputs of such a
+                               call are undefined.  No effect on the radix-2 path. */
+    MXFFT_OPT_FUSED2D = 6     /* tensor-core path only, 0 or 1; default 1.  1: forward,
+                               inverse and round trip of n0, n1 in {256, 512} with k = 32 run
+                               as one fused kernel per transform: each slice is spread over
+                               one thread-block cluster (n0 n1 / 16384 CTAs, one per SM), its
+                               prescale statistics (Alg. 1) are reduced on chip, and rows and
+                               columns are transformed without the slice leaving the chip
+                               (16 bytes of HBM traffic per point and transform).  Same
+                               arithmetic per element as the per-axis tensor-core passes.
+                               0: the statistics pass and the two per-axis passes.  When the
+                               device cannot hold the cluster the passes run instead.  The
+                               fused round trip (mxfft_roundtrip_fused) always runs the
+                               passes. */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;
@@ -191,8 +203,9 @@ int mxfft_destroy(mxfft_plan_t plan);
  * 0 = statistics kernel (Alg. 1), 1 = generic MX butterfly pass kernel,
  * 2 = register-resident MX butterfly pass kernel (rows and columns of
  * length 64..2048 with k <= 32, and of length 128..2048 with k = 64 or 128),
- * 3 = tensor-core radix-16 pass kernel.  Returns MXFFT_ERR_INVALID for a NULL
- * plan or nkinds < 1.
+ * 3 = tensor-core radix-16 pass kernel, 4 = fused 2D tensor-core kernel (a
+ * whole transform per launch).  Returns MXFFT_ERR_INVALID for a NULL plan or
+ * nkinds < 1.
  */
 int mxfft_profile(mxfft_plan_t plan, int enable);
 int mxfft_profile_read(mxfft_plan_t plan, double *total_ms, int *launches, int nkinds);

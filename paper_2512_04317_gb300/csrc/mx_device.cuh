@@ -102,12 +102,12 @@ __device__ __forceinline__ float mag_c3_fast(float re, float im) {
 //   k2 = ceil(log2(2^e_tau / max(p_tau, 1e-30))) = e_tau - max(floor(log2 p_tau), -100)
 //        (floor(log2 1e-30) = -100), and floor(log2 p_tau) is the histogram bin
 //        holding rank r = floor(fl32(tau * fl32(n_nz - 1))) of the sorted nonzeros.
-// Called by one full warp; returns k in every lane.
-__device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams& kp) {
+// Called by one full warp with the slice's totals (hist_at(bin) returns the
+// count of a bin); returns k in every lane.
+template <class HistAt>
+__device__ __forceinline__ int select_k_core(uint32_t nonfinite, uint32_t ab, uint32_t nnz,
+                                             HistAt hist_at, const KParams& kp) {
     const int lane = threadIdx.x & 31;
-    uint32_t nonfinite = __ldcg(&st->nonfinite);
-    uint32_t ab = __ldcg(&st->amax_bits);
-    uint32_t nnz = __ldcg(&st->nnz);
     if (nonfinite || ab == 0 || nnz == 0) return 0;
     float rf = __fmul_rn(kp.tau, (float)(int)(nnz - 1));
     int r = (int)floorf(rf);
@@ -119,7 +119,7 @@ __device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         int bin = base + i;
-        c[i] = bin < kHistBins ? __ldcg(&st->hist[bin]) : 0u;
+        c[i] = bin < kHistBins ? hist_at(bin) : 0u;
         tot += c[i];
     }
     uint32_t incl = tot;   // inclusive warp scan of the lane totals
@@ -155,6 +155,13 @@ __device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams
     int k2 = kp.taumin_exp - max(ep, -100);
     int k = max(k1, k2);
     return min(max(k, kp.kmin), kp.kmax);
+}
+
+// The selection from a slice's record in global memory (after the atomics of
+// every CTA of the slice).  Called by one full warp; returns k in every lane.
+__device__ __forceinline__ int select_k_warp(const SliceStats* st, const KParams& kp) {
+    return select_k_core(__ldcg(&st->nonfinite), __ldcg(&st->amax_bits), __ldcg(&st->nnz),
+                         [st](int bin) { return __ldcg(&st->hist[bin]); }, kp);
 }
 
 // Accumulates one value's contribution to Alg. 1's statistics in per-thread

@@ -39,6 +39,7 @@ struct PassLaunch {
     int ref0, count;      // slice references [ref0, ref0 + count)
     int branch;           // fork branch within its stage
     int fused = 0;        // 1: forward + inverse columns of the fused round trip
+    int whole = 0;        // 1: the fused 2D kernel (statistics, rows, columns)
 };
 
 // Host image of one run: the device tables and the launches that read them.
@@ -242,11 +243,17 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         L.srefs.push_back(StatsRef{x, st, npts, (uint32_t)ctas, kp});
         for (int c = 0; c < ctas; c++) L.ctas.push_back(make_int2(idx, c));
     };
-    // statistics of every input
+    // slices of plans that run the fused 2D kernel take their statistics on
+    // chip (forward, inverse and both halves of round trips)
+    auto whole2d = [&](int i) {
+        return item_plan[i] && uses_tc2d(item_plan[i]) && items[i].op != MXFFT_OP_ROUNDTRIP_FUSED;
+    };
+    // statistics of every other input
     L.cta1 = 0;
     for (int i = 0; i < n; i++) {
         const mxfft_item& it = items[i];
         const int np = it.n0 * it.n1;
+        if (whole2d(i)) continue;
         for (int s = 0; s < it.slices; s++)
             add_stats((const float2*)it.in + (size_t)s * np, st_base + first[i] + s, np,
                       kparams(item_plan[i]));
@@ -277,6 +284,13 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
                                           st_base + first[i] + s, nullptr});
         }
         const int count = (int)L.refs.size() - rows0;
+        if (kind != 2 && uses_tc2d(p)) {
+            // one launch: statistics, rows and columns of every slice of the group
+            PassLaunch w{p, 2, dir, PRO_PRESCALE, EPI_UNSCALE, rows0, count, (int)gi};
+            w.whole = 1;
+            L.stage1.push_back(w);
+            continue;
+        }
         const int cols0 = (int)L.refs.size();
         for (int r = 0; r < count; r++) {
             SliceRef c = L.refs[rows0 + r];
@@ -301,8 +315,9 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         if (items[i].op != MXFFT_OP_ROUNDTRIP || items[i].slices == 0) continue;
         const int np = items[i].n0 * items[i].n1;
         for (int s = 0; s < items[i].slices; s++) {
-            add_stats((const float2*)items[i].out + (size_t)s * np, st_base + st_cap + first[i] + s,
-                      np, kparams(item_plan[i]));
+            if (!whole2d(i))
+                add_stats((const float2*)items[i].out + (size_t)s * np, st_base + st_cap + first[i] + s,
+                          np, kparams(item_plan[i]));
             L.rt[first[i] + s] = 1;
         }
         if (std::find(rt_plans.begin(), rt_plans.end(), item_plan[i]) == rt_plans.end())
@@ -321,6 +336,12 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
             }
         }
         const int count = (int)L.refs.size() - r0;
+        if (uses_tc2d(p)) {
+            PassLaunch w{p, 2, 1, PRO_PRESCALE, EPI_RT_FINAL, r0, count, (int)gi};
+            w.whole = 1;
+            L.stage2.push_back(w);
+            continue;
+        }
         L.stage2.push_back(PassLaunch{p, 1, 1, PRO_PRESCALE, EPI_RAW, r0, count, (int)gi});
         L.stage2.push_back(PassLaunch{p, 0, 1, PRO_NONE, EPI_RT_FINAL, r0, count, (int)gi});
     }
@@ -359,6 +380,12 @@ cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, i
     }
     for (const PassLaunch& pl : stage) {
         if (err != cudaSuccess) break;
+        if (pl.whole) {
+            Tc2dArgs t = tc2d_args(pl.p, pl.dir, nullptr, nullptr, nullptr, pl.epilogue);
+            t.ref = d_refs + pl.ref0;
+            err = timed_tc2d(pl.p, t, pl.count, nf > 1 ? e->fork[pl.branch % nf] : s);
+            continue;
+        }
         PassArgs a = pass_args(pl.p, pl.dim, pl.dir, nullptr, nullptr);
         a.ref = d_refs + pl.ref0;
         a.prologue = pl.prologue;

@@ -110,6 +110,29 @@ struct Tc16Args {
     int inv;                          // 1: inverse transform (sign of the radix-4 stage)
 };
 
+// Arguments of the fused 2D tensor-core transform (mx_tc2d.cu): every slice
+// [n0][n1] (n0, n1 in {256, 512}) on one thread-block cluster, Alg. 1's
+// statistics taken on chip (k written to the slice's record), rows and
+// columns, the epilogue scaling.
+struct Tc2dArgs {
+    const float2* in;
+    float2* out;
+    const SliceRef* ref;              // as in PassArgs
+    SliceStats* st;
+    int batch, n0, n1;
+    const uint8_t* bmat;              // B operand: 64 x 32 element codes (outputs, then re/im swapped)
+    const float4* twA1;               // rows: [j2 < M1][k1 < 16] (w.re, w.re, -w.im, w.im) x 2^s
+    const float4* twC1;               // rows: [j22 < r1][k21 < 16]
+    const float4* twA0;               // columns
+    const float4* twC0;
+    int epilogue;                     // EPI_UNSCALE, EPI_RT_FINAL (k of this transform) or EPI_RAW
+    int lg_total;
+    uint32_t idesc;                   // tcgen05 instruction descriptor (M 128, N 64)
+    int* err;                         // set when a bounded wait gives up
+    int stall;                        // test hook: issue no matrix product
+    KParams kp;
+};
+
 // One slice of a ragged statistics launch (slices of different sizes and
 // plans in one grid): its points, its record, its point count (even), the
 // number of CTAs that cover it and its plan's selection parameters.
@@ -162,6 +185,14 @@ void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng,
 // The register-resident pass with ng groups per CTA (ng = 0: tuned or default).
 cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                                 int ng, cudaStream_t s);
+// Fused 2D tensor-core transform: n0, n1 in {256, 512}, 8-bit formats, k = 32;
+// cudaErrorNotSupported (launching nothing) when the device cannot hold the
+// kernel's cluster.
+bool tc2d_supported(int n0, int n1, int fmt, int kblk);
+// Clusters of the fused kernel for this shape and format that the current
+// device holds at once (0: it cannot run it).
+int tc2d_resident_clusters(int n0, int n1, int fmt);
+cudaError_t launch_tc2d(const Tc2dArgs& a, int fmt, cudaStream_t s);
 // Tensor-core radix-16 pass: n in {256, 512, 1024}, 8-bit formats, other a multiple
 // of 4096 / n.
 bool tc16_supported(int n, int other, int fmt);

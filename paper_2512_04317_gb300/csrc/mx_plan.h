@@ -34,6 +34,10 @@ struct mxfft_plan_s {
     uint8_t* d_bmat[2];        // [dir] tensor-core DFT matrix codes (core-matrix layout)
     float2* d_twA[2][2];       // [axis][dir] radix-16 stage twiddles
     float2* d_twC[2][2];       // [axis][dir] twiddles before the radix-2 stage (n = 512)
+    uint8_t* d_bmat64[2];      // [dir] the same matrix with N = 64 (outputs, then re/im swapped)
+    float4* d_tw4A[2][2];      // [axis][dir] radix-16 stage twiddles as (re, re, -im, im)
+    float4* d_tw4C[2][2];      // [axis][dir] twiddles before the radix-2 stage
+    int fused2d;               // MXFFT_OPT_FUSED2D: fused 2D transform where it applies
     int* d_err;                // device flag: a bounded wait gave up
     mxfft::SliceStats* d_st;          // 2 * st_cap records: forward, inverse
     int st_cap;
@@ -53,6 +57,14 @@ KParams kparams(const mxfft_plan_s* p);
 // Arguments of a pass of plan p along dim (1 rows, 0 columns) in direction dir
 // (0 forward, 1 inverse); st, prologue and epilogue are left for the caller.
 PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out);
+// Whether a plan's forward / inverse transforms run as the fused 2D
+// tensor-core kernel; its arguments for one launch (dir 0 forward, 1 inverse).
+bool uses_tc2d(const mxfft_plan_s* p);
+Tc2dArgs tc2d_args(const mxfft_plan_s* p, int dir, const float2* in, float2* out, SliceStats* st,
+                   int epilogue);
+// The fused 2D launch (profiled as kind 4); cudaErrorNotSupported when the
+// device cannot run it (the caller then runs the passes).
+cudaError_t timed_tc2d(mxfft_plan_s* p, const Tc2dArgs& a, int batch, cudaStream_t s);
 // Launch one pass over batch slices with the plan's kernel choice.
 cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s);
 cudaError_t fused_cols_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s);

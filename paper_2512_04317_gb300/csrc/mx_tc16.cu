@@ -41,14 +41,16 @@
 #include <stdint.h>
 
 #include "mx_device.cuh"
+#include "mx_tcgen05.cuh"
 
 namespace mxfft {
 namespace tc16 {
 
+using namespace tcg;
+
 constexpr int kThreads = 256;
 constexpr int kTilePts = 4096;        // points per tile = 256 vectors x 16
 constexpr uint32_t kTmemCols = 64;    // two 128 x 32 FP32 accumulators
-constexpr uint64_t kWaitNs = 100000000;   // bound of one completion wait: 100 ms
 // Dynamic shared memory: A operand (2 x 128 rows x 32 B), B operand (32 x 32
 // B), twiddles (rows of 16 padded to 18 values so that a quarter-warp's 16-byte
 // reads of 8 consecutive rows hit distinct banks), then the two tile buffers.
@@ -103,85 +105,6 @@ __device__ __forceinline__ int slot_col(int t, int e) {
 template <int LOGN, int DIM>
 __device__ __forceinline__ int slot(int t, int e) {
     return DIM == 1 ? slot_row<LOGN>(t, e) : slot_col<LOGN>(t, e);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor, K-major without swizzle: an 8-row x 16-byte
-// core matrix is contiguous; K-adjacent core matrices are LBO bytes apart,
-// row-group-adjacent ones SBO bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-template <int FMT> __device__ __forceinline__ uint16_t enc2(float lo, float hi);
-template <> __device__ __forceinline__ uint16_t enc2<0>(float lo, float hi) {
-    unsigned short p;
-    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(p) : "f"(hi), "f"(lo));
-    return p;
-}
-template <> __device__ __forceinline__ uint16_t enc2<1>(float lo, float hi) {
-    unsigned short p;
-    asm("cvt.rn.satfinite.e5m2x2.f32 %0, %1, %2;" : "=h"(p) : "f"(hi), "f"(lo));
-    return p;
-}
-
-__device__ __forceinline__ float fmax_nan(float a, float b) {
-    float d;
-    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
-    return d;
-}
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the mbarrier phase of parity `phase` to complete, at most kWaitNs.
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase) {
-    uint32_t done = 0;
-    const uint64_t t0 = globaltimer_ns();
-    for (;;) {
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
-                     " selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done) : "r"(mbar), "r"(phase));
-        if (done || globaltimer_ns() - t0 > kWaitNs) break;
-    }
-    return done != 0;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&d)[32]) {
-    uint32_t v[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                   "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                   "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-    for (int c = 0; c < 32; c++) d[c] = __uint_as_float(v[c]);
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_prev() {   // all but the newest group
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Shared state of one CTA's MMA rounds.

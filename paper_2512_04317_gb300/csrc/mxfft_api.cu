@@ -155,9 +155,12 @@ void twiddle_block16(long m, long N, int sgn, const FmtHost& f, float2* out) {
 void free_plan_device(mxfft_plan_s* p) {
     for (int d = 0; d < 2; d++) {
         if (p->d_bmat[d]) cudaFree(p->d_bmat[d]);
+        if (p->d_bmat64[d]) cudaFree(p->d_bmat64[d]);
         for (int a = 0; a < 2; a++) {
             if (p->d_twA[a][d]) cudaFree(p->d_twA[a][d]);
             if (p->d_twC[a][d]) cudaFree(p->d_twC[a][d]);
+            if (p->d_tw4A[a][d]) cudaFree(p->d_tw4A[a][d]);
+            if (p->d_tw4C[a][d]) cudaFree(p->d_tw4C[a][d]);
         }
     }
     if (p->d_err) cudaFree(p->d_err);
@@ -247,6 +250,17 @@ int build_tc16_tables(mxfft_plan_s* p) {
         for (float sc : scales)
             if (sc != (float)std::ldexp(1.0, -f.emax)) return MXFFT_ERR_UNSUPPORTED;
         rc = upload(&p->d_bmat[d], codes);
+        // the fused 2D kernel's operand: N = 64 rows, the 32 output rows and
+        // then the same rows with each (re, im) pair swapped, so the product
+        // also yields (im, re) of every output (core-matrix layout as above)
+        std::vector<uint8_t> codes64(2048, 0);
+        for (int nrow = 0; nrow < 64; nrow++) {
+            const int srow = nrow < 32 ? nrow : ((nrow - 32) ^ 1);
+            for (int k = 0; k < 32; k++)
+                codes64[(nrow >> 3) * 256 + (k >> 4) * 128 + (nrow & 7) * 16 + (k & 15)] =
+                    codes[(srow >> 3) * 256 + (k >> 4) * 128 + (srow & 7) * 16 + (k & 15)];
+        }
+        if (rc == MXFFT_OK) rc = upload(&p->d_bmat64[d], codes64);
         for (int axis = 0; axis < 2 && rc == MXFFT_OK; axis++) {
             const int n = axis == 0 ? p->n0 : p->n1;
             const int r = n / 256, M = 16 * r;
@@ -255,6 +269,12 @@ int build_tc16_tables(mxfft_plan_s* p) {
             for (int j22 = 0; j22 < r; j22++) twiddle_block16(j22, M, sgn, f, &twc[(size_t)j22 * 16]);
             rc = upload(&p->d_twA[axis][d], twa);
             if (rc == MXFFT_OK) rc = upload(&p->d_twC[axis][d], twc);
+            // the same twiddles as (re, re, -im, im) for packed multiplies
+            std::vector<float4> t4a(twa.size()), t4c(twc.size());
+            for (size_t i = 0; i < twa.size(); i++) t4a[i] = make_float4(twa[i].x, twa[i].x, -twa[i].y, twa[i].y);
+            for (size_t i = 0; i < twc.size(); i++) t4c[i] = make_float4(twc[i].x, twc[i].x, -twc[i].y, twc[i].y);
+            if (rc == MXFFT_OK) rc = upload(&p->d_tw4A[axis][d], t4a);
+            if (rc == MXFFT_OK) rc = upload(&p->d_tw4C[axis][d], t4c);
         }
     }
     if (rc == MXFFT_OK && !p->d_err) {
@@ -315,6 +335,22 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
     const float2* x = (const float2*)in;
     float2* y = (float2*)out;
     const int dir0 = op == 1 ? 1 : 0;
+    if (op != 3 && uses_tc2d(p)) {
+        // the fused 2D tensor-core transform: statistics, rows and columns of
+        // each slice in one launch (the round trip: forward, then inverse)
+        e = timed_tc2d(p, tc2d_args(p, dir0, x, y, st_f, EPI_UNSCALE), batch, s);
+        if (e == cudaSuccess && op == 2)
+            e = timed_tc2d(p, tc2d_args(p, 1, y, y, st_i, EPI_RT_FINAL), batch, s);
+        if (e != cudaErrorNotSupported) {
+            if (e != cudaSuccess) return cuda_status(e);
+            p->last_batch = batch;
+            p->last_op = op;
+            p->last_stream = s;
+            return MXFFT_OK;
+        }
+        // the device cannot hold the kernel's cluster: the per-axis passes
+        // (nothing was launched)
+    }
     ProfRec* r = prof_begin(p, 0, s);
     e = launch_stats(x, batch, p->n0, p->n1, st_f, kparams(p), s);
     prof_end(r, s);
@@ -410,6 +446,44 @@ PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, fl
     return a;
 }
 
+bool uses_tc2d(const mxfft_plan_s* p) {
+    return p->path == 1 && p->fused2d && tc2d_supported(p->n0, p->n1, p->fmt, p->kblk) &&
+           tc2d_resident_clusters(p->n0, p->n1, p->fmt) > 0;
+}
+
+Tc2dArgs tc2d_args(const mxfft_plan_s* p, int dir, const float2* in, float2* out, SliceStats* st,
+                   int epilogue) {
+    Tc2dArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.in = in;
+    t.out = out;
+    t.st = st;
+    t.n0 = p->n0;
+    t.n1 = p->n1;
+    t.bmat = p->d_bmat64[dir];
+    t.twA1 = p->d_tw4A[1][dir];
+    t.twC1 = p->d_tw4C[1][dir];
+    t.twA0 = p->d_tw4A[0][dir];
+    t.twC0 = p->d_tw4C[0][dir];
+    t.epilogue = epilogue;
+    t.lg_total = ilog2(p->n0) + ilog2(p->n1);
+    const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
+    t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+    t.err = p->d_err;
+    t.stall = p->test_stall;
+    t.kp = kparams(p);
+    return t;
+}
+
+cudaError_t timed_tc2d(mxfft_plan_s* p, const Tc2dArgs& a, int batch, cudaStream_t s) {
+    Tc2dArgs b = a;
+    b.batch = batch;
+    ProfRec* r = prof_begin(p, 4, s);
+    cudaError_t e = launch_tc2d(b, p->fmt, s);
+    prof_end(r, s);
+    return e;
+}
+
 // The tensor-core pass when that path is selected, else the register-resident
 // kernel where it applies (n in [64, 2048], m <= 16; m = 32, 64 for n >= 128),
 // else the generic shared-memory kernel.
@@ -501,6 +575,7 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
     p->taumin_exp = format == MXFFT_E5M2 ? -12 : (format == MXFFT_FP16 ? -24 : -10);
     p->kmin = -126;
     p->kmax = 126;
+    p->fused2d = 1;
     p->fp.emax = f.emax;
     p->fp.emin = f.emin;
     p->fp.mbits = f.mbits;
@@ -597,6 +672,10 @@ int mxfft_set_option(mxfft_plan_t p, int key, double value) {
         case MXFFT_OPT_TEST_STALL:
             if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
             p->test_stall = value != 0.0;
+            return MXFFT_OK;
+        case MXFFT_OPT_FUSED2D:
+            if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
+            p->fused2d = value != 0.0;
             return MXFFT_OK;
         default:
             return MXFFT_ERR_INVALID;

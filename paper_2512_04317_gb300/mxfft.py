@@ -22,7 +22,7 @@ MXFFT_ERR_NONFINITE = 5
 MXFFT_ERR_TIMEOUT = 6
 
 FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
-OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL = 0, 1, 2, 3, 4, 5
+OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL, OPT_FUSED2D = range(7)
 
 OPS = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}
 ENGINE_GRAPHS, ENGINE_TC16 = 1, 2
@@ -77,7 +77,7 @@ _lib = None
 # mxfft_profile_read): a statistics launch reads the slice once; a row or
 # column pass moves half of a transform's 16 B per point
 KERNEL_ALG_BYTES_PER_PT = {"stats_kernel": 8, "pass_kernel": 8, "fast_pass_kernel": 8,
-                           "tc16_pass_kernel": 8}
+                           "tc16_pass_kernel": 8, "tc2d_kernel": 16}
 
 
 def tc16_supported(n0: int, n1: int, fmt, k: int) -> bool:
@@ -208,7 +208,8 @@ def mxfft_profile(plan, enable: bool) -> None:
         raise MxfftError(st, "mxfft_profile")
 
 
-PROFILE_KINDS = ("stats_kernel", "pass_kernel", "fast_pass_kernel", "tc16_pass_kernel")
+PROFILE_KINDS = ("stats_kernel", "pass_kernel", "fast_pass_kernel", "tc16_pass_kernel",
+                 "tc2d_kernel")
 
 
 def mxfft_profile_read(plan):
@@ -374,7 +375,7 @@ class Plan:
     def __init__(self, n0: int, n1: int, fmt="e4m3", k: int = 32, tau: float = 1e-3,
                  target: float = 0.5, tau_min: float | None = None,
                  kmin: int | None = None, kmax: int | None = None, generic: bool = False,
-                 path: str = "radix2"):
+                 path: str = "radix2", fused2d: bool = True):
         self.n0, self.n1, self.fmt, self.k = int(n0), int(n1), fmt, int(k)
         self.handle = mxfft_plan(n0, n1, fmt, k, tau, target)
         self._last = (0, 0)   # (batch, op)
@@ -390,6 +391,8 @@ class Plan:
             raise ValueError(path)
         if path == "tc16":
             mxfft_set_option(self.handle, OPT_PATH, 1)
+            if not fused2d:
+                mxfft_set_option(self.handle, OPT_FUSED2D, 0)
         self.path = path
 
     def _run(self, name, x, out):

@@ -89,7 +89,7 @@ typedef enum {
                                stops issuing work, and mxfft_get_status returns
                                MXFFT_ERR_TIMEOUT (device flag bit 1); the outputs of such a
                                call are undefined.  No effect on the radix-2 path. */
-    MXFFT_OPT_FUSED2D = 6     /* tensor-core path only, 0 or 1; default 1.  1: forward,
+    MXFFT_OPT_FUSED2D = 6     /* tensor-core path only, 0 or 1; default 0.  1: forward,
                                inverse and round trip of n0, n1 in {256, 512} with k = 32 run
                                as one fused kernel per transform: each slice is spread over
                                one thread-block cluster (n0 n1 / 16384 CTAs, one per SM), its
@@ -97,10 +97,12 @@ typedef enum {
                                columns are transformed without the slice leaving the chip
                                (16 bytes of HBM traffic per point and transform).  Same
                                arithmetic per element as the per-axis tensor-core passes.
-                               0: the statistics pass and the two per-axis passes.  When the
-                               device cannot hold the cluster the passes run instead.  The
-                               fused round trip (mxfft_roundtrip_fused) always runs the
-                               passes. */
+                               0: the statistics pass and the two per-axis passes, which
+                               are faster on GB300 (all SMs busy, loads overlapped with
+                               compute; the fused kernel keeps one CTA per SM and at 512x512
+                               only 7 sixteen-CTA clusters fit at once).  When the device
+                               cannot hold the cluster the passes run instead.  The fused
+                               round trip (mxfft_roundtrip_fused) always runs the passes. */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;
@@ -287,6 +289,7 @@ typedef struct mxfft_engine_s *mxfft_engine_t;
 /* Engine flags. */
 #define MXFFT_ENGINE_GRAPHS 1  /* capture each batch signature into a CUDA graph, replay it */
 #define MXFFT_ENGINE_TC16 2    /* tensor-core radix-16 passes where a plan supports them */
+#define MXFFT_ENGINE_FUSED2D 4 /* with MXFFT_ENGINE_TC16: MXFFT_OPT_FUSED2D on the engine's plans */
 
 /*
  * mxfft_engine_create -- executor bound to the current device, with its own

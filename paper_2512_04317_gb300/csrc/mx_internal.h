@@ -120,14 +120,14 @@ struct Tc2dArgs {
     const SliceRef* ref;              // as in PassArgs
     SliceStats* st;
     int batch, n0, n1;
-    const uint8_t* bmat;              // B operand: 64 x 32 element codes (outputs, then re/im swapped)
+    const uint8_t* bmat;              // B operand: 32 x 32 element codes (core-matrix layout)
     const float4* twA1;               // rows: [j2 < M1][k1 < 16] (w.re, w.re, -w.im, w.im) x 2^s
     const float4* twC1;               // rows: [j22 < r1][k21 < 16]
     const float4* twA0;               // columns
     const float4* twC0;
     int epilogue;                     // EPI_UNSCALE, EPI_RT_FINAL (k of this transform) or EPI_RAW
     int lg_total;
-    uint32_t idesc;                   // tcgen05 instruction descriptor (M 128, N 64)
+    uint32_t idesc;                   // tcgen05 instruction descriptor (M 128, N 32)
     int* err;                         // set when a bounded wait gives up
     int stall;                        // test hook: issue no matrix product
     KParams kp;

@@ -34,7 +34,6 @@ struct mxfft_plan_s {
     uint8_t* d_bmat[2];        // [dir] tensor-core DFT matrix codes (core-matrix layout)
     float2* d_twA[2][2];       // [axis][dir] radix-16 stage twiddles
     float2* d_twC[2][2];       // [axis][dir] twiddles before the radix-2 stage (n = 512)
-    uint8_t* d_bmat64[2];      // [dir] the same matrix with N = 64 (outputs, then re/im swapped)
     float4* d_tw4A[2][2];      // [axis][dir] radix-16 stage twiddles as (re, re, -im, im)
     float4* d_tw4C[2][2];      // [axis][dir] twiddles before the radix-2 stage
     int fused2d;               // MXFFT_OPT_FUSED2D: fused 2D transform where it applies

@@ -24,11 +24,16 @@
 // rewritten with packed FP32 pairs: the block scale, the 8-bit encode, FP32
 // accumulation of 32 exact products in tensor memory, the scales applied to
 // the result, twiddles multiplied in FP32 with separately rounded products.
-// The B operand has N = 64 columns: the 32 outputs (re, im interleaved) and
-// the same 32 with re and im swapped, so a twiddle multiply is three packed
-// operations (w.re (re, im) + (-w.im, w.im) (im, re)), then the exact power-
-// of-two scale; in the normal range that gives the bits of the pass kernel's
-// scale-then-multiply order.
+// A twiddle multiply is packed: the products w.re (re, im) and (-w.im, w.im)
+// (im, re) of the unscaled accumulator pair, each times the exact power-of-
+// two scale, then one add; in the normal range that gives the bits of the
+// pass kernel's scale-then-multiply order.  The scale is applied to each
+// product before the add on purpose: the code generator may merge a multiply
+// into the add that follows it (a fused multiply-add rounds once), and only
+// a product by a power of two is exact, so that merge cannot change a bit.
+// (The (im, re) pair is taken from the same accumulator registers: a second
+// set of B columns with re and im swapped would recompute each dot product,
+// and the tensor core need not round the two computations alike.)
 //
 // Waits: the MMA completion and the slab copies are bounded (100 ms each by
 // the global timer); after a time-out the CTA records the error, issues no
@@ -50,7 +55,7 @@ using namespace tcg;
 constexpr int kThreads = 256;
 constexpr int kTilePts = 4096;        // points per tile = 256 vectors x 16
 constexpr int kSlabPts = 16384;       // points per CTA
-constexpr uint32_t kTmemCols = 128;   // two 128 x 64 FP32 accumulators
+constexpr uint32_t kTmemCols = 64;    // two 128 x 32 FP32 accumulators
 constexpr int kTwRow = 17;            // float4 slots per twiddle row (16 + 1 pad)
 
 // One axis of length n = 2^LOGN in {256, 512}.
@@ -83,8 +88,8 @@ struct Geo {
     static constexpr int STG_SLOTS = n0 * A0::T + (A0::T < 16 ? A0::T * (n0 / 16) : 0);
     // dynamic shared memory (bytes)
     static constexpr int OFF_A = 0;                                   // A operand, 2 x 4 KB
-    static constexpr int OFF_B = 8192;                                // B operand, 64 x 32 B
-    static constexpr int OFF_TWA1 = OFF_B + 2048;
+    static constexpr int OFF_B = 8192;                                // B operand, 32 x 32 B
+    static constexpr int OFF_TWA1 = OFF_B + 1024;
     static constexpr int OFF_TWC1 = OFF_TWA1 + A1::M * kTwRow * 16;
     static constexpr int OFF_TWA0 = OFF_TWC1 + A1::r * kTwRow * 16;
     static constexpr int OFF_TWC0 = OFF_TWA0 + A0::M * kTwRow * 16;
@@ -110,6 +115,32 @@ __device__ __forceinline__ int slot_row(int t, int e) {
 template <class A>
 __device__ __forceinline__ int slot_col(int t, int e) {
     return e * A::T + (A::T < 16 ? A::T * (e >> 4) : 0) + t;
+}
+
+// Packed FP32 pairs with an explicit rounding mode: each component is one
+// correctly rounded operation.  (A multiply feeding an add may still be
+// merged into one fused multiply-add by the code generator: the products
+// below are arranged so that such a merge changes no result.)
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 a, b, d; mov.b64 a, {%2, %3}; mov.b64 b, {%4, %5};"
+        " mul.rn.f32x2 d, a, b; mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 a, b, d; mov.b64 a, {%2, %3}; mov.b64 b, {%4, %5};"
+        " add.rn.f32x2 d, a, b; mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 a, b, d; mov.b64 a, {%2, %3}; mov.b64 b, {%4, %5};"
+        " sub.rn.f32x2 d, a, b; mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
 
 // max(|a|, |b|, |c|), NaN if any input is NaN.
@@ -149,14 +180,14 @@ struct Mma {
 // One radix-16 round on 256 vectors (thread i: vector i, operand half i / 128,
 // row i % 128): MX-encode x (shared scale 2^sv from the largest component,
 // elements rounded by cvt.rn.satfinite), one thread issues both products
-// against the N = 64 DFT operand, every thread reads its row back.  d gets
-// the 32 outputs (re, im interleaved), dsw (when SW) the same with re and im
-// swapped, both unscaled; returns the exact scale 2^(sv - emax) (NaN for a
-// block holding Inf/NaN).  A CTA barrier inside orders every thread's reads
-// of its round inputs before any thread's writes of the results.
-template <int FMT, bool SW>
-__device__ __forceinline__ float round_mma(const float2 (&x)[16], float (&d)[32], float (&dsw)[32],
-                                           Mma& mm, uint32_t idesc, int emax, bool issue) {
+// against the DFT operand, every thread reads its row back.  d gets the 32
+// outputs (re, im interleaved), unscaled; returns the exact scale 2^(sv -
+// emax) (NaN for a block holding Inf/NaN).  A CTA barrier inside orders every
+// thread's reads of its round inputs before any thread's writes of the
+// results.
+template <int FMT>
+__device__ __forceinline__ float round_mma(const float2 (&x)[16], float (&d)[32], Mma& mm,
+                                           uint32_t idesc, int emax, bool issue) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const float A = vec_max_abs(x);
     const bool bad = !(A <= 3.402823466e38f);
@@ -166,8 +197,8 @@ __device__ __forceinline__ float round_mma(const float2 (&x)[16], float (&d)[32]
     uint32_t w32[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-        const float2 a = __fmul2_rn(x[2 * j], inv2);
-        const float2 b = __fmul2_rn(x[2 * j + 1], inv2);
+        const float2 a = mul2_rn(x[2 * j], inv2);
+        const float2 b = mul2_rn(x[2 * j + 1], inv2);
         w32[j] = (uint32_t)enc2<FMT>(a.x, a.y) | ((uint32_t)enc2<FMT>(b.x, b.y) << 16);
     }
     // row rr of half h: K bytes 0..15 in core matrix (rr / 8, 0), 16..31 in (rr / 8, 1)
@@ -189,49 +220,43 @@ __device__ __forceinline__ float round_mma(const float2 (&x)[16], float (&d)[32]
                      :: "r"(mm.tbase), "l"(a0), "l"(bd), "r"(idesc), "r"(0));
         asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
                      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
-                     :: "r"(mm.tbase + 64u), "l"(a1), "l"(bd), "r"(idesc), "r"(0));
+                     :: "r"(mm.tbase + 32u), "l"(a1), "l"(bd), "r"(idesc), "r"(0));
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(mm.mbar));
     }
     bool done = false;
-    if (go) {
-        // tcgen05.ld below is warp-collective: the warp reads only if every
-        // lane saw the products complete
-        done = __all_sync(0xffffffffu, wait_phase(mm.mbar, mm.phase));
-        mm.phase ^= 1u;
-        mm.pending = !done;
-    } else if (mm.ok && !issue) {
-        // test hook: nothing was issued, so the bounded wait runs out
-        done = __all_sync(0xffffffffu, wait_phase(mm.mbar, mm.phase));
+    if (mm.ok) {
+        // warp 0 waits, the others sleep on the CTA barrier; with the test
+        // hook nothing was issued, so the bounded wait runs out
+        done = wait_phase_cta(mm.mbar, mm.phase);
+        if (go) {
+            mm.phase ^= 1u;
+            mm.pending = !done;
+        }
     }
     if (!done) mm.ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (done) {
         // warp w reads lanes 32 (w % 4) .. of accumulator w / 4
-        const uint32_t ta = mm.tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 64);
-        tmem_ld32(ta, d);
-        if (SW) tmem_ld32(ta + 32u, dsw);
+        tmem_ld32(mm.tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 32), d);
     } else {
 #pragma unroll
-        for (int c = 0; c < 32; c++) {
-            d[c] = 0.f;
-            if (SW) dsw[c] = 0.f;
-        }
+        for (int c = 0; c < 32; c++) d[c] = 0.f;
     }
     // D is exact-scaled by the vector's scale and the matrix rows' scale 2^-emax
     return bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
 }
 
-// Output k of a round times twiddle w = (w.re, w.re, -w.im, w.im), then the
-// exact scale: ((w.re re - w.im im), (w.re im + w.im re)) sc.
-__device__ __forceinline__ float2 tw_out(const float (&d)[32], const float (&dsw)[32], int k,
-                                         float4 w, float2 sc2) {
-    const float2 p1 = __fmul2_rn(make_float2(d[2 * k], d[2 * k + 1]), make_float2(w.x, w.y));
-    const float2 p2 = __fmul2_rn(make_float2(dsw[2 * k], dsw[2 * k + 1]), make_float2(w.z, w.w));
-    return __fmul2_rn(__fadd2_rn(p1, p2), sc2);
+// Output k of a round times twiddle w = (w.re, w.re, -w.im, w.im), with the
+// exact scale: (w.re re - w.im im, w.re im + w.im re) sc, each product
+// rounded, scaled exactly, then added (see above).
+__device__ __forceinline__ float2 tw_out(const float (&d)[32], int k, float4 w, float2 sc2) {
+    const float2 p1 = mul2_rn(mul2_rn(make_float2(d[2 * k], d[2 * k + 1]), make_float2(w.x, w.y)), sc2);
+    const float2 p2 = mul2_rn(mul2_rn(make_float2(d[2 * k + 1], d[2 * k]), make_float2(w.z, w.w)), sc2);
+    return add2_rn(p1, p2);
 }
 __device__ __forceinline__ float2 plain_out(const float (&d)[32], int k, float2 sc2) {
-    return __fmul2_rn(make_float2(d[2 * k], d[2 * k + 1]), sc2);
+    return mul2_rn(make_float2(d[2 * k], d[2 * k + 1]), sc2);
 }
 
 // Slice buffers.
@@ -308,7 +333,7 @@ tc2d_kernel(const Tc2dArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     // operand B and the twiddle tables
-    if (tid < 128)
+    if (tid < 64)
         reinterpret_cast<uint4*>(smem + G::OFF_B)[tid] = __ldg(reinterpret_cast<const uint4*>(a.bmat) + tid);
     {
         float4* t = reinterpret_cast<float4*>(smem + G::OFF_TWA1);
@@ -336,7 +361,6 @@ tc2d_kernel(const Tc2dArgs a) {
     uint32_t ld_phase = 0;
     bool ld_ok = true, ld_pending = false;
     const bool issue = !a.stall;
-    float dummy[32];
 
     // every CTA of a cluster walks the same slices: cluster cl takes cl, cl + ncl, ...
     if (clus < a.batch) {
@@ -355,8 +379,7 @@ tc2d_kernel(const Tc2dArgs a) {
         for (int i = tid; i < G::REC_WORDS; i += kThreads) rec[i] = 0u;
         // ---- 1. the slab ---------------------------------------------------
         if (ld_ok) {
-            const bool got = __all_sync(0xffffffffu, wait_phase(ldb, ld_phase));
-            if (__syncthreads_or(!got)) {
+            if (!wait_phase_cta(ldb, ld_phase)) {
                 ld_ok = false;           // the copies stay pending on phase ld_phase
             } else {
                 ld_pending = false;
@@ -430,21 +453,21 @@ tc2d_kernel(const Tc2dArgs a) {
             {   // round A: vector (t, j2), elements x[M j1 + j2]
                 const int t = tid >> A1::LGM, j2 = tid & (A1::M - 1);
                 float2 x[16];
-                float D[32], Dsw[32];
+                float D[32];
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = __fmul2_rn(d[slot_row<A1>(t, A1::M * j + j2)], pre2);
-                const float sc = round_mma<FMT, true>(x, D, Dsw, mm, a.idesc, emax, issue);
+                for (int j = 0; j < 16; j++) x[j] = mul2_rn(d[slot_row<A1>(t, A1::M * j + j2)], pre2);
+                const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                 const float2 sc2 = make_float2(sc, sc);
                 const float4* tw = twA1 + j2 * kTwRow;
 #pragma unroll
-                for (int kk = 0; kk < 16; kk++) d[slot_row<A1>(t, A1::M * kk + j2)] = tw_out(D, Dsw, kk, tw[kk], sc2);
+                for (int kk = 0; kk < 16; kk++) d[slot_row<A1>(t, A1::M * kk + j2)] = tw_out(D, kk, tw[kk], sc2);
                 __syncthreads();
             }
             {   // round C1: vector (t, k1, j22), elements Y[M k1 + r j21 + j22]
                 const int t = tid >> A1::LGM, rem = tid & (A1::M - 1);
                 const int k1 = rem >> A1::LGR, j22 = rem & (A1::r - 1);
                 float2 x[16];
-                float D[32], Dsw[32];
+                float D[32];
                 if (A1::r == 1) {
                     const float4* g = reinterpret_cast<const float4*>(d + slot_row<A1>(t, A1::M * k1));
 #pragma unroll
@@ -453,7 +476,7 @@ tc2d_kernel(const Tc2dArgs a) {
                         x[2 * c] = make_float2(q.x, q.y);
                         x[2 * c + 1] = make_float2(q.z, q.w);
                     }
-                    const float sc = round_mma<FMT, false>(x, D, dummy, mm, a.idesc, emax, issue);
+                    const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                     const float2 sc2 = make_float2(sc, sc);
                     // X[k1 + 16 k2], natural order (every input was read before the round's barrier)
 #pragma unroll
@@ -462,12 +485,12 @@ tc2d_kernel(const Tc2dArgs a) {
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; j++) x[j] = d[slot_row<A1>(t, A1::M * k1 + 2 * j + j22)];
-                    const float sc = round_mma<FMT, true>(x, D, Dsw, mm, a.idesc, emax, issue);
+                    const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                     const float2 sc2 = make_float2(sc, sc);
                     const float4* tw = twC1 + j22 * kTwRow;
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
-                        d[slot_row<A1>(t, A1::M * k1 + 2 * kk + j22)] = tw_out(D, Dsw, kk, tw[kk], sc2);
+                        d[slot_row<A1>(t, A1::M * k1 + 2 * kk + j22)] = tw_out(D, kk, tw[kk], sc2);
                     __syncthreads();
                     // C2: radix 2 over j22, X[k1 + 16 (k21 + 16 k22)]; every
                     // pair is read before any result is written
@@ -478,8 +501,8 @@ tc2d_kernel(const Tc2dArgs a) {
                         const int c1 = u & 15, k21 = (u >> 4) & 15, tt = u >> 8;
                         const float4 pq = *reinterpret_cast<const float4*>(d + slot_row<A1>(tt, A1::M * c1 + 2 * k21));
                         const float2 p = make_float2(pq.x, pq.y), q = make_float2(pq.z, pq.w);
-                        s0[i] = __fadd2_rn(p, q);
-                        s1[i] = __ffma2_rn(q, make_float2(-1.f, -1.f), p);   // p - q, one rounding
+                        s0[i] = add2_rn(p, q);
+                        s1[i] = sub2_rn(p, q);
                     }
                     __syncthreads();
 #pragma unroll
@@ -540,37 +563,37 @@ tc2d_kernel(const Tc2dArgs a) {
             {   // round A: vector (t, j2), elements x[M j1 + j2] of column t
                 const int t = tid & (A0::T - 1), j2 = tid >> A0::LGT;
                 float2 x[16];
-                float D[32], Dsw[32];
+                float D[32];
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = stg[slot_col<A0>(t, A0::M * j + j2)];
-                const float sc = round_mma<FMT, true>(x, D, Dsw, mm, a.idesc, emax, issue);
+                const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                 const float2 sc2 = make_float2(sc, sc);
                 const float4* tw = twA0 + j2 * kTwRow;
 #pragma unroll
-                for (int kk = 0; kk < 16; kk++) stg[slot_col<A0>(t, A0::M * kk + j2)] = tw_out(D, Dsw, kk, tw[kk], sc2);
+                for (int kk = 0; kk < 16; kk++) stg[slot_col<A0>(t, A0::M * kk + j2)] = tw_out(D, kk, tw[kk], sc2);
                 __syncthreads();
             }
             {   // round C1 (and C2 for n0 = 512), results to HBM
                 const int t = tid & (A0::T - 1), rem = tid >> A0::LGT;
                 const int k1 = rem >> A0::LGR, j22 = rem & (A0::r - 1);
                 float2 x[16];
-                float D[32], Dsw[32];
+                float D[32];
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = stg[slot_col<A0>(t, A0::M * k1 + A0::r * j + j22)];
                 if (A0::r == 1) {
-                    const float sc = round_mma<FMT, false>(x, D, dummy, mm, a.idesc, emax, issue);
+                    const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                     const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
-                        out[(size_t)(k1 + 16 * kk) * A1::n + col0 + t] = __fmul2_rn(plain_out(D, kk, sc2), post2);
+                        out[(size_t)(k1 + 16 * kk) * A1::n + col0 + t] = mul2_rn(plain_out(D, kk, sc2), post2);
                     __syncthreads();
                 } else {
-                    const float sc = round_mma<FMT, true>(x, D, Dsw, mm, a.idesc, emax, issue);
+                    const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                     const float2 sc2 = make_float2(sc, sc);
                     const float4* tw = twC0 + j22 * kTwRow;
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
-                        stg[slot_col<A0>(t, A0::M * k1 + 2 * kk + j22)] = tw_out(D, Dsw, kk, tw[kk], sc2);
+                        stg[slot_col<A0>(t, A0::M * k1 + 2 * kk + j22)] = tw_out(D, kk, tw[kk], sc2);
                     __syncthreads();
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
@@ -578,8 +601,8 @@ tc2d_kernel(const Tc2dArgs a) {
                         const int tt = u & 7, k21 = 8 * ((u >> 3) & 1) + (u >> 8), c1 = (u >> 4) & 15;
                         const int e = A0::M * c1 + 2 * k21;
                         const float2 p = stg[slot_col<A0>(tt, e)], qv = stg[slot_col<A0>(tt, e + 1)];
-                        const float2 s0 = __fmul2_rn(__fadd2_rn(p, qv), post2);
-                        const float2 s1 = __fmul2_rn(__ffma2_rn(qv, make_float2(-1.f, -1.f), p), post2);
+                        const float2 s0 = mul2_rn(add2_rn(p, qv), post2);
+                        const float2 s1 = mul2_rn(sub2_rn(p, qv), post2);
                         const int e0 = c1 + 16 * k21;
                         out[(size_t)e0 * A1::n + col0 + tt] = s0;
                         out[(size_t)(e0 + 256) * A1::n + col0 + tt] = s1;

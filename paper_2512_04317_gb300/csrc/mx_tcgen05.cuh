@@ -61,6 +61,34 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t phase) {
     return done != 0;
 }
 
+// The same bounded wait with the hardware suspending the thread between
+// checks (try_wait with a suspend-time hint: the thread sleeps until the
+// phase completes or the hint elapses), for a waiter that should not take
+// issue slots from the other warps.
+__device__ __forceinline__ bool wait_phase_sleep(uint32_t mbar, uint32_t phase) {
+    uint32_t done = 0;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;"
+                     " selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(mbar), "r"(phase), "r"(1000000u));
+        if (done || globaltimer_ns() - t0 > kWaitNs) break;
+    }
+    return done != 0;
+}
+
+// A CTA-wide bounded wait: warp 0 waits on the mbarrier phase, the other
+// warps on the CTA barrier (which takes no issue slots); every thread gets
+// whether the phase completed.  Every thread of the CTA must call it.  After
+// it, shared-memory data that completed the phase (bulk copies) are visible
+// to every thread; before reading tensor memory a thread still issues
+// tcgen05.fence::after_thread_sync.
+__device__ __forceinline__ bool wait_phase_cta(uint32_t mbar, uint32_t phase) {
+    bool ok = true;
+    if (threadIdx.x < 32) ok = __all_sync(0xffffffffu, wait_phase_sleep(mbar, phase));
+    return __syncthreads_or(!ok) == 0;
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&d)[32]) {
     uint32_t v[32];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "

@@ -155,7 +155,6 @@ void twiddle_block16(long m, long N, int sgn, const FmtHost& f, float2* out) {
 void free_plan_device(mxfft_plan_s* p) {
     for (int d = 0; d < 2; d++) {
         if (p->d_bmat[d]) cudaFree(p->d_bmat[d]);
-        if (p->d_bmat64[d]) cudaFree(p->d_bmat64[d]);
         for (int a = 0; a < 2; a++) {
             if (p->d_twA[a][d]) cudaFree(p->d_twA[a][d]);
             if (p->d_twC[a][d]) cudaFree(p->d_twC[a][d]);
@@ -250,17 +249,6 @@ int build_tc16_tables(mxfft_plan_s* p) {
         for (float sc : scales)
             if (sc != (float)std::ldexp(1.0, -f.emax)) return MXFFT_ERR_UNSUPPORTED;
         rc = upload(&p->d_bmat[d], codes);
-        // the fused 2D kernel's operand: N = 64 rows, the 32 output rows and
-        // then the same rows with each (re, im) pair swapped, so the product
-        // also yields (im, re) of every output (core-matrix layout as above)
-        std::vector<uint8_t> codes64(2048, 0);
-        for (int nrow = 0; nrow < 64; nrow++) {
-            const int srow = nrow < 32 ? nrow : ((nrow - 32) ^ 1);
-            for (int k = 0; k < 32; k++)
-                codes64[(nrow >> 3) * 256 + (k >> 4) * 128 + (nrow & 7) * 16 + (k & 15)] =
-                    codes[(srow >> 3) * 256 + (k >> 4) * 128 + (srow & 7) * 16 + (k & 15)];
-        }
-        if (rc == MXFFT_OK) rc = upload(&p->d_bmat64[d], codes64);
         for (int axis = 0; axis < 2 && rc == MXFFT_OK; axis++) {
             const int n = axis == 0 ? p->n0 : p->n1;
             const int r = n / 256, M = 16 * r;
@@ -460,7 +448,7 @@ Tc2dArgs tc2d_args(const mxfft_plan_s* p, int dir, const float2* in, float2* out
     t.st = st;
     t.n0 = p->n0;
     t.n1 = p->n1;
-    t.bmat = p->d_bmat64[dir];
+    t.bmat = p->d_bmat[dir];
     t.twA1 = p->d_tw4A[1][dir];
     t.twC1 = p->d_tw4C[1][dir];
     t.twA0 = p->d_tw4A[0][dir];
@@ -468,7 +456,7 @@ Tc2dArgs tc2d_args(const mxfft_plan_s* p, int dir, const float2* in, float2* out
     t.epilogue = epilogue;
     t.lg_total = ilog2(p->n0) + ilog2(p->n1);
     const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
-    t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+    t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
     t.err = p->d_err;
     t.stall = p->test_stall;
     t.kp = kparams(p);
@@ -575,7 +563,7 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
     p->taumin_exp = format == MXFFT_E5M2 ? -12 : (format == MXFFT_FP16 ? -24 : -10);
     p->kmin = -126;
     p->kmax = 126;
-    p->fused2d = 1;
+    p->fused2d = 0;
     p->fp.emax = f.emax;
     p->fp.emin = f.emin;
     p->fp.mbits = f.mbits;

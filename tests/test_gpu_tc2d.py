@@ -121,7 +121,7 @@ def test_fused2d_in_place(cuda_device):
     x = phantom.mri_batch(512, 512, 2, 1, config_id=44, domain="image")
     want, _, _, _, _ = run(x, "e5m2", "roundtrip", True)
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    with mxfft.Plan(512, 512, "e5m2", 32, path="tc16") as p:
+    with mxfft.Plan(512, 512, "e5m2", 32, path="tc16", fused2d=True) as p:
         p.roundtrip(xt, out=xt)
         torch.cuda.synchronize()
     np.testing.assert_array_equal(bits(xt.cpu().numpy()), bits(want))
@@ -140,7 +140,7 @@ def test_fused2d_engine_step_is_two_launches(cuda_device):
         wk = p.forward(xk).cpu().numpy()
         wi = p.roundtrip(xi).cpu().numpy()
     for graphs in (False, True):
-        with mxfft.Engine(graphs=graphs, tc16=True) as eng:
+        with mxfft.Engine(graphs=graphs, tc16=True, fused2d=True) as eng:
             yk, yi = torch.empty_like(xk), torch.empty_like(xi)
             for _ in range(2):
                 eng.run([("forward", xk, yk, "e4m3", 32), ("roundtrip", xi, yi, "e4m3", 32)])
@@ -160,9 +160,9 @@ def test_fused2d_bounded_wait_times_out(cuda_device):
 
     from paper_2512_04317_gb300 import mxfft
     x = torch.from_numpy(phantom.mri_batch(512, 512, 2, 1, config_id=46)).cuda()
-    with mxfft.Plan(512, 512, "e4m3", 32, path="tc16") as ref:
+    with mxfft.Plan(512, 512, "e4m3", 32, path="tc16", fused2d=True) as ref:
         want = ref.forward(x).cpu().numpy()
-    with mxfft.Plan(512, 512, "e4m3", 32, path="tc16") as p:
+    with mxfft.Plan(512, 512, "e4m3", 32, path="tc16", fused2d=True) as p:
         mxfft.mxfft_set_option(p.handle, mxfft.OPT_TEST_STALL, 1)
         p.forward(x)
         torch.cuda.synchronize()

@@ -66,8 +66,10 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--path", choices=["radix2", "tc16"], default="radix2",
-                    help="radix2: bit-exact radix-2 MX path; tc16: radix-16 tcgen05 variant")
+    ap.add_argument("--path", choices=["radix2", "tc16"], default="tc16",
+                    help="tc16: radix-16 tcgen05 variant (within the stated NRMSE; the default "
+                         "where the workload's shape allows it); radix2: the bit-exact radix-2 "
+                         "MX path (always timed beside the headline)")
     ap.add_argument("--api", choices=["engine", "plan"], default="engine",
                     help="engine: one batch-executor run per step, replayed as a CUDA graph; "
                          "plan: mxfft_forward + mxfft_roundtrip calls")
@@ -349,7 +351,7 @@ def _pct(lat_ms):
 
 
 def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
-                fractions=SERVING_FRACTIONS, rates=None, rss=True):
+                fractions=SERVING_FRACTIONS, rates=None, rss=True, tc16=False):
     """Continuous-batching server under the serving mix: saturated rate, then
     Poisson arrivals at fractions of it, p50 / p99 latency (submit to result in
     host memory); the plain FP32 per-slice GPU path (torch.fft, one call per
@@ -372,7 +374,7 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
 
     def run_mx(rate):
         with mxfft.Server(slots=slots, max_batch_slices=batch_slices,
-                          max_batch_bytes=batch_mb << 20) as srv:
+                          max_batch_bytes=batch_mb << 20, tc16=tc16) as srv:
             # plans of every (size, format) resident before the clock starts
             def submit(tag, sz, c, fmt, op, slot):
                 if rss:
@@ -440,7 +442,9 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
            "result": "one root-sum-of-squares image per request (Eq. (1))" if rss
                      else "the complex coil images",
            "server": f"{slots} slots, batches of at most {batch_slices} slices and "
-                     f"{batch_mb} MiB, memory budget 80% of free"}
+                     f"{batch_mb} MiB, memory budget 80% of free",
+           "path": "tensor-core plans where a request's shape allows them (256-1024), radix-2 "
+                   "otherwise" if tc16 else "radix-2"}
     # no garbage-collector pauses in the submitting loop while it keeps time
     gc.collect()
     gc_was_enabled = gc.isenabled()
@@ -622,6 +626,10 @@ def main():
             dist.barrier()
 
     n0, n1 = w["n0"], w["n1"]
+    # the tensor-core variant where the shape, format and k allow it, else radix-2
+    path = args.path
+    if path == "tc16" and not mxfft.tc16_supported(n0, n1, w["fmt"], w["k"]):
+        path = "radix2"
     ksp_np, img_np = make_inputs(w, rank)
     batch = ksp_np.shape[0]
     pts = batch * n0 * n1
@@ -630,14 +638,14 @@ def main():
     yk = torch.empty_like(xk)
     yi = torch.empty_like(xi)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"], path=args.path)
+    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"], path=path)
     stream = torch.cuda.current_stream(dev)
     engine = None
     if args.api == "engine":
         # one run per step: a statistics launch over both batches, the forward
         # passes of both as one launch per axis, then the round trip's
         # statistics and inverse passes; captured once, replayed as a graph
-        engine = mxfft.Engine(graphs=True, tc16=args.path == "tc16")
+        engine = mxfft.Engine(graphs=True, tc16=path == "tc16")
         work = [("forward", xk, yk, w["fmt"], w["k"]), ("roundtrip", xi, yi, w["fmt"], w["k"])]
 
         def step():
@@ -652,6 +660,8 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    if engine is not None:
+        launches_per_step = engine.launches_per_run()   # kernels of the replayed graph
 
     # ---- device-timed region: K steps, L2 flushed between them ----------------
     clocks = ClockSampler(local, enabled=not args.no_clocks)
@@ -680,29 +690,34 @@ def main():
                  "launches_per_step": 6,
                  "step": "forward of the k-space batch + fused round trip of the image batch"}
 
-    # ---- the tensor-core radix-16 variant (Sec. 4.2 note; approximate, within
-    # the stated NRMSE) on the same workload and step, timed the same way ---
-    tc_leg = None
-    if args.path == "radix2" and engine is not None and mxfft.tc16_supported(n0, n1, w["fmt"], w["k"]):
-        eng_tc = mxfft.Engine(graphs=True, tc16=True)
-        ytk, yti = torch.empty_like(xk), torch.empty_like(xi)
-        work_tc = [("forward", xk, ytk, w["fmt"], w["k"]), ("roundtrip", xi, yti, w["fmt"], w["k"])]
+    # ---- the other path on the same workload and step, timed the same way:
+    # beside the tensor-core headline the bit-exact radix-2 path of Alg. 2,
+    # beside a radix-2 headline the tensor-core variant --------------------------
+    other_leg = None
+    other = "radix2" if path == "tc16" else "tc16"
+    if engine is not None and (other == "radix2" or
+                               mxfft.tc16_supported(n0, n1, w["fmt"], w["k"])):
+        eng_o = mxfft.Engine(graphs=True, tc16=other == "tc16")
+        yok, yoi = torch.empty_like(xk), torch.empty_like(xi)
+        work_o = [("forward", xk, yok, w["fmt"], w["k"]), ("roundtrip", xi, yoi, w["fmt"], w["k"])]
         for _ in range(args.warmup):
-            eng_tc.run(work_tc)
-        tt_ms = timed_steps(torch, lambda: eng_tc.run(work_tc), args.steps, flush, stream, world,
+            eng_o.run(work_o)
+        to_ms = timed_steps(torch, lambda: eng_o.run(work_o), args.steps, flush, stream, world,
                             dist, dev, barrier)
-        tt_step = tt_ms / args.steps
-        with mxfft.Plan(n0, n1, w["fmt"], w["k"], path="tc16") as ptc:
-            tc_acc = accuracy(ptc, xk, xi, torch)
-        tc_leg = {"value": job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, tt_ms),
-                  "unit": "Mpts/s", "ms_per_step": tt_step,
-                  "hbm_roofline_frac_per_transform":
-                      pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (tt_step * 1e-3) / 1e9
-                      / load_peaks()[0],
-                  "accuracy_vs_fp64": tc_acc,
-                  "launches_per_step": eng_tc.launches_per_run(),
-                  "step": "the same engine run (forward + round trip) on tensor-core plans"}
-        eng_tc.close()
+        to_step = to_ms / args.steps
+        with mxfft.Plan(n0, n1, w["fmt"], w["k"], path=other) as po:
+            o_acc = accuracy(po, xk, xi, torch)
+        other_leg = {"path": other,
+                     "value": job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, to_ms),
+                     "unit": "Mpts/s", "ms_per_step": to_step,
+                     "hbm_roofline_frac_per_transform":
+                         pts * TRANSFORMS_PER_STEP * ALG_BYTES_PER_PT / (to_step * 1e-3) / 1e9
+                         / load_peaks()[0],
+                     "accuracy_vs_fp64": o_acc,
+                     "launches_per_step": eng_o.launches_per_run(),
+                     "bit_exact_with_oracle": other == "radix2",
+                     "step": "the same engine run (forward + round trip) on this path's plans"}
+        eng_o.close()
 
     # ---- per-kernel device time (event pairs around each launch on the launch
     # stream; the same kernels through the plan calls, since launches inside a
@@ -771,7 +786,7 @@ def main():
             b = {"xk": torch.empty_like(xk), "xi": torch.empty_like(xi), "yk": torch.empty_like(yk),
                  "yi": torch.empty_like(yi), "ok": torch.empty_like(hk).pin_memory(),
                  "oi": torch.empty_like(hi).pin_memory()}
-            lanes.append((torch.cuda.Stream(dev), mxfft.Engine(graphs=True, tc16=args.path == "tc16"), b))
+            lanes.append((torch.cuda.Stream(dev), mxfft.Engine(graphs=True, tc16=path == "tc16"), b))
 
         def e2e_step(i):
             st_, eng_j, b = lanes[i % len(lanes)]
@@ -858,7 +873,7 @@ def main():
         cpu = cpu_baseline(w, ksp_np, img_np)
     serving = None
     if world == 1 and not args.no_serving:
-        serving = serving_leg(args.serving_requests, torch)
+        serving = serving_leg(args.serving_requests, torch, tc16=path == "tc16")
     rss_acc = rss_image_metrics(torch) if rank == 0 else None
 
     if rank == 0:
@@ -867,7 +882,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype_label(w["fmt"]), "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "path": args.path,
+            "config": {"workload": args.workload, "desc": w["desc"], "path": path,
                        "api": args.api, "tuning": tuning,
                        "n0": n0, "n1": n1,
                        "batch_per_gpu": batch, "format": w["fmt"], "k": w["k"],
@@ -875,7 +890,7 @@ def main():
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
-            "tensor_core_variant": tc_leg,
+            "other_path": other_leg,
             "roofline_alu": roofline_alu,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Mpts/s", "h2d_bytes_per_step": bytes_io,

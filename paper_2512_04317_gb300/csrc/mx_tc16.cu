@@ -137,14 +137,7 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
                                             uint32_t idesc, int emax, bool issue, int g,
                                             int lgt, uint32_t* sAm) {
     const int tid = threadIdx.x, warp = tid >> 5;
-    float m[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) m[j] = fmax_nan(fabsf(x[j].x), fabsf(x[j].y));
-#pragma unroll
-    for (int w = 1; w < 16; w <<= 1)
-#pragma unroll
-        for (int j = 0; j + w < 16; j += 2 * w) m[j] = fmax_nan(m[j], m[j + w]);
-    float A = m[0];
+    float A = vec_max_abs(x);
     if (g > 1) {
         // one shared scale for the g vectors of the block (members may sit in
         // other warps: exchanged through shared memory; the previous round's
@@ -156,12 +149,12 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
     const bool bad = !(A <= 3.402823466e38f);
     const int sv = mx_scale_exp(__float_as_uint(A), emax);
     const float inv = exp2i(-sv);
+    const float2 inv2 = make_float2(inv, inv);
     uint32_t w32[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-        const uint32_t lo = enc2<FMT>(__fmul_rn(x[2 * j].x, inv), __fmul_rn(x[2 * j].y, inv));
-        const uint32_t hi = enc2<FMT>(__fmul_rn(x[2 * j + 1].x, inv), __fmul_rn(x[2 * j + 1].y, inv));
-        w32[j] = lo | (hi << 16);
+        const float2 a = mul2_rn(x[2 * j], inv2), b = mul2_rn(x[2 * j + 1], inv2);
+        w32[j] = (uint32_t)enc2<FMT>(a.x, a.y) | ((uint32_t)enc2<FMT>(b.x, b.y) << 16);
     }
     // row rr of half h: K bytes 0..15 in core matrix (rr / 8, 0), 16..31 in (rr / 8, 1)
     const int h = tid >> 7, rr = tid & 127;
@@ -185,9 +178,9 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(mm.mbar));
     }
-    // tcgen05.ld below is warp-collective: the warp reads only if every lane saw
-    // the products complete
-    const bool done = __all_sync(0xffffffffu, wait_phase(mm.mbar, mm.phase));
+    // warp 0 waits (sleeping between checks), the other warps on the CTA
+    // barrier, so that they take no issue slots from the SM's other CTA
+    const bool done = wait_phase_cta(mm.mbar, mm.phase);
     mm.phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     float d[32];
@@ -202,11 +195,9 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
     // D is exact-scaled by the vector's scale and the matrix rows' scale, which
     // is 2^-emax for every row (each row holds an entry of magnitude 1)
     const float sc = bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
+    const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        y[k].x = __fmul_rn(d[2 * k], sc);
-        y[k].y = __fmul_rn(d[2 * k + 1], sc);
-    }
+    for (int k = 0; k < 16; k++) y[k] = mul2_rn(make_float2(d[2 * k], d[2 * k + 1]), sc2);
 }
 
 __device__ __forceinline__ float2 cmul(float2 w, float2 y) {
@@ -370,7 +361,7 @@ tc16_pass_kernel(const Args a) {
             if (a.prologue == PRO_PRESCALE) {
                 const float pre = exp2i(kslice);
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = scale2(d[slot<LOGN, DIM>(t, M * j + j2)], pre);
+                for (int j = 0; j < 16; j++) x[j] = mul2_rn(d[slot<LOGN, DIM>(t, M * j + j2)], make_float2(pre, pre));
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];

@@ -120,6 +120,60 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 
+// ---- packed FP32 arithmetic and block maxima ----------------------------------
+
+// Packed FP32 pairs with an explicit rounding mode: each component is one
+// correctly rounded operation.  (A multiply feeding an add may still be
+// merged into one fused multiply-add by the code generator: the products
+// below are arranged so that such a merge changes no result.)
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 a, b, d; mov.b64 a, {%2, %3}; mov.b64 b, {%4, %5};"
+        " mul.rn.f32x2 d, a, b; mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 a, b, d; mov.b64 a, {%2, %3}; mov.b64 b, {%4, %5};"
+        " add.rn.f32x2 d, a, b; mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 a, b, d; mov.b64 a, {%2, %3}; mov.b64 b, {%4, %5};"
+        " sub.rn.f32x2 d, a, b; mov.b64 {%0, %1}, d;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// max(|a|, |b|, |c|), NaN if any input is NaN.
+__device__ __forceinline__ float max3_abs_nan(float a, float b, float c) {
+    float d;
+    asm("max.NaN.abs.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Largest |component| of 16 complex values (NaN if any is NaN): a tree of
+// three-input maxima, 17 instructions for 32 values.
+__device__ __forceinline__ float vec_max_abs(const float2 (&x)[16]) {
+    float a[32];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        a[2 * j] = x[j].x;
+        a[2 * j + 1] = x[j].y;
+    }
+#pragma unroll
+    for (int w = 1; w < 32; w *= 3)
+#pragma unroll
+        for (int t = 0; t < 32; t += 3 * w) {
+            if (t + 2 * w < 32) a[t] = max3_abs_nan(a[t], a[t + w], a[t + 2 * w]);
+            else if (t + w < 32) a[t] = max3_abs_nan(a[t], a[t + w], a[t + w]);
+        }
+    return a[0];
+}
+
 // ---- thread-block clusters ---------------------------------------------------
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {

@@ -51,3 +51,48 @@ def test_large_2048_fp6_sampled(fmt, k, op, cuda_device):
     assert st == 0 and flags == 0
     want, kw, _ = run_oracle(x[:1], fmt, k, op)
     assert_bitwise(got[:1], want, f"2048^2 {fmt} k={k} {op}")
+
+
+def test_bench_default_step_full_size_sampled(cuda_device):
+    # the headline configuration as bench.py times it: 16 coils x 32 slices
+    # 512x512 (the same seeded inputs), forward + round trip through one
+    # graph-replayed executor run on tensor-core plans, and the radix-2 leg
+    # on the same batches; sampled slices against the emulation of the
+    # tensor-core variant (element-wise, bounded by each row's peak) and
+    # against the oracle (bit for bit)
+    import sys
+
+    import bench
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import tc16_ref
+    w = bench.WORKLOADS["multicoil_16x32_512x512"]
+    ksp, img = bench.make_inputs(w, 0)
+    assert ksp.shape == (512, 512, 512)
+    xk, xi = torch.from_numpy(ksp).cuda(), torch.from_numpy(img).cuda()
+    samples = [0, 301, 511]
+    for tc in (True, False):
+        yk, yi = torch.empty_like(xk), torch.empty_like(xi)
+        with mxfft.Engine(graphs=True, tc16=tc) as eng:
+            for _ in range(2):
+                eng.run([("forward", xk, yk, "e4m3", 32), ("roundtrip", xi, yi, "e4m3", 32)])
+            torch.cuda.synchronize()
+            flags, _ = eng.status()
+            assert flags == 0
+            assert eng.launches_per_run() == 6
+        for s in samples:
+            if tc:
+                for got, x, op in ((yk, ksp, "forward"), (yi, img, "roundtrip")):
+                    g = got[s].cpu().numpy()
+                    want = tc16_ref.mxfft2d(x[s:s + 1], "e4m3", op)[0]
+                    err = np.abs(g.astype(np.complex128) - want)
+                    peak = np.abs(want.astype(np.complex128)).max(axis=-1, keepdims=True)
+                    rel = err / peak
+                    assert rel.max() < 0.1 and np.mean(rel > 1e-5) < 1e-3, (s, op, rel.max())
+            else:
+                wk, _, _ = oracle.mxfft2d(ksp[s:s + 1], "e4m3", 32, op="forward")
+                wi, _, _ = oracle.mxfft2d(img[s:s + 1], "e4m3", 32, op="roundtrip")
+                assert_bitwise(yk[s:s + 1].cpu().numpy(), wk, f"C3 forward slice {s}")
+                assert_bitwise(yi[s:s + 1].cpu().numpy(), wi, f"C3 round trip slice {s}")

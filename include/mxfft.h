@@ -412,6 +412,49 @@ int mxfft_server_destroy(mxfft_server_t s);
  */
 int mxfft_rss(const void *z, void *out, int images, int coils, int n0, int n1, void *stream);
 
+/*
+ * mxfft_quantize -- the element rounding Q of Alg. 2 (Sec. 2.2: the
+ * quantisation inside EncodeBlockMX / EncodeFromMantBlock, applied to values
+ * already divided by their block's power-of-two scale): round to the nearest
+ * value of the element format, ties to the even code, saturating at the
+ * largest normal, signed zeros and subnormals kept; run on the device with
+ * the transforms' own code, for comparison with an independent
+ * implementation.
+ *   in, out  device arrays of n float32 values (out may equal in).
+ *   format   MXFFT_E4M3 .. MXFFT_E2M1.
+ *   path     0: the register-resident pass's conversions (the hardware
+ *            cvt.rn.satfinite.<fmt>x2.f32 and back to exact f16 values;
+ *            n even, 8-byte aligned arrays); 1: the generic pass's FP32
+ *            add-and-subtract rounding (4-byte aligned arrays).
+ * Asynchronous on stream; MXFFT_ERR_INVALID for bad arguments.  Finite
+ * inputs only (the transforms handle Inf / NaN by the block scale).
+ */
+int mxfft_quantize(const void *in, void *out, long long n, int format, int path, void *stream);
+
+/*
+ * mxfft_test_fail_alloc -- test hook of the plan allocator (no counterpart in
+ * the paper).  after >= 0: the device allocation of a plan (tables, statistics
+ * records; mxfft_plan, mxfft_set_option, the statistics growth of a
+ * transform call) that comes after `after` further successful ones fails as
+ * if the device were out of memory, once; the call that made it returns
+ * MXFFT_ERR_NOMEM and frees what it had allocated.  after = -1 disarms it.
+ * Process-wide, not thread-safe; for tests of the failure paths only.
+ */
+int mxfft_test_fail_alloc(int after);
+
+/*
+ * mxfft_debug_bounds -- bounds-check build (no counterpart in the paper).  A
+ * library built with MXFFT_DEBUG_BOUNDS defined checks the computed global
+ * and shared-memory indices of its transform kernels (register-resident,
+ * generic, tensor-core and fused 2D passes); an index outside its buffer is
+ * counted and replaced by a valid one instead of being used.  This call
+ * synchronises the device and returns *enabled = 1 and the number of
+ * violations since the previous call (then clears the count); in the normal
+ * build *enabled = 0 and *violations = 0.  MXFFT_ERR_INVALID for NULL
+ * arguments.
+ */
+int mxfft_debug_bounds(int *enabled, unsigned long long *violations);
+
 /* mxfft_status_string -- static description of a status code. */
 const char *mxfft_status_string(int status);
 

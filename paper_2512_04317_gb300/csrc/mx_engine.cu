@@ -22,6 +22,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mx_plan.h"
 
 using namespace mxfft;
@@ -506,6 +508,10 @@ int mxfft_engine_create(float tau, float target, int flags, mxfft_engine_t* out)
 }
 
 int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, void* stream) {
+    struct Range {   // NVTX range on the host timeline for the whole call
+        Range() { nvtxRangePushA("mxfft_engine_run"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     if (!e || n_items < 0 || (n_items > 0 && !items)) return MXFFT_ERR_INVALID;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != e->device) return MXFFT_ERR_CUDA;

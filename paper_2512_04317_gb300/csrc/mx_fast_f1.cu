@@ -5,4 +5,5 @@ namespace mxfft {
 namespace fast {
 template cudaError_t launch_fast_fmt<1>(const FastArgs&, int, int, cudaStream_t);
 }  // namespace fast
+MX_BOUNDS_COUNTER(fast_f1)
 }  // namespace mxfft

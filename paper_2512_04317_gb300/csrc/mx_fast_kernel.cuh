@@ -2,6 +2,7 @@
 // and its launcher, instantiated once per element format in mx_fast_f*.cu.
 #pragma once
 
+#include "mx_debug.cuh"
 #include "mx_fast_impl.cuh"
 
 namespace mxfft {
@@ -34,7 +35,9 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
     stage_a<FMT, LOGM, 8>(r, twa, fp, (unsigned)TG);
     stage_a<FMT, LOGM, 16>(r, twa, fp, (unsigned)TG);
 #pragma unroll
-    for (int t = 0; t < 32; t++) Gs[(32 * sigma + t) * S + tau] = r[t];
+    const int gs_slots = (1 << L) * S;   // the group's shared rows
+#pragma unroll
+    for (int t = 0; t < 32; t++) Gs[MX_BND((32 * sigma + t) * S + tau, gs_slots)] = r[t];
     __syncthreads();
 
     // ---- phase B: stage pairs (h, 2h), an odd last stage alone ---------------
@@ -64,7 +67,7 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-            for (int i = 0; i < 8; i++) R[q][i] = Gs[(e0[q] + i) * S + tau];
+            for (int i = 0; i < 8; i++) R[q][i] = Gs[MX_BND((e0[q] + i) * S + tau, gs_slots)];
         if (LOGM == 6 && h == 32) {
             // m = 64 > h: a block of stage 32 is both groups of the slot's runs,
             // a block of stage 64 the whole group (always a stage pair: n >= 128)
@@ -83,7 +86,7 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-            for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
+            for (int i = 0; i < 8; i++) Gs[MX_BND((e0[q] + i) * S + tau, gs_slots)] = R[q][i];
         __syncthreads();
     }
 }
@@ -115,6 +118,10 @@ fast_pass_kernel(const FastArgs fa) {
     float2* __restrict__ out = a.ref ? a.ref[slice].out : a.out + sbase;
     const SliceStats* stp = a.ref ? a.ref[slice].st : a.st + slice;
     const FmtParams fp = a.fp;
+    const size_t slice_pts = (size_t)a.n0 * a.n1;      // bounds of the debug build
+    const size_t sm_slots = (size_t)fa.NG * n * S;
+    (void)slice_pts;
+    (void)sm_slots;
 
     const float pre = a.prologue == PRO_PRESCALE ? exp2i(stp->k) : 1.0f;
     const int s = n >> 5;                        // chunk stride of the bit-reversed gather
@@ -125,7 +132,7 @@ fast_pass_kernel(const FastArgs fa) {
     if (DIM == 0) {
 #pragma unroll
         for (int j = 0; j < 32; j++) {
-            float2 v = in[(size_t)(rc + j * s) * a.n1 + tr];
+            float2 v = in[MX_BND((size_t)(rc + j * s) * a.n1 + tr, slice_pts)];
             if (a.prologue == PRO_PRESCALE) { v.x = __fmul_rn(v.x, pre); v.y = __fmul_rn(v.y, pre); }
             r[rev5(j)] = v;
         }
@@ -144,20 +151,21 @@ fast_pass_kernel(const FastArgs fa) {
             const int p = rest & ((n >> 1) - 1);
             const int g = rest >> (L - 1);
             v[b] = __ldg(reinterpret_cast<const float4*>(
-                in + (size_t)(t0 + g * TG + tc) * a.n1 + 2 * p));
+                in + MX_BND((size_t)(t0 + g * TG + tc) * a.n1 + 2 * p, slice_pts - 1)));
         }
 #pragma unroll
         for (int b = 0; b < 16; b++) {
             const int rest = r0 + b * dr;
             const int p = rest & ((n >> 1) - 1);
             const int g = rest >> (L - 1);
-            float2* Gg = sm + (size_t)g * n * S;
-            Gg[(2 * p) * S + tc] = make_float2(__fmul_rn(v[b].x, pre), __fmul_rn(v[b].y, pre));
-            Gg[(2 * p + 1) * S + tc] = make_float2(__fmul_rn(v[b].z, pre), __fmul_rn(v[b].w, pre));
+            sm[MX_BND((size_t)g * n * S + (2 * p) * S + tc, sm_slots)] =
+                make_float2(__fmul_rn(v[b].x, pre), __fmul_rn(v[b].y, pre));
+            sm[MX_BND((size_t)g * n * S + (2 * p + 1) * S + tc, sm_slots)] =
+                make_float2(__fmul_rn(v[b].z, pre), __fmul_rn(v[b].w, pre));
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 32; j++) r[rev5(j)] = Gs[(rc + j * s) * S + tau];
+        for (int j = 0; j < 32; j++) r[rev5(j)] = Gs[MX_BND((rc + j * s) * S + tau, n * S)];
         __syncthreads();
     }
 
@@ -171,10 +179,10 @@ fast_pass_kernel(const FastArgs fa) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
-            for (int i = 0; i < 8; i++) Gs[(e0[q] + i) * S + tau] = R[q][i];
+            for (int i = 0; i < 8; i++) Gs[MX_BND((e0[q] + i) * S + tau, n * S)] = R[q][i];
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 32; j++) r[rev5(j)] = Gs[(rc + j * s) * S + tau];
+        for (int j = 0; j < 32; j++) r[rev5(j)] = Gs[MX_BND((rc + j * s) * S + tau, n * S)];
         __syncthreads();
         all_stages<FMT, LOGM>(r, R, e0, Gs, fa.twa2, fa.twh2, a.tws, L, S, TG, sigma, tau, s, fp);
     }
@@ -188,18 +196,18 @@ fast_pass_kernel(const FastArgs fa) {
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i++)
-                out[(size_t)(e0[q] + i) * a.n1 + tr] = epi_value(R[q][i], a.epilogue, post);
+                out[MX_BND((size_t)(e0[q] + i) * a.n1 + tr, slice_pts)] = epi_value(R[q][i], a.epilogue, post);
     } else {
         // each run R[q] is 8 consecutive elements of this thread's own row:
         // four 16-byte stores per run, straight from registers
-        float2* __restrict__ orow = out + (size_t)tr * a.n1;
 #pragma unroll
         for (int q = 0; q < 4; q++)
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {
                 const float2 v0 = epi_value(R[q][i], a.epilogue, post);
                 const float2 v1 = epi_value(R[q][i + 1], a.epilogue, post);
-                *reinterpret_cast<float4*>(orow + e0[q] + i) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                *reinterpret_cast<float4*>(out + MX_BND((size_t)tr * a.n1 + e0[q] + i, slice_pts - 1)) =
+                    make_float4(v0.x, v0.y, v1.x, v1.y);
             }
     }
 }

@@ -24,6 +24,22 @@ struct FmtParams {
     uint32_t qadd_bits;  // ((23 - mbits) << 23) | 0x400000: turns 2^E into 1.5 * 2^(E+23-mbits)
 };
 
+#ifdef MXFFT_DEBUG_BOUNDS
+// Readers of the bounds-check counters of the instrumented translation units
+// (each returns its count and clears it; ~0 on a CUDA error).
+unsigned long long bounds_take_fast_f0();
+unsigned long long bounds_take_fast_f1();
+unsigned long long bounds_take_fast_f2();
+unsigned long long bounds_take_fast_f3();
+unsigned long long bounds_take_fast_f4();
+unsigned long long bounds_take_pass();
+unsigned long long bounds_take_tc16();
+unsigned long long bounds_take_tc2d();
+#endif
+
+// Element-format constants of an mxfft_format code (false for an unknown code).
+bool fmt_params(int code, FmtParams* fp);
+
 // Per-slice statistics of Alg. 1 (one record per slice and transform).
 // Zeroed before every transform that accumulates into it.
 struct SliceStats {

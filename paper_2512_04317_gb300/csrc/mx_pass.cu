@@ -9,6 +9,7 @@
 // and the block maxima of Alg. 2 are reduced with xor shuffles.
 #include <cuda_fp16.h>
 
+#include "mx_debug.cuh"
 #include "mx_device.cuh"
 #include "mxfft.h"
 
@@ -52,8 +53,8 @@ __device__ __forceinline__ void load_bf(Bf& q, const float2* A, int b, int nb, i
         int j = b & (h - 1);
         q.iu = 2 * b - j;          // 2h*g + j with g = b / h
         q.iv = q.iu + h;
-        q.u = A[q.iu];
-        q.v = A[q.iv];
+        q.u = A[MX_BND(q.iu, 2 * nb)];
+        q.v = A[MX_BND(q.iv, 2 * nb)];
         float2 w = __ldg(tw + (h - 1) + j);
         q.xr = w.x;
         q.xi = w.y;
@@ -117,14 +118,14 @@ __device__ __forceinline__ void mx_butterfly_pair(float2* A, int b0, int nb, int
     if (q0.ok) {
         const float wr = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p0r, f0), fp), d0), nan0);
         const float wi = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p0i, f0), fp), d0), nan0);
-        A[q0.iu] = make_float2(__fadd_rn(q0.u.x, wr), __fadd_rn(q0.u.y, wi));
-        A[q0.iv] = make_float2(__fsub_rn(q0.u.x, wr), __fsub_rn(q0.u.y, wi));
+        A[MX_BND(q0.iu, 2 * nb)] = make_float2(__fadd_rn(q0.u.x, wr), __fadd_rn(q0.u.y, wi));
+        A[MX_BND(q0.iv, 2 * nb)] = make_float2(__fsub_rn(q0.u.x, wr), __fsub_rn(q0.u.y, wi));
     }
     if (q1.ok) {
         const float wr = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p1r, f1), fp), d1), nan1);
         const float wi = __fmul_rn(__fmul_rn(q_elem(__fmul_rn(p1i, f1), fp), d1), nan1);
-        A[q1.iu] = make_float2(__fadd_rn(q1.u.x, wr), __fadd_rn(q1.u.y, wi));
-        A[q1.iv] = make_float2(__fsub_rn(q1.u.x, wr), __fsub_rn(q1.u.y, wi));
+        A[MX_BND(q1.iu, 2 * nb)] = make_float2(__fadd_rn(q1.u.x, wr), __fadd_rn(q1.u.y, wi));
+        A[MX_BND(q1.iv, 2 * nb)] = make_float2(__fsub_rn(q1.u.x, wr), __fsub_rn(q1.u.y, wi));
     }
 }
 
@@ -148,10 +149,10 @@ __device__ __forceinline__ void fp16_butterfly_pair(float2* A, int b0, int nb, i
         if (b >= nb) continue;
         const int j = b & (h - 1);
         const int iu = 2 * b - j, iv = iu + h;
-        const float2 u = A[iu];
-        const float2 p = fp16_product(__ldg(tw + (h - 1) + j), A[iv]);
-        A[iu] = make_float2(__fadd_rn(u.x, p.x), __fadd_rn(u.y, p.y));
-        A[iv] = make_float2(__fsub_rn(u.x, p.x), __fsub_rn(u.y, p.y));
+        const float2 u = A[MX_BND(iu, 2 * nb)];
+        const float2 p = fp16_product(__ldg(tw + (h - 1) + j), A[MX_BND(iv, 2 * nb)]);
+        A[MX_BND(iu, 2 * nb)] = make_float2(__fadd_rn(u.x, p.x), __fadd_rn(u.y, p.y));
+        A[MX_BND(iv, 2 * nb)] = make_float2(__fsub_rn(u.x, p.x), __fsub_rn(u.y, p.y));
     }
 }
 
@@ -167,6 +168,8 @@ pass_kernel(PassArgs a) {
     const int slice = blockIdx.x / per_slice;
     const int t0 = (blockIdx.x - slice * per_slice) * tpc;
     const size_t sbase = (size_t)slice * a.n0 * a.n1;
+    const size_t slice_pts = (size_t)a.n0 * a.n1;     // bounds of the debug build
+    (void)slice_pts;
     const float2* __restrict__ in = a.ref ? a.ref[slice].in : a.in + sbase;
     float2* __restrict__ out = a.ref ? a.ref[slice].out : a.out + sbase;
     const SliceStats* stp = a.ref ? a.ref[slice].st : a.st + slice;
@@ -187,13 +190,13 @@ pass_kernel(PassArgs a) {
             t = idx - i * tpc;
             g = (size_t)i * a.n1 + t0 + t;
         }
-        float2 v = in[g];
+        float2 v = in[MX_BND(g, slice_pts)];
         if (a.prologue == PRO_PRESCALE) {
             v.x = __fmul_rn(v.x, pre);
             v.y = __fmul_rn(v.y, pre);
             if (fp16) { v.x = to_fp16(v.x); v.y = to_fp16(v.y); }   // input rounding
         }
-        sm[t * n + (int)(__brev((unsigned)i) >> (32 - logn))] = v;
+        sm[MX_BND(t * n + (int)(__brev((unsigned)i) >> (32 - logn)), total)] = v;
     }
     __syncthreads();
 
@@ -227,7 +230,7 @@ pass_kernel(PassArgs a) {
             t = idx - i * tpc;
             g = (size_t)i * a.n1 + t0 + t;
         }
-        float2 v = sm[t * n + i];
+        float2 v = sm[MX_BND(t * n + i, total)];
         if (a.epilogue != EPI_RAW) {
             // FP16 control: output rounding in the prescaled domain, then the
             // exact unscale
@@ -235,7 +238,7 @@ pass_kernel(PassArgs a) {
             v.x = __fmul_rn(v.x, post);
             v.y = __fmul_rn(v.y, post);
         }
-        out[g] = v;
+        out[MX_BND(g, slice_pts)] = v;
     }
 }
 
@@ -255,5 +258,7 @@ cudaError_t launch_pass(const PassArgs& a, int batch, cudaStream_t s) {
     note_launch();
     return cudaGetLastError();
 }
+
+MX_BOUNDS_COUNTER(pass)
 
 }  // namespace mxfft

@@ -40,6 +40,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "mx_debug.cuh"
 #include "mx_device.cuh"
 #include "mx_tcgen05.cuh"
 
@@ -95,12 +96,12 @@ struct Geo {
 template <int LOGN>
 __device__ __forceinline__ int slot_row(int t, int e) {
     using G = Geo<LOGN>;
-    return t * G::TS + e + G::PADR * (e >> G::LGM);
+    return (int)MX_BND(t * G::TS + e + G::PADR * (e >> G::LGM), G::BUF_SLOTS);
 }
 template <int LOGN>
 __device__ __forceinline__ int slot_col(int t, int e) {
     using G = Geo<LOGN>;
-    return e * G::T + (G::T < 16 ? G::T * (e >> 4) : 0) + t;
+    return (int)MX_BND(e * G::T + (G::T < 16 ? G::T * (e >> 4) : 0) + t, G::BUF_SLOTS);
 }
 template <int LOGN, int DIM>
 __device__ __forceinline__ int slot(int t, int e) {
@@ -246,14 +247,16 @@ __device__ __forceinline__ void load_tile(const Args& a, const float2* in, int t
         const int q = threadIdx.x + i * kThreads;      // 16-byte chunk of the tile
         const float2* src;
         int t, e;
+        const size_t slice_pts = (size_t)a.n0 * a.n1;
+        (void)slice_pts;
         if (DIM == 1) {
             t = q >> (LOGN - 1);
             e = 2 * (q & ((G::n >> 1) - 1));
-            src = in + (size_t)(t0 + t) * a.n1 + e;
+            src = in + MX_BND((size_t)(t0 + t) * a.n1 + e, slice_pts - 1);
         } else {
             e = q >> (G::LGT - 1);
             t = 2 * (q & ((G::T >> 1) - 1));
-            src = in + (size_t)e * a.n1 + t0 + t;
+            src = in + MX_BND((size_t)e * a.n1 + t0 + t, slice_pts - 1);
         }
         cp_async16(buf + 8u * (uint32_t)slot<LOGN, DIM>(t, e), src);
     }
@@ -307,6 +310,8 @@ tc16_pass_kernel(const Args a) {
         ? ((int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0)
         : share + ((int)blockIdx.x < extra ? 1 : 0);
     const bool with_k = a.prologue == PRO_PRESCALE || a.epilogue != EPI_RAW;
+    const size_t slice_pts = (size_t)a.n0 * a.n1;      // bounds of the debug build
+    (void)slice_pts;
     SliceCache ld, cs;   // slices of the tile being loaded and of the current tile
     if (my_tiles > 0) {
         const int sl = tile_begin / per_slice;
@@ -412,8 +417,8 @@ tc16_pass_kernel(const Args a) {
                 for (int k = 0; k < 16; k++) {
                     const float2 val = scale_out ? scale2(y[k], post) : y[k];
                     const int e = k1 + 16 * k;
-                    if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + e] = val;
-                    else out[(size_t)e * a.n1 + t0 + t] = val;
+                    if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + e, slice_pts)] = val;
+                    else out[MX_BND((size_t)e * a.n1 + t0 + t, slice_pts)] = val;
                 }
             } else {
                 const float4* tw = reinterpret_cast<const float4*>(sTwC + j22 * kTwRow);
@@ -477,8 +482,8 @@ tc16_pass_kernel(const Args a) {
                 for (int k22 = 0; k22 < 4; k22++) {
                     const float2 val = scale_out ? scale2(X[k22], post) : X[k22];
                     const int eo = k1 + 16 * k21 + 256 * k22;
-                    if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + eo] = val;
-                    else out[(size_t)eo * a.n1 + t0 + t] = val;
+                    if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + eo, slice_pts)] = val;
+                    else out[MX_BND((size_t)eo * a.n1 + t0 + t, slice_pts)] = val;
                 }
             }
             // the buffer is refilled by the next iteration's prefetch
@@ -554,8 +559,8 @@ tc16_pass_kernel(const Args a) {
                                      : make_float2(__fsub_rn(E[k4].x, P[k4].x), __fsub_rn(E[k4].y, P[k4].y));
                     if (scale_out) X = scale2(X, post);
                     const int eo = k1 + 16 * k21 + 256 * k;
-                    if (DIM == 1) out[(size_t)(t0 + t) * a.n1 + eo] = X;
-                    else out[(size_t)eo * a.n1 + t0 + t] = X;
+                    if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + eo, slice_pts)] = X;
+                    else out[MX_BND((size_t)eo * a.n1 + t0 + t, slice_pts)] = X;
                 }
             }
             // the buffer is refilled by the next iteration's prefetch
@@ -584,11 +589,11 @@ tc16_pass_kernel(const Args a) {
                 if (scale_out) { s0 = scale2(s0, post); s1 = scale2(s1, post); }
                 const int e0 = k1 + 16 * k21, e1 = e0 + 256;
                 if (DIM == 1) {
-                    out[(size_t)(t0 + t) * a.n1 + e0] = s0;
-                    out[(size_t)(t0 + t) * a.n1 + e1] = s1;
+                    out[MX_BND((size_t)(t0 + t) * a.n1 + e0, slice_pts)] = s0;
+                    out[MX_BND((size_t)(t0 + t) * a.n1 + e1, slice_pts)] = s1;
                 } else {
-                    out[(size_t)e0 * a.n1 + t0 + t] = s0;
-                    out[(size_t)e1 * a.n1 + t0 + t] = s1;
+                    out[MX_BND((size_t)e0 * a.n1 + t0 + t, slice_pts)] = s0;
+                    out[MX_BND((size_t)e1 * a.n1 + t0 + t, slice_pts)] = s1;
                 }
             }
             // the buffer is refilled by the next iteration's prefetch
@@ -665,5 +670,7 @@ cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t
     if (fmt == 1) return tc16::launch_fmt<1>(b, s);
     return cudaErrorNotSupported;
 }
+
+MX_BOUNDS_COUNTER(tc16)
 
 }  // namespace mxfft

@@ -44,6 +44,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "mx_debug.cuh"
 #include "mx_device.cuh"
 #include "mx_tcgen05.cuh"
 
@@ -238,7 +239,7 @@ __device__ __forceinline__ void load_slab(const float2* in, uint32_t rank, uint3
     const float2* src = in + (size_t)rank * G::R * A1::n;
     for (int q = threadIdx.x; q < RUNS; q += kThreads) {
         const int row = q / (A1::n / A1::M), run = q % (A1::n / A1::M);
-        bulk_g2s(slab_u32 + 8u * (uint32_t)slot_row<A1>(row, run * A1::M),
+        bulk_g2s(slab_u32 + 8u * (uint32_t)MX_BND(slot_row<A1>(row, run * A1::M), G::SLAB_SLOTS - A1::M + 1),
                  src + (size_t)row * A1::n + run * A1::M, (uint32_t)(A1::M * 8), mbar);
     }
 }
@@ -266,6 +267,11 @@ tc2d_kernel(const Tc2dArgs a) {
     const float4* twC1 = reinterpret_cast<const float4*>(smem + G::OFF_TWC1);
     const float4* twA0 = reinterpret_cast<const float4*>(smem + G::OFF_TWA0);
     const float4* twC0 = reinterpret_cast<const float4*>(smem + G::OFF_TWC0);
+    // slab and staging slots, checked in the debug build
+    auto srow = [](int t, int e) { return (int)MX_BND(slot_row<A1>(t, e), G::SLAB_SLOTS); };
+    auto scol = [](int t, int e) { return (int)MX_BND(slot_col<A0>(t, e), G::STG_SLOTS); };
+    const size_t slice_pts = (size_t)G::n0 * G::n1;
+    (void)slice_pts;
     const uint32_t slab_u32 = smem_u32(slab);
     const uint32_t rec_u32 = smem_u32(rec);
     const uint32_t ldb = smem_u32(&mbar_ld);
@@ -344,7 +350,7 @@ tc2d_kernel(const Tc2dArgs a) {
             for (int i = 0; i < kSlabPts / 2 / kThreads; i++) {
                 const int c = tid + i * kThreads;              // pair of points
                 const int row = c / (A1::n / 2), col = 2 * (c % (A1::n / 2));
-                const float4 v = *reinterpret_cast<const float4*>(slab + slot_row<A1>(row, col));
+                const float4 v = *reinterpret_cast<const float4*>(slab + srow(row, col));
                 acc.add<true>(v.x, v.y, rec + 4);
                 acc.add<true>(v.z, v.w, rec + 4);
             }
@@ -403,12 +409,12 @@ tc2d_kernel(const Tc2dArgs a) {
                 float2 x[16];
                 float D[32];
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = mul2_rn(d[slot_row<A1>(t, A1::M * j + j2)], pre2);
+                for (int j = 0; j < 16; j++) x[j] = mul2_rn(d[srow(t, A1::M * j + j2)], pre2);
                 const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                 const float2 sc2 = make_float2(sc, sc);
                 const float4* tw = twA1 + j2 * kTwRow;
 #pragma unroll
-                for (int kk = 0; kk < 16; kk++) d[slot_row<A1>(t, A1::M * kk + j2)] = tw_out(D, kk, tw[kk], sc2);
+                for (int kk = 0; kk < 16; kk++) d[srow(t, A1::M * kk + j2)] = tw_out(D, kk, tw[kk], sc2);
                 __syncthreads();
             }
             {   // round C1: vector (t, k1, j22), elements Y[M k1 + r j21 + j22]
@@ -417,7 +423,7 @@ tc2d_kernel(const Tc2dArgs a) {
                 float2 x[16];
                 float D[32];
                 if (A1::r == 1) {
-                    const float4* g = reinterpret_cast<const float4*>(d + slot_row<A1>(t, A1::M * k1));
+                    const float4* g = reinterpret_cast<const float4*>(d + srow(t, A1::M * k1));
 #pragma unroll
                     for (int c = 0; c < 8; c++) {
                         const float4 q = g[c];
@@ -428,17 +434,17 @@ tc2d_kernel(const Tc2dArgs a) {
                     const float2 sc2 = make_float2(sc, sc);
                     // X[k1 + 16 k2], natural order (every input was read before the round's barrier)
 #pragma unroll
-                    for (int kk = 0; kk < 16; kk++) d[slot_row<A1>(t, k1 + 16 * kk)] = plain_out(D, kk, sc2);
+                    for (int kk = 0; kk < 16; kk++) d[srow(t, k1 + 16 * kk)] = plain_out(D, kk, sc2);
                     __syncthreads();
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; j++) x[j] = d[slot_row<A1>(t, A1::M * k1 + 2 * j + j22)];
+                    for (int j = 0; j < 16; j++) x[j] = d[srow(t, A1::M * k1 + 2 * j + j22)];
                     const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                     const float2 sc2 = make_float2(sc, sc);
                     const float4* tw = twC1 + j22 * kTwRow;
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
-                        d[slot_row<A1>(t, A1::M * k1 + 2 * kk + j22)] = tw_out(D, kk, tw[kk], sc2);
+                        d[srow(t, A1::M * k1 + 2 * kk + j22)] = tw_out(D, kk, tw[kk], sc2);
                     __syncthreads();
                     // C2: radix 2 over j22, X[k1 + 16 (k21 + 16 k22)]; every
                     // pair is read before any result is written
@@ -447,7 +453,7 @@ tc2d_kernel(const Tc2dArgs a) {
                     for (int i = 0; i < 8; i++) {
                         const int u = tid + i * kThreads;      // (t, k1, k21), T x 16 x 16
                         const int c1 = u & 15, k21 = (u >> 4) & 15, tt = u >> 8;
-                        const float4 pq = *reinterpret_cast<const float4*>(d + slot_row<A1>(tt, A1::M * c1 + 2 * k21));
+                        const float4 pq = *reinterpret_cast<const float4*>(d + srow(tt, A1::M * c1 + 2 * k21));
                         const float2 p = make_float2(pq.x, pq.y), q = make_float2(pq.z, pq.w);
                         s0[i] = add2_rn(p, q);
                         s1[i] = sub2_rn(p, q);
@@ -457,8 +463,8 @@ tc2d_kernel(const Tc2dArgs a) {
                     for (int i = 0; i < 8; i++) {
                         const int u = tid + i * kThreads;
                         const int c1 = u & 15, k21 = (u >> 4) & 15, tt = u >> 8;
-                        d[slot_row<A1>(tt, c1 + 16 * k21)] = s0[i];
-                        d[slot_row<A1>(tt, c1 + 16 * k21 + 256)] = s1[i];
+                        d[srow(tt, c1 + 16 * k21)] = s0[i];
+                        d[srow(tt, c1 + 16 * k21 + 256)] = s1[i];
                     }
                     __syncthreads();
                 }
@@ -483,7 +489,7 @@ tc2d_kernel(const Tc2dArgs a) {
                     const int g = tid + i * kThreads;
                     const int j = g / (G::R * CPR), rem = g % (G::R * CPR);
                     const int rho = rem / CPR, c2 = rem % CPR;
-                    const int src = slot_row<A1>(rho, col0 + 2 * c2);
+                    const int src = srow(rho, col0 + 2 * c2);
                     v[i] = ld_cluster_f4(mapa_shared(slab_u32 + 8u * (uint32_t)src, (uint32_t)j));
                 }
 #pragma unroll
@@ -491,7 +497,7 @@ tc2d_kernel(const Tc2dArgs a) {
                     const int g = tid + i * kThreads;
                     const int j = g / (G::R * CPR), rem = g % (G::R * CPR);
                     const int rho = rem / CPR, c2 = rem % CPR;
-                    *reinterpret_cast<float4*>(stg + slot_col<A0>(2 * c2, G::R * j + rho)) = v[i];
+                    *reinterpret_cast<float4*>(stg + scol(2 * c2, G::R * j + rho)) = v[i];
                 }
             }
             __syncthreads();
@@ -513,12 +519,12 @@ tc2d_kernel(const Tc2dArgs a) {
                 float2 x[16];
                 float D[32];
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = stg[slot_col<A0>(t, A0::M * j + j2)];
+                for (int j = 0; j < 16; j++) x[j] = stg[scol(t, A0::M * j + j2)];
                 const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                 const float2 sc2 = make_float2(sc, sc);
                 const float4* tw = twA0 + j2 * kTwRow;
 #pragma unroll
-                for (int kk = 0; kk < 16; kk++) stg[slot_col<A0>(t, A0::M * kk + j2)] = tw_out(D, kk, tw[kk], sc2);
+                for (int kk = 0; kk < 16; kk++) stg[scol(t, A0::M * kk + j2)] = tw_out(D, kk, tw[kk], sc2);
                 __syncthreads();
             }
             {   // round C1 (and C2 for n0 = 512), results to HBM
@@ -527,13 +533,13 @@ tc2d_kernel(const Tc2dArgs a) {
                 float2 x[16];
                 float D[32];
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = stg[slot_col<A0>(t, A0::M * k1 + A0::r * j + j22)];
+                for (int j = 0; j < 16; j++) x[j] = stg[scol(t, A0::M * k1 + A0::r * j + j22)];
                 if (A0::r == 1) {
                     const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
                     const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
-                        out[(size_t)(k1 + 16 * kk) * A1::n + col0 + t] = mul2_rn(plain_out(D, kk, sc2), post2);
+                        out[MX_BND((size_t)(k1 + 16 * kk) * A1::n + col0 + t, slice_pts)] = mul2_rn(plain_out(D, kk, sc2), post2);
                     __syncthreads();
                 } else {
                     const float sc = round_mma<FMT>(x, D, mm, a.idesc, emax, issue);
@@ -541,19 +547,19 @@ tc2d_kernel(const Tc2dArgs a) {
                     const float4* tw = twC0 + j22 * kTwRow;
 #pragma unroll
                     for (int kk = 0; kk < 16; kk++)
-                        stg[slot_col<A0>(t, A0::M * k1 + 2 * kk + j22)] = tw_out(D, kk, tw[kk], sc2);
+                        stg[scol(t, A0::M * k1 + 2 * kk + j22)] = tw_out(D, kk, tw[kk], sc2);
                     __syncthreads();
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
                         const int u = tid + i * kThreads;      // (t, k1, k21), T x 16 x 16
                         const int tt = u & 7, k21 = 8 * ((u >> 3) & 1) + (u >> 8), c1 = (u >> 4) & 15;
                         const int e = A0::M * c1 + 2 * k21;
-                        const float2 p = stg[slot_col<A0>(tt, e)], qv = stg[slot_col<A0>(tt, e + 1)];
+                        const float2 p = stg[scol(tt, e)], qv = stg[scol(tt, e + 1)];
                         const float2 s0 = mul2_rn(add2_rn(p, qv), post2);
                         const float2 s1 = mul2_rn(sub2_rn(p, qv), post2);
                         const int e0 = c1 + 16 * k21;
-                        out[(size_t)e0 * A1::n + col0 + tt] = s0;
-                        out[(size_t)(e0 + 256) * A1::n + col0 + tt] = s1;
+                        out[MX_BND((size_t)e0 * A1::n + col0 + tt, slice_pts)] = s0;
+                        out[MX_BND((size_t)(e0 + 256) * A1::n + col0 + tt, slice_pts)] = s1;
                     }
                     __syncthreads();
                 }
@@ -661,5 +667,7 @@ cudaError_t launch_tc2d(const Tc2dArgs& a, int fmt, cudaStream_t s) {
     if (!tc2d_supported(a.n0, a.n1, fmt, 32)) return cudaErrorNotSupported;
     return fmt == 0 ? tc2d::launch_fmt<0>(a, s) : tc2d::launch_fmt<1>(a, s);
 }
+
+MX_BOUNDS_COUNTER(tc2d)
 
 }  // namespace mxfft

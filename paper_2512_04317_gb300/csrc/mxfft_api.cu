@@ -10,11 +10,35 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mx_plan.h"
 
 using namespace mxfft;
 
 namespace {
+
+// NVTX range around one enqueued call (shown by profilers on the host timeline).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Device allocations of a plan (its tables and statistics records) go
+// through plan_malloc, so that a test can make the n-th one fail as if the
+// device were out of memory (mxfft_test_fail_alloc).
+std::atomic<int> g_fail_alloc_after{-1};
+
+cudaError_t plan_malloc(void** p, size_t bytes) {
+    const int c = g_fail_alloc_after.load();
+    if (c == 0) {
+        g_fail_alloc_after.store(-1);
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    if (c > 0) g_fail_alloc_after.store(c - 1);
+    return cudaMalloc(p, bytes);
+}
 
 struct FmtHost {
     int emax, emin, mbits;
@@ -184,7 +208,7 @@ int ensure_stats(mxfft_plan_s* p, int batch) {
         p->d_st = nullptr;
         p->st_cap = 0;
     }
-    cudaError_t e = cudaMalloc(&p->d_st, sizeof(SliceStats) * 2 * (size_t)cap);
+    cudaError_t e = plan_malloc((void**)&p->d_st, sizeof(SliceStats) * 2 * (size_t)cap);
     if (e != cudaSuccess) { p->d_st = nullptr; return cuda_status(e); }
     p->st_cap = cap;
     return MXFFT_OK;
@@ -227,7 +251,7 @@ void build_dft16_matrix(int sgn, int fmt, const FmtHost& f, std::vector<uint8_t>
 
 template <class T>
 int upload(T** dst, const std::vector<T>& v) {
-    int rc = cuda_status(cudaMalloc(dst, sizeof(T) * v.size()));
+    int rc = cuda_status(plan_malloc((void**)dst, sizeof(T) * v.size()));
     if (rc == MXFFT_OK)
         rc = cuda_status(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
     return rc;
@@ -266,7 +290,7 @@ int build_tc16_tables(mxfft_plan_s* p) {
         }
     }
     if (rc == MXFFT_OK && !p->d_err) {
-        rc = cuda_status(cudaMalloc(&p->d_err, sizeof(int)));
+        rc = cuda_status(plan_malloc((void**)&p->d_err, sizeof(int)));
         if (rc == MXFFT_OK) rc = cuda_status(cudaMemset(p->d_err, 0, sizeof(int)));
     }
     return rc;
@@ -300,6 +324,9 @@ void prof_clear(mxfft_plan_s* p) {
 
 // op: 0 forward, 1 inverse, 2 round trip, 3 fused round trip
 int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int op) {
+    static const char* const kNames[4] = {"mxfft_forward", "mxfft_inverse", "mxfft_roundtrip",
+                                          "mxfft_roundtrip_fused"};
+    NvtxRange range(kNames[op & 3]);
     if (!p || batch < 0) return MXFFT_ERR_INVALID;
     if (op == 3 && p->fmt == MXFFT_FP16) return MXFFT_ERR_UNSUPPORTED;
     if (batch == 0) return MXFFT_OK;
@@ -339,9 +366,12 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
         // the device cannot hold the kernel's cluster: the per-axis passes
         // (nothing was launched)
     }
-    ProfRec* r = prof_begin(p, 0, s);
-    e = launch_stats(x, batch, p->n0, p->n1, st_f, kparams(p), s);
-    prof_end(r, s);
+    {
+        NvtxRange sr("mxfft statistics");
+        ProfRec* r = prof_begin(p, 0, s);
+        e = launch_stats(x, batch, p->n0, p->n1, st_f, kparams(p), s);
+        prof_end(r, s);
+    }
     if (e != cudaSuccess) return cuda_status(e);
     PassArgs rows = pass_args(p, 1, dir0, x, y);
     rows.st = st_f;
@@ -366,9 +396,12 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
     }
     if (op == 2) {
         // the inverse's own prescale statistics, on the forward output y
-        ProfRec* rs = prof_begin(p, 0, s);
-        e = launch_stats(y, batch, p->n0, p->n1, st_i, kparams(p), s);
-        prof_end(rs, s);
+        {
+            NvtxRange sr("mxfft statistics");
+            ProfRec* rs = prof_begin(p, 0, s);
+            e = launch_stats(y, batch, p->n0, p->n1, st_i, kparams(p), s);
+            prof_end(rs, s);
+        }
         if (e != cudaSuccess) return cuda_status(e);
         PassArgs r2 = pass_args(p, 1, 1, y, y);
         r2.st = st_i;
@@ -392,6 +425,18 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
 namespace mxfft {
 
 std::atomic<long long> g_kernel_launches{0};
+
+bool fmt_params(int code, FmtParams* fp) {
+    FmtHost f;
+    if (!fmt_host(code, &f)) return false;
+    fp->emax = f.emax;
+    fp->emin = f.emin;
+    fp->mbits = f.mbits;
+    fp->maxnorm = (float)f.maxnorm;
+    fp->qmin_bits = (uint32_t)(f.emin + 127) << 23;
+    fp->qadd_bits = ((uint32_t)(23 - f.mbits) << 23) | 0x400000u;
+    return true;
+}
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return MXFFT_OK;
@@ -464,6 +509,7 @@ Tc2dArgs tc2d_args(const mxfft_plan_s* p, int dir, const float2* in, float2* out
 }
 
 cudaError_t timed_tc2d(mxfft_plan_s* p, const Tc2dArgs& a, int batch, cudaStream_t s) {
+    NvtxRange range("mxfft fused 2D transform");
     Tc2dArgs b = a;
     b.batch = batch;
     ProfRec* r = prof_begin(p, 4, s);
@@ -476,6 +522,7 @@ cudaError_t timed_tc2d(mxfft_plan_s* p, const Tc2dArgs& a, int batch, cudaStream
 // kernel where it applies (n in [64, 2048], m <= 16; m = 32, 64 for n >= 128),
 // else the generic shared-memory kernel.
 cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream_t s) {
+    NvtxRange range(a.dim == 1 ? "mxfft rows pass" : "mxfft columns pass");
     const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
     if (p->path == 1) {
         Tc16Args t;
@@ -564,12 +611,7 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
     p->kmin = -126;
     p->kmax = 126;
     p->fused2d = 0;
-    p->fp.emax = f.emax;
-    p->fp.emin = f.emin;
-    p->fp.mbits = f.mbits;
-    p->fp.maxnorm = (float)f.maxnorm;
-    p->fp.qmin_bits = (uint32_t)(f.emin + 127) << 23;
-    p->fp.qadd_bits = ((uint32_t)(23 - f.mbits) << 23) | 0x400000u;
+    fmt_params(format, &p->fp);
     p->recs = new (std::nothrow) std::vector<ProfRec>();
     if (!p->recs) { delete p; return MXFFT_ERR_NOMEM; }
     p->recs->reserve(1024);
@@ -585,7 +627,7 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
         build_twiddles(n, p->m[axis], f, fw, iv, sw, format == MXFFT_FP16);
         for (int d = 0; d < 2 && rc == MXFFT_OK; d++) {
             const std::vector<float2>& t = d == 0 ? fw : iv;
-            rc = cuda_status(cudaMalloc(&p->d_tw[axis][d], sizeof(float2) * t.size()));
+            rc = cuda_status(plan_malloc((void**)&p->d_tw[axis][d], sizeof(float2) * t.size()));
             if (rc == MXFFT_OK)
                 rc = cuda_status(cudaMemcpy(p->d_tw[axis][d], t.data(), sizeof(float2) * t.size(),
                                             cudaMemcpyHostToDevice));
@@ -605,12 +647,12 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
             // of 8 twiddles the register pass loads starts 32-byte aligned
             std::vector<uint32_t> h2s(h2.size() + 1, 0u);
             std::copy(h2.begin(), h2.end(), h2s.begin() + 1);
-            rc = cuda_status(cudaMalloc(&p->d_twh[axis][d], sizeof(uint32_t) * h2s.size()));
+            rc = cuda_status(plan_malloc((void**)&p->d_twh[axis][d], sizeof(uint32_t) * h2s.size()));
             if (rc == MXFFT_OK)
                 rc = cuda_status(cudaMemcpy(p->d_twh[axis][d], h2s.data(), sizeof(uint32_t) * h2s.size(),
                                             cudaMemcpyHostToDevice));
         }
-        if (rc == MXFFT_OK) rc = cuda_status(cudaMalloc(&p->d_tws[axis], sw.size()));
+        if (rc == MXFFT_OK) rc = cuda_status(plan_malloc((void**)&p->d_tws[axis], sw.size()));
         if (rc == MXFFT_OK)
             rc = cuda_status(cudaMemcpy(p->d_tws[axis], sw.data(), sw.size(), cudaMemcpyHostToDevice));
     }
@@ -760,6 +802,36 @@ int mxfft_profile_read(mxfft_plan_t p, double* total_ms, int* launches, int nkin
     }
     prof_clear(p);
     return rc;
+}
+
+int mxfft_debug_bounds(int* enabled, unsigned long long* violations) {
+    if (!enabled || !violations) return MXFFT_ERR_INVALID;
+#ifdef MXFFT_DEBUG_BOUNDS
+    using namespace mxfft;
+    if (cudaDeviceSynchronize() != cudaSuccess) return MXFFT_ERR_CUDA;
+    unsigned long long (*const take[])() = {bounds_take_fast_f0, bounds_take_fast_f1,
+                                            bounds_take_fast_f2, bounds_take_fast_f3,
+                                            bounds_take_fast_f4, bounds_take_pass,
+                                            bounds_take_tc16, bounds_take_tc2d};
+    unsigned long long total = 0;
+    for (auto f : take) {
+        const unsigned long long v = f();
+        if (v == ~0ull) return MXFFT_ERR_CUDA;
+        total += v;
+    }
+    *enabled = 1;
+    *violations = total;
+#else
+    *enabled = 0;
+    *violations = 0;
+#endif
+    return MXFFT_OK;
+}
+
+int mxfft_test_fail_alloc(int after) {
+    if (after < -1) return MXFFT_ERR_INVALID;
+    g_fail_alloc_after.store(after);
+    return MXFFT_OK;
 }
 
 const char* mxfft_status_string(int status) {

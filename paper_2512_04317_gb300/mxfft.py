@@ -35,7 +35,8 @@ EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
            "mxfft_engine_launches", "mxfft_engine_destroy", "mxfft_tune", "mxfft_tune_save", "mxfft_tune_load",
            "mxfft_tune_clear", "mxfft_server_create", "mxfft_server_submit",
            "mxfft_server_poll", "mxfft_server_wait", "mxfft_server_stats",
-           "mxfft_server_destroy", "mxfft_rss", "mxfft_status_string")
+           "mxfft_server_destroy", "mxfft_rss", "mxfft_quantize", "mxfft_test_fail_alloc",
+           "mxfft_debug_bounds", "mxfft_status_string")
 
 
 class Item(ctypes.Structure):
@@ -123,6 +124,9 @@ def load(path: str | None = None):
         lib.mxfft_engine_run.argtypes = [P, ctypes.POINTER(Item), I, P]
         lib.mxfft_engine_get_status.argtypes = [P, P, P, I]
         lib.mxfft_engine_launches.argtypes = [P, P]
+        lib.mxfft_quantize.argtypes = [P, P, ctypes.c_longlong, I, I, P]
+        lib.mxfft_test_fail_alloc.argtypes = [I]
+        lib.mxfft_debug_bounds.argtypes = [P, P]
         lib.mxfft_engine_destroy.argtypes = [P]
         lib.mxfft_tune.argtypes = [P, I, P, P]
         lib.mxfft_tune_save.argtypes = [ctypes.c_char_p]
@@ -281,6 +285,26 @@ def mxfft_engine_launches(engine) -> int:
 def mxfft_engine_destroy(engine) -> None:
     if engine:
         load().mxfft_engine_destroy(engine)
+
+
+def mxfft_debug_bounds():
+    """(enabled, violations since the last call) of the bounds-check build."""
+    en, v = ctypes.c_int(0), ctypes.c_ulonglong(0)
+    _check(load().mxfft_debug_bounds(ctypes.byref(en), ctypes.byref(v)), "mxfft_debug_bounds")
+    return bool(en.value), int(v.value)
+
+
+def mxfft_test_fail_alloc(after: int) -> None:
+    """Test hook: the plan allocation after `after` more successful ones fails
+    (MXFFT_ERR_NOMEM); -1 disarms it."""
+    _check(load().mxfft_test_fail_alloc(int(after)), "mxfft_test_fail_alloc")
+
+
+# ---- element quantiser (Alg. 2's rounding Q) --------------------------------------------
+
+def mxfft_quantize(in_ptr, out_ptr, n, fmt, path, stream=None) -> None:
+    _check(load().mxfft_quantize(in_ptr, out_ptr, int(n), _fmt(fmt), int(path), stream),
+           "mxfft_quantize")
 
 
 # ---- root-sum-of-squares coil combine (Eq. (1)) -------------------------------------

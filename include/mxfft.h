@@ -255,8 +255,13 @@ int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, 
  * Ragged batch executor.  Not a construct of the paper: it runs many
  * independent 2D transforms of the method (each exactly as mxfft_forward /
  * mxfft_inverse / mxfft_roundtrip would on its own) in one set of launches:
- * one statistics launch over every slice of every item (Alg. 1), one pass
- * launch per (plan, direction) group and axis, the groups as parallel
+ * one statistics launch over every slice of every item (Alg. 1), then for
+ * the radix-2 plans with k = 32 and n0, n1 <= 1024 one ragged launch per
+ * axis and stage over all of them (every CTA takes its slice, plan and
+ * transforms from a device table), so any mix of such plans takes at most 6
+ * launches (statistics, rows, columns, and for round trips statistics,
+ * inverse rows, inverse columns); other plans (tensor-core, other k, the
+ * generic pass) one launch per pass and (plan, direction) group, as parallel
  * branches.  Results are bit-identical to the per-plan calls.
  * ====================================================================== */
 typedef enum {
@@ -290,6 +295,8 @@ typedef struct mxfft_engine_s *mxfft_engine_t;
 #define MXFFT_ENGINE_GRAPHS 1  /* capture each batch signature into a CUDA graph, replay it */
 #define MXFFT_ENGINE_TC16 2    /* tensor-core radix-16 passes where a plan supports them */
 #define MXFFT_ENGINE_FUSED2D 4 /* with MXFFT_ENGINE_TC16: MXFFT_OPT_FUSED2D on the engine's plans */
+#define MXFFT_ENGINE_NO_RAGGED 8 /* one launch per pass and plan group instead of the ragged
+                                    launches (same results; for comparison) */
 
 /*
  * mxfft_engine_create -- executor bound to the current device, with its own

@@ -2,9 +2,14 @@
 // prescale, then the Alg. 2 radix-2 passes along rows and columns, Eq. (1)
 // round trips) enqueued as
 //   table upload -> statistics records cleared -> one statistics launch over
-//   every slice of every item -> per (plan, direction) group, as parallel
-//   branches: rows pass, columns pass -> [round trips: one statistics launch
-//   over the forward outputs -> per plan: inverse rows, inverse columns]
+//   every slice of every item -> one ragged rows launch and one ragged
+//   columns launch over every (plan, direction) group whose passes fit the
+//   ragged register-resident kernel (k = 32, n <= 1024) -> [round trips: one
+//   statistics launch over the forward outputs -> one ragged inverse rows and
+//   one inverse columns launch]
+// so any mix of such plans runs in at most 6 launches.  Groups of other plans
+// (tensor-core paths, other k, the generic pass) keep one launch per pass and
+// group, as parallel branches on fork streams beside the ragged launches.
 // Every pass kernel reads its slices' buffers and statistics records from a
 // table in device memory (SliceRef), so a group is one launch whatever the
 // addresses, and a captured graph stays valid when a later call passes other
@@ -44,6 +49,18 @@ struct PassLaunch {
     int whole = 0;        // 1: the fused 2D kernel (statistics, rows, columns)
 };
 
+// One ragged launch: the register-resident passes of several plans along
+// one axis (k = 32), every CTA 256 threads, its work from a table of
+// (group, slice, first transform) entries; the groups' arguments travel as a
+// kernel parameter.
+struct RaggedPhase {
+    int dim = 1;
+    std::vector<char> groups;         // ngroups records of fast_ragged_arg_size() bytes
+    int ngroups = 0;
+    int cta0 = 0, ncta = 0;           // entries [cta0, cta0 + ncta) of Layout::rctas
+    size_t smem = 0;                  // largest dynamic shared memory of its groups
+};
+
 // Host image of one run: the device tables and the launches that read them.
 struct Layout {
     std::vector<SliceRef> refs;
@@ -51,11 +68,14 @@ struct Layout {
     std::vector<int2> ctas;
     std::vector<PassLaunch> stage1, stage2;
     std::vector<RssRef> rrefs;        // RSS outputs, in item order
+    // ragged launches: stage-1 rows, stage-1 columns, stage-2 rows, stage-2 columns
+    RaggedPhase rag[4];
+    std::vector<int4> rctas;
     int nbranch1 = 0, nbranch2 = 0;
     int cta1 = 0, ncta1 = 0, cta2 = 0, ncta2 = 0;
     int nslices = 0;
     std::vector<char> rt;             // per slice: round trip
-    size_t off_srefs = 0, off_ctas = 0, off_rss = 0, bytes = 0;
+    size_t off_srefs = 0, off_ctas = 0, off_rss = 0, off_rctas = 0, bytes = 0;
     std::string signature;
 };
 
@@ -223,23 +243,67 @@ int build_layout(mxfft_engine_s* e, const mxfft_item* items, int n, Layout& L,
         ctas += sl * c * (1 + rt);
         rss += (sl > 0 && items[i].rss) ? 1 : 0;
     }
+    // ragged CTA entries: at most (n0 + n1) / 8 per slice and stage (a CTA
+    // holds at least 8 transforms), two stages
+    size_t rctas = 0;
+    for (int i = 0; i < n; i++) rctas += (size_t)items[i].slices * (items[i].n0 + items[i].n1) / 4;
     L.off_srefs = align16(refs * sizeof(SliceRef));
     L.off_ctas = align16(L.off_srefs + srefs * sizeof(StatsRef));
     L.off_rss = align16(L.off_ctas + ctas * sizeof(int2));
-    L.bytes = align16(L.off_rss + rss * sizeof(RssRef));
+    L.off_rctas = align16(L.off_rss + rss * sizeof(RssRef));
+    L.bytes = align16(L.off_rctas + rctas * sizeof(int4));
     return MXFFT_OK;
 }
 
 // Fill the tables for records at st_base (forward) and st_base + st_cap
 // (inverse statistics of round trips).
+// (d_blob: the device copy of the tables, whose slice references the ragged
+// launches' arguments point into; ragged: use the ragged launches.)
 void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*>& item_plan,
-                 SliceStats* st_base, int st_cap, Layout& L) {
+                 SliceStats* st_base, int st_cap, const void* d_blob, bool ragged, Layout& L) {
     L.refs.clear();
     L.srefs.clear();
     L.ctas.clear();
     L.stage1.clear();
     L.stage2.clear();
     L.rt.assign(L.nslices, 0);
+    // ragged launches of the register-resident pass (k = 32): a plan's group
+    // joins them when both of its axes fit the ragged geometry
+    for (int ph = 0; ph < 4; ph++) {
+        L.rag[ph] = RaggedPhase();
+        L.rag[ph].dim = (ph & 1) ? 0 : 1;
+    }
+    L.rctas.clear();
+    std::vector<int4> rc[4];
+    const SliceRef* d_refs = static_cast<const SliceRef*>(d_blob);
+    const int max_groups = fast_ragged_max_groups();
+    auto ragged_ok = [&](mxfft_plan_s* p, int ph_a, int ph_b, int ph_c) {
+        if (!ragged || p->path != 0 || p->force_generic) return false;
+        for (int ph : {ph_a, ph_b, ph_c})
+            if (ph >= 0 && L.rag[ph].ngroups >= max_groups) return false;
+        return fast_ragged_supported(pass_args(p, 1, 0, nullptr, nullptr)) &&
+               fast_ragged_supported(pass_args(p, 0, 0, nullptr, nullptr));
+    };
+    auto add_ragged = [&](int ph, mxfft_plan_s* p, int dim, int dir, int pro, int epi, int ref0,
+                          int count, bool fused) {
+        PassArgs a = pass_args(p, dim, dir, nullptr, nullptr);
+        a.ref = d_refs + ref0;
+        a.prologue = pro;
+        a.epilogue = epi;
+        RaggedPhase& R = L.rag[ph];
+        const size_t sz = fast_ragged_arg_size();
+        R.groups.resize((size_t)(R.ngroups + 1) * sz);
+        int tpc = 0;
+        size_t smem = 0;
+        fast_ragged_fill(R.groups.data() + (size_t)R.ngroups * sz, a, p->d_twh[dim][dir], p->twa[dim][dir],
+                         fused ? p->d_twh[0][1] : nullptr, fused ? &p->twa[0][1] : nullptr, &tpc, &smem);
+        const int other = dim == 1 ? p->n0 : p->n1;
+        for (int sl = 0; sl < count; sl++)
+            for (int t0 = 0; t0 < other; t0 += tpc) rc[ph].push_back(make_int4(R.ngroups, sl, t0, 0));
+        R.smem = std::max(R.smem, smem);
+        R.ngroups++;
+    };
+    int branch = 0;   // fork branches of the per-plan launches
     std::vector<int> first(n, 0);
     for (int i = 0, g = 0; i < n; i++) { first[i] = g; g += items[i].slices; }
     auto add_stats = [&](const float2* x, SliceStats* st, int npts, const KParams& kp) {
@@ -291,7 +355,7 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         const int count = (int)L.refs.size() - rows0;
         if (kind != 2 && uses_tc2d(p)) {
             // one launch: statistics, rows and columns of every slice of the group
-            PassLaunch w{p, 2, dir, PRO_PRESCALE, EPI_UNSCALE, rows0, count, (int)gi};
+            PassLaunch w{p, 2, dir, PRO_PRESCALE, EPI_UNSCALE, rows0, count, branch++};
             w.whole = 1;
             L.stage1.push_back(w);
             continue;
@@ -302,17 +366,26 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
             c.in = c.out;
             L.refs.push_back(c);
         }
-        L.stage1.push_back(PassLaunch{p, 1, dir, PRO_PRESCALE, EPI_RAW, rows0, count, (int)gi});
+        if (ragged_ok(p, 0, 1, kind == 2 ? 2 : -1)) {
+            // rows and columns in the ragged launches; the fused round trip's
+            // inverse rows join the stage-2 rows launch (they need only its columns)
+            add_ragged(0, p, 1, dir, PRO_PRESCALE, EPI_RAW, rows0, count, false);
+            add_ragged(1, p, 0, dir, PRO_NONE, kind == 2 ? EPI_RAW : EPI_UNSCALE, cols0, count, kind == 2);
+            if (kind == 2) add_ragged(2, p, 1, 1, PRO_NONE, EPI_RT_FINAL, cols0, count, false);
+            continue;
+        }
+        const int br = branch++;
+        L.stage1.push_back(PassLaunch{p, 1, dir, PRO_PRESCALE, EPI_RAW, rows0, count, br});
         if (kind == 2) {
             // fused round trip: columns forward + inverse, then the inverse rows
             // with the one decode (2^(-k - log2(n0 n1)), k of the input)
-            L.stage1.push_back(PassLaunch{p, 0, 0, PRO_NONE, EPI_RAW, cols0, count, (int)gi, 1});
-            L.stage1.push_back(PassLaunch{p, 1, 1, PRO_NONE, EPI_RT_FINAL, cols0, count, (int)gi});
+            L.stage1.push_back(PassLaunch{p, 0, 0, PRO_NONE, EPI_RAW, cols0, count, br, 1});
+            L.stage1.push_back(PassLaunch{p, 1, 1, PRO_NONE, EPI_RT_FINAL, cols0, count, br});
         } else {
-            L.stage1.push_back(PassLaunch{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, (int)gi});
+            L.stage1.push_back(PassLaunch{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, br});
         }
     }
-    L.nbranch1 = (int)groups.size();
+    L.nbranch1 = branch;
     // round trips: statistics of the forward outputs, then the inverse passes
     L.cta2 = (int)L.ctas.size();
     std::vector<mxfft_plan_s*> rt_plans;
@@ -329,6 +402,7 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
             rt_plans.push_back(item_plan[i]);
     }
     L.ncta2 = (int)L.ctas.size() - L.cta2;
+    branch = 0;
     for (size_t gi = 0; gi < rt_plans.size(); gi++) {
         mxfft_plan_s* p = rt_plans[gi];
         const int np = p->n0 * p->n1;
@@ -342,15 +416,26 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         }
         const int count = (int)L.refs.size() - r0;
         if (uses_tc2d(p)) {
-            PassLaunch w{p, 2, 1, PRO_PRESCALE, EPI_RT_FINAL, r0, count, (int)gi};
+            PassLaunch w{p, 2, 1, PRO_PRESCALE, EPI_RT_FINAL, r0, count, branch++};
             w.whole = 1;
             L.stage2.push_back(w);
             continue;
         }
-        L.stage2.push_back(PassLaunch{p, 1, 1, PRO_PRESCALE, EPI_RAW, r0, count, (int)gi});
-        L.stage2.push_back(PassLaunch{p, 0, 1, PRO_NONE, EPI_RT_FINAL, r0, count, (int)gi});
+        if (ragged_ok(p, 2, 3, -1)) {
+            add_ragged(2, p, 1, 1, PRO_PRESCALE, EPI_RAW, r0, count, false);
+            add_ragged(3, p, 0, 1, PRO_NONE, EPI_RT_FINAL, r0, count, false);
+            continue;
+        }
+        const int br = branch++;
+        L.stage2.push_back(PassLaunch{p, 1, 1, PRO_PRESCALE, EPI_RAW, r0, count, br});
+        L.stage2.push_back(PassLaunch{p, 0, 1, PRO_NONE, EPI_RT_FINAL, r0, count, br});
     }
-    L.nbranch2 = (int)rt_plans.size();
+    L.nbranch2 = branch;
+    for (int ph = 0; ph < 4; ph++) {
+        L.rag[ph].cta0 = (int)L.rctas.size();
+        L.rag[ph].ncta = (int)rc[ph].size();
+        L.rctas.insert(L.rctas.end(), rc[ph].begin(), rc[ph].end());
+    }
     // root-sum-of-squares outputs of the items that ask for them
     L.rrefs.clear();
     for (int i = 0; i < n; i++)
@@ -361,7 +446,8 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
     L.off_srefs = align16(L.refs.size() * sizeof(SliceRef));
     L.off_ctas = align16(L.off_srefs + L.srefs.size() * sizeof(StatsRef));
     L.off_rss = align16(L.off_ctas + L.ctas.size() * sizeof(int2));
-    L.bytes = align16(L.off_rss + L.rrefs.size() * sizeof(RssRef));
+    L.off_rctas = align16(L.off_rss + L.rrefs.size() * sizeof(RssRef));
+    L.bytes = align16(L.off_rctas + L.rctas.size() * sizeof(int4));
 }
 
 void pack(const Layout& L, char* dst) {
@@ -370,11 +456,14 @@ void pack(const Layout& L, char* dst) {
     std::memcpy(dst + L.off_srefs, L.srefs.data(), L.srefs.size() * sizeof(StatsRef));
     std::memcpy(dst + L.off_ctas, L.ctas.data(), L.ctas.size() * sizeof(int2));
     std::memcpy(dst + L.off_rss, L.rrefs.data(), L.rrefs.size() * sizeof(RssRef));
+    std::memcpy(dst + L.off_rctas, L.rctas.data(), L.rctas.size() * sizeof(int4));
 }
 
+// One stage: main(s) enqueues the ragged launches on the run's own stream
+// while the per-plan launches run as parallel branches on the fork streams.
+template <class Main>
 cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, int nbranch,
-                      const SliceRef* d_refs, cudaStream_t s, size_t& ev) {
-    if (stage.empty()) return cudaSuccess;
+                      const SliceRef* d_refs, cudaStream_t s, size_t& ev, Main main) {
     const int nf = std::min(nbranch, kForkStreams);
     cudaError_t err = cudaSuccess;
     if (nf > 1) {
@@ -383,6 +472,7 @@ cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, i
         for (int f = 0; f < nf && err == cudaSuccess; f++) err = cudaStreamWaitEvent(e->fork[f], e->evs[ev], 0);
         ev++;
     }
+    if (err == cudaSuccess) err = main(s);
     for (const PassLaunch& pl : stage) {
         if (err != cudaSuccess) break;
         if (pl.whole) {
@@ -425,10 +515,23 @@ cudaError_t enqueue(mxfft_engine_s* e, const Layout& L, RunBuffers& b, cudaStrea
                 seen.push_back(pl.p);
                 err = cudaMemsetAsync(pl.p->d_err, 0, sizeof(int), s);
             }
+    const int4* d_rctas = (const int4*)(d + L.off_rctas);
+    auto ragged = [&](int ph_a, int ph_b) {
+        return [&, ph_a, ph_b](cudaStream_t ms) {
+            cudaError_t r = cudaSuccess;
+            for (int ph : {ph_a, ph_b}) {
+                const RaggedPhase& R = L.rag[ph];
+                if (r == cudaSuccess && R.ngroups > 0)
+                    r = launch_fast_ragged(R.groups.data(), R.ngroups, d_rctas + R.cta0, R.ncta, R.dim,
+                                           R.smem, ms);
+            }
+            return r;
+        };
+    };
     if (err == cudaSuccess) err = launch_stats_ref(d_srefs, d_ctas + L.cta1, L.ncta1, s);
-    if (err == cudaSuccess) err = run_stage(e, L.stage1, L.nbranch1, d_refs, s, ev);
+    if (err == cudaSuccess) err = run_stage(e, L.stage1, L.nbranch1, d_refs, s, ev, ragged(0, 1));
     if (err == cudaSuccess && L.ncta2 > 0) err = launch_stats_ref(d_srefs, d_ctas + L.cta2, L.ncta2, s);
-    if (err == cudaSuccess) err = run_stage(e, L.stage2, L.nbranch2, d_refs, s, ev);
+    if (err == cudaSuccess) err = run_stage(e, L.stage2, L.nbranch2, d_refs, s, ev, ragged(2, 3));
     const RssRef* d_rss = (const RssRef*)(d + L.off_rss);
     for (size_t j = 0; j < L.rrefs.size() && err == cudaSuccess; j++)
         err = launch_rss(L.rrefs[j], d_rss + j, L.rrefs[j].images, L.rrefs[j].npts, s);
@@ -483,7 +586,7 @@ extern "C" {
 int mxfft_engine_create(float tau, float target, int flags, mxfft_engine_t* out) {
     if (!out) return MXFFT_ERR_INVALID;
     *out = nullptr;
-    if (!(tau > 0.0f && tau < 1.0f) || !(target > 0.0f) || (flags & ~7)) return MXFFT_ERR_INVALID;
+    if (!(tau > 0.0f && tau < 1.0f) || !(target > 0.0f) || (flags & ~15)) return MXFFT_ERR_INVALID;
     // validate tau / target the way a plan does
     mxfft_plan_t probe = nullptr;
     int rc = mxfft_plan(2, 2, MXFFT_E4M3, 2, tau, target, &probe);
@@ -546,7 +649,8 @@ int mxfft_engine_run(mxfft_engine_t e, const mxfft_item* items, int n_items, voi
     // buffers are never reallocated under it)
     rc = reserve(*b, L);
     if (rc) return rc;
-    fill_layout(items, n_items, item_plan, b->d_st, b->st_cap, L);
+    fill_layout(items, n_items, item_plan, b->d_st, b->st_cap, b->d_blob,
+                !(e->flags & MXFFT_ENGINE_NO_RAGGED), L);
     bool changed = false;
     rc = stage_tables(*b, L, &changed);
     if (rc) return rc;

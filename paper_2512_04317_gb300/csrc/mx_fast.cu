@@ -13,6 +13,8 @@ extern template cudaError_t launch_fast_fmt<1>(const FastArgs&, int, int, cudaSt
 extern template cudaError_t launch_fast_fmt<2>(const FastArgs&, int, int, cudaStream_t);
 extern template cudaError_t launch_fast_fmt<3>(const FastArgs&, int, int, cudaStream_t);
 extern template cudaError_t launch_fast_fmt<4>(const FastArgs&, int, int, cudaStream_t);
+cudaError_t launch_ragged(const RaggedGroups& groups, const int4* ctas, int nctas, int dim,
+                          size_t smem, cudaStream_t s);
 }  // namespace fast
 
 namespace {
@@ -80,6 +82,58 @@ cudaError_t launch_fast(const PassArgs& a, const uint32_t* twh, const TwA& twa,
     }
 }
 }  // namespace
+
+// ---- ragged pass (mx_fast_ragged.cu): 256 threads per CTA for every group --
+
+bool fast_ragged_geometry(int n, int other, int m, int* TG, int* S, int* NG) {
+    if (m != 16 || n < 64 || n > 1024) return false;
+    *TG = n == 1024 ? 8 : 16;
+    *S = *TG == 16 ? 16 : *TG + 1;
+    const int per_group = *TG * (n / 32);
+    if (per_group > 256 || 256 % per_group) return false;
+    *NG = 256 / per_group;
+    return other % (*TG * *NG) == 0;
+}
+
+bool fast_ragged_supported(const PassArgs& a) {
+    int TG, S, NG;
+    const int other = a.dim == 1 ? a.n0 : a.n1;
+    return a.fmt <= 4 && a.fp.mbits > 0 && fast_ragged_geometry(a.n, other, a.m, &TG, &S, &NG);
+}
+
+size_t fast_ragged_arg_size() { return sizeof(fast::FastArgs); }
+
+bool fast_ragged_fill(void* dst, const PassArgs& a, const uint32_t* twh, const TwA& twa,
+                      const uint32_t* twh2, const TwA* twa2, int* tpc, size_t* smem) {
+    fast::FastArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    const int other = a.dim == 1 ? a.n0 : a.n1;
+    if (!fast_ragged_geometry(a.n, other, a.m, &fa.TG, &fa.S, &fa.NG)) return false;
+    fa.a = a;
+    fa.twa = twa;
+    fa.twh = twh;
+    if (twa2) {
+        fa.fused = 1;
+        fa.twa2 = *twa2;
+        fa.twh2 = twh2;
+    }
+    fa.lgTG = fa.TG == 16 ? 4 : 3;
+    std::memcpy(dst, &fa, sizeof(fa));
+    *tpc = fa.TG * fa.NG;
+    *smem = (size_t)fa.NG * a.n * fa.S * sizeof(float2);
+    return true;
+}
+
+int fast_ragged_max_groups() { return fast::kMaxRaggedGroups; }
+
+cudaError_t launch_fast_ragged(const void* groups, int ngroups, const int4* ctas, int nctas, int dim,
+                               size_t smem, cudaStream_t s) {
+    if (ngroups < 1 || ngroups > fast::kMaxRaggedGroups) return cudaErrorInvalidValue;
+    static thread_local fast::RaggedGroups rg;   // 24 KB: not on the stack
+    rg.n = ngroups;
+    std::memcpy(rg.g, groups, sizeof(fast::FastArgs) * (size_t)ngroups);
+    return fast::launch_ragged(rg, ctas, nctas, dim, smem, s);
+}
 
 cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                                 int ng, cudaStream_t s) {

@@ -295,5 +295,14 @@ struct FastArgs {
     const uint32_t* twh2;
 };
 
+// Arguments of the groups of one ragged launch (mx_fast_ragged.cu), passed as
+// one kernel parameter (at most 32 KB of parameters).
+constexpr int kMaxRaggedGroups = 48;
+struct RaggedGroups {
+    int n;
+    FastArgs g[kMaxRaggedGroups];
+};
+static_assert(sizeof(RaggedGroups) <= 32000, "ragged groups fit the kernel parameter space");
+
 }  // namespace fast
 }  // namespace mxfft

@@ -34,8 +34,8 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
     stage_a<FMT, LOGM, 4>(r, twa, fp, (unsigned)TG);
     stage_a<FMT, LOGM, 8>(r, twa, fp, (unsigned)TG);
     stage_a<FMT, LOGM, 16>(r, twa, fp, (unsigned)TG);
-#pragma unroll
     const int gs_slots = (1 << L) * S;   // the group's shared rows
+    (void)gs_slots;
 #pragma unroll
     for (int t = 0; t < 32; t++) Gs[MX_BND((32 * sigma + t) * S + tau, gs_slots)] = r[t];
     __syncthreads();
@@ -91,11 +91,11 @@ __device__ __forceinline__ void all_stages(float2 (&r)[32], float2 (&R)[4][8], i
     }
 }
 
-// FUSED (columns only): forward, then inverse columns of the fused round trip
-// (reading C17) in one launch.
+// One CTA's work: transforms t0 .. t0 + TG NG - 1 of slice `slice`, all
+// stages.  FUSED (columns only): forward, then inverse columns of the fused
+// round trip (reading C17).
 template <int FMT, int LOGM, int DIM, bool FUSED>
-__global__ void __launch_bounds__(kMaxThreads)
-fast_pass_kernel(const FastArgs fa) {
+__device__ __forceinline__ void fast_body(const FastArgs& fa, const int slice, const int t0) {
     extern __shared__ float2 sm[];
     const PassArgs& a = fa.a;
     const int n = a.n, L = a.logn, TG = fa.TG, S = fa.S;
@@ -106,11 +106,6 @@ fast_pass_kernel(const FastArgs fa) {
     const int w = tid & ((1 << lg_pg) - 1);
     const int tau = w & (TG - 1);
     const int sigma = w >> lgTG;
-    const int other = DIM == 1 ? a.n0 : a.n1;
-    const int tpc = TG * fa.NG;
-    const int per_slice = other / tpc;
-    const int slice = blockIdx.x / per_slice;
-    const int t0 = (blockIdx.x - slice * per_slice) * tpc;
     const int tr = t0 + (grp << lgTG) + tau;     // row (dim 1) or column (dim 0)
     float2* __restrict__ Gs = sm + (size_t)grp * n * S;
     const size_t sbase = (size_t)slice * a.n0 * a.n1;
@@ -210,6 +205,18 @@ fast_pass_kernel(const FastArgs fa) {
                     make_float4(v0.x, v0.y, v1.x, v1.y);
             }
     }
+}
+
+// One launch of one plan's pass: CTA b takes the b-th run of TG NG
+// transforms, slice by slice.
+template <int FMT, int LOGM, int DIM, bool FUSED>
+__global__ void __launch_bounds__(kMaxThreads)
+fast_pass_kernel(const FastArgs fa) {
+    const int other = DIM == 1 ? fa.a.n0 : fa.a.n1;
+    const int tpc = fa.TG * fa.NG;
+    const int per_slice = other / tpc;
+    const int slice = blockIdx.x / per_slice;
+    fast_body<FMT, LOGM, DIM, FUSED>(fa, slice, (blockIdx.x - slice * per_slice) * tpc);
 }
 
 // Launch geometry: TG transforms per group (8 for n = 2048 so a group fits in

@@ -198,6 +198,20 @@ cudaError_t launch_rss(const RssRef& val, const RssRef* dev, long long images, l
 int fast_ng_candidates(int n, int other, int m, int* out, int max);
 int fast_ng_tuned(int n, int other, int dim, int fmt, int m, int batch);
 void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng, double us);
+// Ragged register-resident pass: one launch over many plans' passes along
+// one axis (k = 32, n in [64, 1024]), every CTA 256 threads.  A group's
+// arguments are filled on the host into fast_ragged_arg_size() bytes (with
+// twa2 / twh2 for the fused round trip's columns); tpc receives the
+// transforms per CTA and smem the CTA's dynamic shared memory.  ctas[b] =
+// (group, slice within the group's references, first transform, 0).
+bool fast_ragged_supported(const PassArgs& a);
+size_t fast_ragged_arg_size();
+bool fast_ragged_fill(void* dst, const PassArgs& a, const uint32_t* twh, const TwA& twa,
+                      const uint32_t* twh2, const TwA* twa2, int* tpc, size_t* smem);
+// groups: ngroups filled records on the host (at most fast_ragged_max_groups()).
+int fast_ragged_max_groups();
+cudaError_t launch_fast_ragged(const void* groups, int ngroups, const int4* ctas, int nctas, int dim,
+                               size_t smem, cudaStream_t s);
 // The register-resident pass with ng groups per CTA (ng = 0: tuned or default).
 cudaError_t launch_fast_pass_ng(const PassArgs& a, const uint32_t* twh, const TwA& twa, int batch,
                                 int ng, cudaStream_t s);

@@ -25,7 +25,7 @@ FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
 OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL, OPT_FUSED2D = range(7)
 
 OPS = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}
-ENGINE_GRAPHS, ENGINE_TC16, ENGINE_FUSED2D = 1, 2, 4
+ENGINE_GRAPHS, ENGINE_TC16, ENGINE_FUSED2D, ENGINE_NO_RAGGED = 1, 2, 4, 8
 
 # every symbol include/mxfft.h declares
 EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
@@ -486,9 +486,9 @@ class Engine:
     current torch stream, with the same bits as the per-plan calls."""
 
     def __init__(self, tau: float = 1e-3, target: float = 0.5, graphs: bool = False,
-                 tc16: bool = False, fused2d: bool = False):
+                 tc16: bool = False, fused2d: bool = False, ragged: bool = True):
         flags = ((ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0) |
-                 (ENGINE_FUSED2D if fused2d else 0))
+                 (ENGINE_FUSED2D if fused2d else 0) | (0 if ragged else ENGINE_NO_RAGGED))
         self.handle = mxfft_engine_create(tau, target, flags)
         self._slices = 0
 

@@ -66,3 +66,23 @@ def check(x, fmt="e4m3", k=32, op="forward", **kw):
     assert_bitwise(got[ok], want[ok], f"{fmt} k={k} {op} {shape}")
     assert np.array_equal(np.asarray(kg).reshape(np.asarray(kw_).shape), kw_), (kg, kw_)
     return got, want
+
+
+def assert_close_to_emulation(got, want, what=""):
+    """Element-wise comparison of the tensor-core variant with its emulation.
+    The hardware accumulates the 32 exact products of a DFT row in FP32 and
+    the emulation in FP64, so a rare element can differ by one FP32 rounding,
+    which may move a later 8-bit rounding by one grid step of its block.  Each
+    element's error is bounded by the peak of its row and, separately, of its
+    column (an index error confined to one row or one column shows in the
+    other view): almost every element agrees to FP32 level and none by more
+    than a few grid steps, while an index error gives O(1) errors."""
+    g = np.asarray(got).astype(np.complex128)
+    w = np.asarray(want).astype(np.complex128)
+    assert np.isfinite(g).all(), what
+    for axis in (-1, -2):
+        err = np.abs(g - w)
+        peak = np.abs(w).max(axis=axis, keepdims=True)
+        rel = err / np.maximum(peak, 1e-300)
+        assert rel.max() < 0.1, (what, axis, rel.max())
+        assert np.mean(rel > 1e-5) < 1e-3, (what, axis, np.mean(rel > 1e-5))

@@ -218,3 +218,70 @@ def test_engine_graph_cache_eviction(cuda_device):
             eng.run([("forward", xt[:b], yt[:b], "e4m3", 16)])
         torch.cuda.synchronize()
     assert_same([yt.cpu().numpy()], [want])
+
+
+def _plan_reference(items):
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    outs = []
+    for op, x, fmt, k in items:
+        with mxfft.Plan(x.shape[-2], x.shape[-1], fmt, k) as p:
+            outs.append(getattr(p, op)(x).cpu().numpy())
+    torch.cuda.synchronize()
+    return outs
+
+
+def test_ragged_mix_runs_in_six_launches_and_equals_plan_calls(cuda_device):
+    # sizes 128..1024, non-square, three formats, all four ops in one run: the
+    # radix-2 passes of every group go into one ragged launch per axis and stage
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    shapes = [(128, 128), (256, 256), (512, 512), (1024, 1024), (256, 512), (128, 1024), (512, 128)]
+    fmts = ["e4m3", "e5m2", "e2m3"]
+    ops = ["forward", "inverse", "roundtrip", "roundtrip_fused"]
+    items = []
+    for i, (n0, n1) in enumerate(shapes):
+        for j in range(2):
+            op = ops[(i + j) % 4]
+            dom = "image" if op.startswith("roundtrip") else "kspace"
+            x = torch.from_numpy(phantom.mri_batch(n0, n1, 1 + (i + j) % 3, 1, config_id=70 + 2 * i + j,
+                                                   domain=dom)).cuda()
+            items.append((op, x, fmts[(i + 2 * j) % 3], 32))
+    want = _plan_reference(items)
+    for graphs in (False, True):
+        for ragged in (True, False):
+            with mxfft.Engine(graphs=graphs, ragged=ragged) as eng:
+                outs = [torch.empty_like(x) for _, x, _, _ in items]
+                for _ in range(2):
+                    eng.run([(op, x, y, f, k) for (op, x, f, k), y in zip(items, outs)])
+                    torch.cuda.synchronize()
+                    if ragged:
+                        assert eng.launches_per_run() == 6
+                    for y, w in zip(outs, want):
+                        np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), w.view(np.uint32))
+
+
+def test_ragged_groups_beyond_one_launch_fall_back(cuda_device):
+    # 60 (plan, direction) groups that fit the ragged launch: the first 48 go
+    # into the ragged launches, the rest keep their own; every result is unchanged
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    items = []
+    shapes = [(128, 128), (256, 256), (512, 512), (1024, 1024), (128, 256), (256, 128)]
+    for i, (n0, n1) in enumerate(shapes):
+        for j, fmt in enumerate(["e4m3", "e5m2", "e2m3", "e3m2", "e2m1"]):
+            for op in ("forward", "inverse"):
+                x = torch.from_numpy(phantom.random_complex((1, n0, n1), seed=100 + 10 * i + j,
+                                                            scale=2.0)).cuda()
+                items.append((op, x, fmt, 32))
+    want = _plan_reference(items)
+    with mxfft.Engine(graphs=True) as eng:
+        outs = [torch.empty_like(x) for _, x, _, _ in items]
+        eng.run([(op, x, y, f, k) for (op, x, f, k), y in zip(items, outs)])
+        torch.cuda.synchronize()
+        assert eng.launches_per_run() > 3
+    for y, w in zip(outs, want):
+        np.testing.assert_array_equal(y.cpu().numpy().view(np.uint32), w.view(np.uint32))

@@ -351,7 +351,7 @@ def _pct(lat_ms):
 
 
 def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
-                fractions=SERVING_FRACTIONS, rates=None, rss=True, tc16=False):
+                fractions=SERVING_FRACTIONS, rates=None, rss=True, tc16=False, ragged=True):
     """Continuous-batching server under the serving mix: saturated rate, then
     Poisson arrivals at fractions of it, p50 / p99 latency (submit to result in
     host memory); the plain FP32 per-slice GPU path (torch.fft, one call per
@@ -374,7 +374,7 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
 
     def run_mx(rate):
         with mxfft.Server(slots=slots, max_batch_slices=batch_slices,
-                          max_batch_bytes=batch_mb << 20, tc16=tc16) as srv:
+                          max_batch_bytes=batch_mb << 20, tc16=tc16, ragged=ragged) as srv:
             # plans of every (size, format) resident before the clock starts
             def submit(tag, sz, c, fmt, op, slot):
                 if rss:

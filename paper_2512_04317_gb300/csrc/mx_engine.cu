@@ -277,12 +277,19 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
     std::vector<int4> rc[4];
     const SliceRef* d_refs = static_cast<const SliceRef*>(d_blob);
     const int max_groups = fast_ragged_max_groups();
+    auto fits = [&](mxfft_plan_s* p) {
+        return ragged && p->path == 0 && !p->force_generic &&
+               fast_ragged_supported(pass_args(p, 1, 0, nullptr, nullptr)) &&
+               fast_ragged_supported(pass_args(p, 0, 0, nullptr, nullptr));
+    };
+    // a stage uses the ragged launches when at least two groups fit them (a
+    // single group keeps its tuned per-plan launches, as few in number)
+    bool use = false;
     auto ragged_ok = [&](mxfft_plan_s* p, int ph_a, int ph_b, int ph_c) {
-        if (!ragged || p->path != 0 || p->force_generic) return false;
+        if (!use || !fits(p)) return false;
         for (int ph : {ph_a, ph_b, ph_c})
             if (ph >= 0 && L.rag[ph].ngroups >= max_groups) return false;
-        return fast_ragged_supported(pass_args(p, 1, 0, nullptr, nullptr)) &&
-               fast_ragged_supported(pass_args(p, 0, 0, nullptr, nullptr));
+        return true;
     };
     auto add_ragged = [&](int ph, mxfft_plan_s* p, int dim, int dir, int pro, int epi, int ref0,
                           int count, bool fused) {
@@ -338,6 +345,12 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         if (items[i].slices == 0) continue;
         const std::pair<mxfft_plan_s*, int> key(item_plan[i], kind_of(items[i].op));
         if (std::find(groups.begin(), groups.end(), key) == groups.end()) groups.push_back(key);
+    }
+    {
+        int fit = 0;
+        for (const auto& g : groups)
+            fit += fits(g.first) && (g.second == 2 || !uses_tc2d(g.first));
+        use = fit >= 2;
     }
     for (size_t gi = 0; gi < groups.size(); gi++) {
         mxfft_plan_s* p = groups[gi].first;
@@ -403,6 +416,11 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
     }
     L.ncta2 = (int)L.ctas.size() - L.cta2;
     branch = 0;
+    {
+        int fit = L.rag[2].ngroups;   // fused round trips' inverse rows, already ragged
+        for (mxfft_plan_s* p : rt_plans) fit += fits(p) && !uses_tc2d(p);
+        use = fit >= 2;
+    }
     for (size_t gi = 0; gi < rt_plans.size(); gi++) {
         mxfft_plan_s* p = rt_plans[gi];
         const int np = p->n0 * p->n1;

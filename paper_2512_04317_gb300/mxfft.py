@@ -548,8 +548,9 @@ class Server:
     stay alive until their completion is returned by poll()."""
 
     def __init__(self, slots=4, max_batch_slices=256, mem_budget=0, tau=1e-3, target=0.5,
-                 graphs=False, tc16=False, max_batch_bytes=0):
-        flags = (ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0)
+                 graphs=False, tc16=False, max_batch_bytes=0, ragged=True):
+        flags = ((ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0) |
+                 (0 if ragged else ENGINE_NO_RAGGED))
         self.handle = mxfft_server_create(slots, max_batch_slices, mem_budget, tau, target, flags,
                                           max_batch_bytes)
         self._keep = {}

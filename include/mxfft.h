@@ -153,7 +153,10 @@ int mxfft_inverse(mxfft_plan_t plan, const void *in, void *out, int batch,
  * mxfft_roundtrip -- (1/(n0 n1)) F^-1{F{x}} per slice (Eq. 1 "round-trip"):
  * the forward output y = 2^-k A is formed, the inverse takes its own prescale
  * k_inv from y, and one scaling by 2^(-k_inv - log2(n0 n1)) ends it.
- * `out` also serves as the intermediate buffer.
+ * `out` also serves as the intermediate buffer.  On the tensor-core path
+ * (MXFFT_OPT_PATH = 1, n0 != 2048) the forward columns pass accumulates
+ * y's statistics as it stores y, so no separate statistics pass over y runs;
+ * k_inv is the same exponent either way.
  */
 int mxfft_roundtrip(mxfft_plan_t plan, const void *in, void *out, int batch,
                     void *stream);
@@ -262,7 +265,9 @@ int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, 
  * launches (statistics, rows, columns, and for round trips statistics,
  * inverse rows, inverse columns); other plans (tensor-core, other k, the
  * generic pass) one launch per pass and (plan, direction) group, as parallel
- * branches.  Results are bit-identical to the per-plan calls.
+ * branches; round trips on the tensor-core path take their inverse
+ * statistics in the forward columns pass (no second statistics launch).
+ * Results are bit-identical to the per-plan calls.
  * ====================================================================== */
 typedef enum {
     MXFFT_OP_FORWARD = 0,

@@ -229,10 +229,25 @@ struct StatAcc {
 // CTA of the slice selects k.  Every thread of the CTA must call it; sh_hist
 // must have been zeroed and the CTA synchronised after the adds.  sh_misc
 // needs 4 words of shared memory.
+__device__ __forceinline__ void stats_flush_and_select_n(StatAcc acc, uint32_t* sh_hist,
+                                                         uint32_t* sh_misc, SliceStats* st,
+                                                         uint32_t contrib, uint32_t total,
+                                                         const KParams& kp);
+
 __device__ __forceinline__ void stats_flush_and_select(StatAcc acc, uint32_t* sh_hist,
                                                        uint32_t* sh_misc, SliceStats* st,
                                                        uint32_t ctas_per_slice,
                                                        const KParams& kp) {
+    stats_flush_and_select_n(acc, sh_hist, sh_misc, st, 1u, ctas_per_slice, kp);
+}
+
+// The same flush for a CTA that covered `contrib` of the slice's `total`
+// units (tiles of a persistent pass): the flush that completes the slice
+// selects k.
+__device__ __forceinline__ void stats_flush_and_select_n(StatAcc acc, uint32_t* sh_hist,
+                                                         uint32_t* sh_misc, SliceStats* st,
+                                                         uint32_t contrib, uint32_t total,
+                                                         const KParams& kp) {
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     // warp reductions
@@ -263,8 +278,8 @@ __device__ __forceinline__ void stats_flush_and_select(StatAcc acc, uint32_t* sh
     __threadfence();
     __syncthreads();
     if (tid == 0) {
-        uint32_t prev = atomicAdd(&st->done, 1u);
-        sh_misc[3] = (prev == ctas_per_slice - 1) ? 1u : 0u;
+        uint32_t prev = atomicAdd(&st->done, contrib);
+        sh_misc[3] = (prev + contrib == total) ? 1u : 0u;
     }
     __syncthreads();
     if (sh_misc[3] && tid < 32) {

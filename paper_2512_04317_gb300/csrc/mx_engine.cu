@@ -47,6 +47,8 @@ struct PassLaunch {
     int branch;           // fork branch within its stage
     int fused = 0;        // 1: forward + inverse columns of the fused round trip
     int whole = 0;        // 1: the fused 2D kernel (statistics, rows, columns)
+    int stats_out = 0;    // 1: the pass accumulates its output's statistics into
+                          // the references' st_out records (round trips, tensor-core path)
 };
 
 // One ragged launch: the register-resident passes of several plans along
@@ -324,6 +326,12 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
     auto whole2d = [&](int i) {
         return item_plan[i] && uses_tc2d(item_plan[i]) && items[i].op != MXFFT_OP_ROUNDTRIP_FUSED;
     };
+    // round trips whose forward columns pass (tensor-core path) takes the
+    // inverse's statistics of its output: no statistics launch for them
+    auto folded = [&](int i) {
+        return items[i].op == MXFFT_OP_ROUNDTRIP && item_plan[i] && tc16_folds_stats(item_plan[i]) &&
+               !uses_tc2d(item_plan[i]);
+    };
     // statistics of every other input
     L.cta1 = 0;
     for (int i = 0; i < n; i++) {
@@ -358,14 +366,18 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         const int dir = kind == 1 ? 1 : 0;
         const int np = p->n0 * p->n1;
         const int rows0 = (int)L.refs.size();
+        std::vector<SliceStats*> st_out;   // per slice: inverse statistics folded into the columns pass
         for (int i = 0; i < n; i++) {
             if (item_plan[i] != p || kind_of(items[i].op) != kind) continue;
-            for (int s = 0; s < items[i].slices; s++)
+            for (int s = 0; s < items[i].slices; s++) {
                 L.refs.push_back(SliceRef{(const float2*)items[i].in + (size_t)s * np,
                                           (float2*)items[i].out + (size_t)s * np,
                                           st_base + first[i] + s, nullptr});
+                st_out.push_back(folded(i) ? st_base + st_cap + first[i] + s : nullptr);
+            }
         }
         const int count = (int)L.refs.size() - rows0;
+        const bool any_out = std::any_of(st_out.begin(), st_out.end(), [](SliceStats* q) { return q; });
         if (kind != 2 && uses_tc2d(p)) {
             // one launch: statistics, rows and columns of every slice of the group
             PassLaunch w{p, 2, dir, PRO_PRESCALE, EPI_UNSCALE, rows0, count, branch++};
@@ -377,6 +389,7 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         for (int r = 0; r < count; r++) {
             SliceRef c = L.refs[rows0 + r];
             c.in = c.out;
+            c.st_out = st_out[r];
             L.refs.push_back(c);
         }
         if (ragged_ok(p, 0, 1, kind == 2 ? 2 : -1)) {
@@ -395,7 +408,9 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
             L.stage1.push_back(PassLaunch{p, 0, 0, PRO_NONE, EPI_RAW, cols0, count, br, 1});
             L.stage1.push_back(PassLaunch{p, 1, 1, PRO_NONE, EPI_RT_FINAL, cols0, count, br});
         } else {
-            L.stage1.push_back(PassLaunch{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, br});
+            PassLaunch c{p, 0, dir, PRO_NONE, EPI_UNSCALE, cols0, count, br};
+            c.stats_out = any_out ? 1 : 0;
+            L.stage1.push_back(c);
         }
     }
     L.nbranch1 = branch;
@@ -406,7 +421,7 @@ void fill_layout(const mxfft_item* items, int n, const std::vector<mxfft_plan_s*
         if (items[i].op != MXFFT_OP_ROUNDTRIP || items[i].slices == 0) continue;
         const int np = items[i].n0 * items[i].n1;
         for (int s = 0; s < items[i].slices; s++) {
-            if (!whole2d(i))
+            if (!whole2d(i) && !folded(i))
                 add_stats((const float2*)items[i].out + (size_t)s * np, st_base + st_cap + first[i] + s,
                           np, kparams(item_plan[i]));
             L.rt[first[i] + s] = 1;
@@ -503,6 +518,7 @@ cudaError_t run_stage(mxfft_engine_s* e, const std::vector<PassLaunch>& stage, i
         a.ref = d_refs + pl.ref0;
         a.prologue = pl.prologue;
         a.epilogue = pl.epilogue;
+        a.stats_out = pl.stats_out;
         cudaStream_t bs = nf > 1 ? e->fork[pl.branch % nf] : s;
         err = pl.fused ? fused_cols_pass(pl.p, a, pl.count, bs) : timed_pass(pl.p, a, pl.count, bs);
     }

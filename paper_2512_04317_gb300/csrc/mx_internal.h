@@ -78,8 +78,10 @@ struct SliceRef {
     const float2* in;
     float2* out;
     SliceStats* st;
-    const void* reserved;   // 32-byte entries
+    SliceStats* st_out;     // non-null: accumulate the statistics of this pass's
+                            // output here (the round trip's inverse prescale)
 };
+static_assert(sizeof(SliceRef) == 32, "32-byte slice references");
 
 struct PassArgs {
     const float2* in;
@@ -93,6 +95,8 @@ struct PassArgs {
     const float2* tw;     // twiddle element values, index (h - 1) + j per stage h
     const int8_t* tws;    // twiddle block scale exponent for the same index
     SliceStats* st;       // statistics holding k for the prologue / epilogue
+    SliceStats* st_out;   // non-null (strided batches): statistics of the output
+    int stats_out;        // 1: accumulate the output's statistics (st_out / ref[i].st_out)
     int prologue, epilogue;
     int lg_total;         // log2(n0 * n1) for EPI_RT_FINAL
     int fmt;              // element format code (mxfft_format)
@@ -124,6 +128,11 @@ struct Tc16Args {
     int stall;                        // test hook: issue no matrix product
     int g;                            // vectors per MX block: k / 32 (1, 2, 4)
     int inv;                          // 1: inverse transform (sign of the radix-4 stage)
+    SliceStats* st_out;               // columns pass, strided batches: Alg. 1 statistics of
+                                      // the output accumulated here (see SliceRef::st_out)
+    int stats_out;                    // 1: accumulate output statistics (records per slice
+                                      // from st_out or the references; null records skipped)
+    KParams kp;                       // exponent selection of those statistics
 };
 
 // Arguments of the fused 2D tensor-core transform (mx_tc2d.cu): every slice

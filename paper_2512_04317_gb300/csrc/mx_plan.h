@@ -58,6 +58,9 @@ KParams kparams(const mxfft_plan_s* p);
 PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out);
 // Whether a plan's forward / inverse transforms run as the fused 2D
 // tensor-core kernel; its arguments for one launch (dir 0 forward, 1 inverse).
+// true when the tensor-core columns pass of a round trip accumulates the
+// inverse's prescale statistics of its output (no separate statistics pass)
+bool tc16_folds_stats(const mxfft_plan_s* p);
 bool uses_tc2d(const mxfft_plan_s* p);
 Tc2dArgs tc2d_args(const mxfft_plan_s* p, int dir, const float2* in, float2* out, SliceStats* st,
                    int epilogue);

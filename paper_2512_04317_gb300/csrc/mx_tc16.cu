@@ -117,8 +117,9 @@ struct Mma {
 
 // One MMA round: every thread MX-encodes its 16-element vector into its row
 // of the A operand (thread i: operand half i / 128, row i % 128), one thread
-// issues both products, all read back their row.  Returns the 16 complex
-// DFT outputs (scales applied) in y.  Ends with a CTA barrier, after which the
+// issues both products, all read back their row.  Leaves the 16 complex
+// DFT outputs in y without their scale and returns that scale (a power of
+// two; NaN for a non-finite block).  Ends with a CTA barrier, after which the
 // A operand, the accumulators and the caller's shared-memory writes made
 // before the call may be reused / are visible.
 // Vector v of a round belongs to transform t and has index q in the round's
@@ -134,7 +135,7 @@ __device__ __forceinline__ int block_member(int v, int g, int lgt, int i) {
 }
 
 template <int FMT, int DIM>
-__device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
+__device__ __forceinline__ float dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
                                             uint32_t idesc, int emax, bool issue, int g,
                                             int lgt, uint32_t* sAm) {
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -194,16 +195,22 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
         mm.ok = false;
     }
     // D is exact-scaled by the vector's scale and the matrix rows' scale, which
-    // is 2^-emax for every row (each row holds an entry of magnitude 1)
-    const float sc = bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
-    const float2 sc2 = make_float2(sc, sc);
+    // is 2^-emax for every row (each row holds an entry of magnitude 1); y
+    // receives D unscaled and the caller applies sc
 #pragma unroll
-    for (int k = 0; k < 16; k++) y[k] = mul2_rn(make_float2(d[2 * k], d[2 * k + 1]), sc2);
+    for (int k = 0; k < 16; k++) y[k] = make_float2(d[2 * k], d[2 * k + 1]);
+    return bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
 }
 
-__device__ __forceinline__ float2 cmul(float2 w, float2 y) {
-    return make_float2(__fsub_rn(__fmul_rn(w.x, y.x), __fmul_rn(w.y, y.y)),
-                       __fadd_rn(__fmul_rn(w.x, y.y), __fmul_rn(w.y, y.x)));
+// Twiddle w times the round output D sc: each product w D rounded, scaled
+// exactly by sc (a power of two), then added, so that a multiply-add
+// contraction of the sum can only absorb an exact product and the value is
+// the separately rounded (w.re y.re - w.im y.im, w.re y.im + w.im y.re) of y =
+// D sc whatever instructions the code generator picks.
+__device__ __forceinline__ float2 cmul_sc(float2 w, float2 D, float sc) {
+    return make_float2(
+        __fsub_rn(__fmul_rn(__fmul_rn(w.x, D.x), sc), __fmul_rn(__fmul_rn(w.y, D.y), sc)),
+        __fadd_rn(__fmul_rn(__fmul_rn(w.x, D.y), sc), __fmul_rn(__fmul_rn(w.y, D.x), sc)));
 }
 
 __device__ __forceinline__ float2 scale2(float2 v, float s) {
@@ -313,6 +320,32 @@ tc16_pass_kernel(const Args a) {
     const size_t slice_pts = (size_t)a.n0 * a.n1;      // bounds of the debug build
     (void)slice_pts;
     SliceCache ld, cs;   // slices of the tile being loaded and of the current tile
+    // Alg. 1 statistics of this pass's output for the next transform's
+    // prescale (the round trip's inverse), columns pass only: every stored
+    // value goes through the statistics kernel's StatAcc; a run of tiles of
+    // one slice is one segment, flushed into the slice's record with its tile
+    // count when the slice changes and at the end (the flush that completes
+    // the slice's tiles selects k).  Not for the strided n = 2048 columns
+    // pass, whose tiles of a slice are spread over all CTAs.
+    __shared__ uint32_t so_hist[kHistBins];
+    __shared__ uint32_t so_misc[4];
+    const bool fold = DIM == 0 && !kStrided && a.stats_out != 0;
+    StatAcc oacc;
+    int seg_slice = -1, seg_tiles = 0;
+    SliceStats* seg_st = nullptr;
+    if (fold)
+        for (int b = tid; b < kHistBins; b += kThreads) so_hist[b] = 0;
+    auto flush_out = [&]() {
+        if (seg_st) {
+            __syncthreads();
+            stats_flush_and_select_n(oacc, so_hist, so_misc, seg_st, (uint32_t)seg_tiles,
+                                     (uint32_t)per_slice, a.kp);
+            __syncthreads();
+            for (int b = tid; b < kHistBins; b += kThreads) so_hist[b] = 0;
+            oacc = StatAcc();
+            __syncthreads();
+        }
+    };
     if (my_tiles > 0) {
         const int sl = tile_begin / per_slice;
         resolve(a, sl, false, ld);
@@ -347,6 +380,14 @@ tc16_pass_kernel(const Args a) {
         cp_async_commit();
         const int slice = tile / per_slice;
         const int t0 = (tile - slice * per_slice) * T;
+        if (fold && slice != seg_slice) {
+            flush_out();
+            seg_slice = slice;
+            seg_tiles = 0;
+            seg_st = a.ref ? a.ref[slice].st_out : (a.st_out ? a.st_out + slice : nullptr);
+        }
+        seg_tiles++;
+        const bool fold_tile = fold && seg_st != nullptr;   // the same for the whole CTA
         // the slice's exponent is fetched while the tile's copies land
         resolve(a, slice, with_k, cs);
         const int kslice = cs.k;
@@ -371,13 +412,13 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            const float sc = dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
                 const float4 w = tw[k >> 1];
-                d[slot<LOGN, DIM>(t, M * k + j2)] = cmul(make_float2(w.x, w.y), y[k]);
-                d[slot<LOGN, DIM>(t, M * (k + 1) + j2)] = cmul(make_float2(w.z, w.w), y[k + 1]);
+                d[slot<LOGN, DIM>(t, M * k + j2)] = cmul_sc(make_float2(w.x, w.y), y[k], sc);
+                d[slot<LOGN, DIM>(t, M * (k + 1) + j2)] = cmul_sc(make_float2(w.z, w.w), y[k + 1], sc);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
@@ -410,12 +451,14 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            const float sc = dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             if (r == 1) {
                 // X[k1 + 16 k2]
 #pragma unroll
                 for (int k = 0; k < 16; k++) {
-                    const float2 val = scale_out ? scale2(y[k], post) : y[k];
+                    const float2 yk = scale2(y[k], sc);
+                    const float2 val = scale_out ? scale2(yk, post) : yk;
+                    if (fold_tile) oacc.add<true>(val.x, val.y, so_hist);
                     const int e = k1 + 16 * k;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + e, slice_pts)] = val;
                     else out[MX_BND((size_t)e * a.n1 + t0 + t, slice_pts)] = val;
@@ -425,8 +468,9 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int k = 0; k < 16; k += 2) {
                     const float4 w = tw[k >> 1];
-                    d[slot<LOGN, DIM>(t, M * k1 + r * k + j22)] = cmul(make_float2(w.x, w.y), y[k]);
-                    d[slot<LOGN, DIM>(t, M * k1 + r * (k + 1) + j22)] = cmul(make_float2(w.z, w.w), y[k + 1]);
+                    d[slot<LOGN, DIM>(t, M * k1 + r * k + j22)] = cmul_sc(make_float2(w.x, w.y), y[k], sc);
+                    d[slot<LOGN, DIM>(t, M * k1 + r * (k + 1) + j22)] =
+                        cmul_sc(make_float2(w.z, w.w), y[k + 1], sc);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -481,6 +525,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int k22 = 0; k22 < 4; k22++) {
                     const float2 val = scale_out ? scale2(X[k22], post) : X[k22];
+                    if (fold_tile) oacc.add<true>(val.x, val.y, so_hist);
                     const int eo = k1 + 16 * k21 + 256 * k22;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + eo, slice_pts)] = val;
                     else out[MX_BND((size_t)eo * a.n1 + t0 + t, slice_pts)] = val;
@@ -558,6 +603,7 @@ tc16_pass_kernel(const Args a) {
                     float2 X = k < 4 ? make_float2(__fadd_rn(E[k4].x, P[k4].x), __fadd_rn(E[k4].y, P[k4].y))
                                      : make_float2(__fsub_rn(E[k4].x, P[k4].x), __fsub_rn(E[k4].y, P[k4].y));
                     if (scale_out) X = scale2(X, post);
+                    if (fold_tile) oacc.add<true>(X.x, X.y, so_hist);
                     const int eo = k1 + 16 * k21 + 256 * k;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + eo, slice_pts)] = X;
                     else out[MX_BND((size_t)eo * a.n1 + t0 + t, slice_pts)] = X;
@@ -587,6 +633,10 @@ tc16_pass_kernel(const Args a) {
                 float2 s0 = make_float2(__fadd_rn(p.x, q.x), __fadd_rn(p.y, q.y));
                 float2 s1 = make_float2(__fsub_rn(p.x, q.x), __fsub_rn(p.y, q.y));
                 if (scale_out) { s0 = scale2(s0, post); s1 = scale2(s1, post); }
+                if (fold_tile) {
+                    oacc.add<true>(s0.x, s0.y, so_hist);
+                    oacc.add<true>(s1.x, s1.y, so_hist);
+                }
                 const int e0 = k1 + 16 * k21, e1 = e0 + 256;
                 if (DIM == 1) {
                     out[MX_BND((size_t)(t0 + t) * a.n1 + e0, slice_pts)] = s0;
@@ -600,6 +650,7 @@ tc16_pass_kernel(const Args a) {
             if (__syncthreads_or(!mm.ok)) break;
         }
     }
+    if (fold) flush_out();
     cp_async_wait_all();
 
     // ---- teardown: an abandoned product is waited for once more, then the

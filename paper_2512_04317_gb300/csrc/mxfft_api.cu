@@ -391,10 +391,16 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
         r2.prologue = PRO_NONE;
         r2.epilogue = EPI_RT_FINAL;
         if ((e = timed_pass(p, r2, batch, s)) != cudaSuccess) return cuda_status(e);
-    } else if ((e = timed_pass(p, cols, batch, s)) != cudaSuccess) {
-        return cuda_status(e);
+    } else {
+        // the round trip on the tensor-core path: the forward columns pass
+        // takes the inverse's prescale statistics of what it stores
+        if (op == 2 && tc16_folds_stats(p)) {
+            cols.st_out = st_i;
+            cols.stats_out = 1;
+        }
+        if ((e = timed_pass(p, cols, batch, s)) != cudaSuccess) return cuda_status(e);
     }
-    if (op == 2) {
+    if (op == 2 && !cols.stats_out) {
         // the inverse's own prescale statistics, on the forward output y
         {
             NvtxRange sr("mxfft statistics");
@@ -403,6 +409,8 @@ int run(mxfft_plan_t p, const void* in, void* out, int batch, void* stream, int 
             prof_end(rs, s);
         }
         if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (op == 2) {
         PassArgs r2 = pass_args(p, 1, 1, y, y);
         r2.st = st_i;
         r2.prologue = PRO_PRESCALE;
@@ -479,6 +487,12 @@ PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, fl
     return a;
 }
 
+bool tc16_folds_stats(const mxfft_plan_s* p) {
+    // the tensor-core columns pass keeps each slice's tiles on consecutive
+    // tiles of a CTA except at n0 = 2048 (tiles of two columns, strided)
+    return p->path == 1 && p->n0 != 2048;
+}
+
 bool uses_tc2d(const mxfft_plan_s* p) {
     return p->path == 1 && p->fused2d && tc2d_supported(p->n0, p->n1, p->fmt, p->kblk) &&
            tc2d_resident_clusters(p->n0, p->n1, p->fmt) > 0;
@@ -526,6 +540,7 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
     const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
     if (p->path == 1) {
         Tc16Args t;
+        std::memset(&t, 0, sizeof(t));
         t.in = a.in;
         t.out = a.out;
         t.ref = a.ref;
@@ -547,6 +562,9 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
         t.stall = p->test_stall;
         t.g = p->kblk / 32;
         t.inv = dir;
+        t.st_out = a.st_out;
+        t.stats_out = a.stats_out;
+        t.kp = a.kp;
         ProfRec* r = prof_begin(p, 3, s);
         cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
         prof_end(r, s);

@@ -72,17 +72,29 @@ def assert_close_to_emulation(got, want, what=""):
     """Element-wise comparison of the tensor-core variant with its emulation.
     The hardware accumulates the 32 exact products of a DFT row in FP32 and
     the emulation in FP64, so a rare element can differ by one FP32 rounding,
-    which may move a later 8-bit rounding by one grid step of its block.  Each
-    element's error is bounded by the peak of its row and, separately, of its
-    column (an index error confined to one row or one column shows in the
-    other view): almost every element agrees to FP32 level and none by more
-    than a few grid steps, while an index error gives O(1) errors."""
+    which may move a later 8-bit rounding by one grid step of its block.  Such
+    a flip in the columns pass changes the outputs of that one column
+    transform (a flip in the rows pass: of one row, before the columns pass
+    spreads it thinly); it never changes many lines of both orientations.
+    Each element's error is measured against the peak of its row and,
+    separately, of its column: (1) none exceeds 10 % of its line's peak, (2)
+    the elements off by more than 1e-5 of a peak lie in at most max(2, 1 %)
+    of the rows or in at most that many columns.  An index error (a swapped
+    operand, a wrong twiddle or slot) gives errors of order one across many
+    rows and columns and fails both."""
     g = np.asarray(got).astype(np.complex128)
     w = np.asarray(want).astype(np.complex128)
     assert np.isfinite(g).all(), what
+    g = g.reshape((-1,) + g.shape[-2:])
+    w = w.reshape(g.shape)
+    err = np.abs(g - w)
+    off = np.zeros(g.shape, bool)
     for axis in (-1, -2):
-        err = np.abs(g - w)
         peak = np.abs(w).max(axis=axis, keepdims=True)
         rel = err / np.maximum(peak, 1e-300)
         assert rel.max() < 0.1, (what, axis, rel.max())
-        assert np.mean(rel > 1e-5) < 1e-3, (what, axis, np.mean(rel > 1e-5))
+        off |= rel > 1e-5
+    rows = int(off.any(axis=-1).sum())      # (slice, row) lines holding an off element
+    cols = int(off.any(axis=-2).sum())
+    limit = max(2, (g.shape[0] * min(g.shape[-2], g.shape[-1])) // 100)
+    assert min(rows, cols) <= limit, (what, "rows", rows, "cols", cols, "limit", limit)

@@ -102,7 +102,13 @@ typedef enum {
                                compute; the fused kernel keeps one CTA per SM and at 512x512
                                only 7 sixteen-CTA clusters fit at once).  When the device
                                cannot hold the cluster the passes run instead.  The fused
-                               round trip (mxfft_roundtrip_fused) always runs the passes. */
+                               round trip (mxfft_roundtrip_fused) always runs the passes. */,
+    MXFFT_OPT_FOLD_STATS = 7  /* tensor-core path only, 0 or 1; default 0.  1: the round
+                               trip's forward columns pass accumulates the inverse's Alg. 1
+                               statistics of the values it stores (n0 != 2048), so no
+                               statistics pass re-reads the forward output; same exponents
+                               and results.  Off by default: on this pass the per-value
+                               histogram work costs more time than the pass it removes. */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;
@@ -154,9 +160,9 @@ int mxfft_inverse(mxfft_plan_t plan, const void *in, void *out, int batch,
  * the forward output y = 2^-k A is formed, the inverse takes its own prescale
  * k_inv from y, and one scaling by 2^(-k_inv - log2(n0 n1)) ends it.
  * `out` also serves as the intermediate buffer.  On the tensor-core path
- * (MXFFT_OPT_PATH = 1, n0 != 2048) the forward columns pass accumulates
- * y's statistics as it stores y, so no separate statistics pass over y runs;
- * k_inv is the same exponent either way.
+ * with MXFFT_OPT_FOLD_STATS (n0 != 2048) the forward columns pass
+ * accumulates y's statistics as it stores y, so no separate statistics pass
+ * over y runs; k_inv is the same exponent either way.
  */
 int mxfft_roundtrip(mxfft_plan_t plan, const void *in, void *out, int batch,
                     void *stream);
@@ -265,8 +271,9 @@ int mxfft_prescale_exponents_noalloc(const void *in, int batch, int n0, int n1, 
  * launches (statistics, rows, columns, and for round trips statistics,
  * inverse rows, inverse columns); other plans (tensor-core, other k, the
  * generic pass) one launch per pass and (plan, direction) group, as parallel
- * branches; round trips on the tensor-core path take their inverse
- * statistics in the forward columns pass (no second statistics launch).
+ * branches (with MXFFT_ENGINE_FOLD_STATS, round trips on the tensor-core
+ * path take their inverse statistics in the forward columns pass: no second
+ * statistics launch for them).
  * Results are bit-identical to the per-plan calls.
  * ====================================================================== */
 typedef enum {
@@ -300,6 +307,8 @@ typedef struct mxfft_engine_s *mxfft_engine_t;
 #define MXFFT_ENGINE_GRAPHS 1  /* capture each batch signature into a CUDA graph, replay it */
 #define MXFFT_ENGINE_TC16 2    /* tensor-core radix-16 passes where a plan supports them */
 #define MXFFT_ENGINE_FUSED2D 4 /* with MXFFT_ENGINE_TC16: MXFFT_OPT_FUSED2D on the engine's plans */
+#define MXFFT_ENGINE_FOLD_STATS 16 /* with MXFFT_ENGINE_TC16: MXFFT_OPT_FOLD_STATS on the
+                                      engine's plans */
 #define MXFFT_ENGINE_NO_RAGGED 8 /* one launch per pass and plan group instead of the ragged
                                     launches (same results; for comparison) */
 

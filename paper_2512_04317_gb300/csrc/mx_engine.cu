@@ -207,6 +207,8 @@ int get_plan(mxfft_engine_s* e, const mxfft_item& it, mxfft_plan_s** out) {
         if (rc != MXFFT_OK && rc != MXFFT_ERR_UNSUPPORTED) { mxfft_destroy(p); return rc; }
         if (rc == MXFFT_OK && (e->flags & MXFFT_ENGINE_FUSED2D))
             rc = mxfft_set_option(p, MXFFT_OPT_FUSED2D, 1.0);
+        if (rc == MXFFT_OK && (e->flags & MXFFT_ENGINE_FOLD_STATS))
+            rc = mxfft_set_option(p, MXFFT_OPT_FOLD_STATS, 1.0);
         if (rc != MXFFT_OK && rc != MXFFT_ERR_UNSUPPORTED) { mxfft_destroy(p); return rc; }
     }
     e->plans[key] = p;
@@ -620,7 +622,7 @@ extern "C" {
 int mxfft_engine_create(float tau, float target, int flags, mxfft_engine_t* out) {
     if (!out) return MXFFT_ERR_INVALID;
     *out = nullptr;
-    if (!(tau > 0.0f && tau < 1.0f) || !(target > 0.0f) || (flags & ~15)) return MXFFT_ERR_INVALID;
+    if (!(tau > 0.0f && tau < 1.0f) || !(target > 0.0f) || (flags & ~31)) return MXFFT_ERR_INVALID;
     // validate tau / target the way a plan does
     mxfft_plan_t probe = nullptr;
     int rc = mxfft_plan(2, 2, MXFFT_E4M3, 2, tau, target, &probe);

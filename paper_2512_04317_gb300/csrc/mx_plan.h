@@ -37,6 +37,7 @@ struct mxfft_plan_s {
     float4* d_tw4A[2][2];      // [axis][dir] radix-16 stage twiddles as (re, re, -im, im)
     float4* d_tw4C[2][2];      // [axis][dir] twiddles before the radix-2 stage
     int fused2d;               // MXFFT_OPT_FUSED2D: fused 2D transform where it applies
+    int fold_stats;            // MXFFT_OPT_FOLD_STATS: round-trip inverse statistics in the columns pass
     int* d_err;                // device flag: a bounded wait gave up
     mxfft::SliceStats* d_st;          // 2 * st_cap records: forward, inverse
     int st_cap;

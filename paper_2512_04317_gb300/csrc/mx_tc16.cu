@@ -202,15 +202,13 @@ __device__ __forceinline__ float dft16_round(const float2 (&x)[16], float2 (&y)[
     return bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
 }
 
-// Twiddle w times the round output D sc: each product w D rounded, scaled
-// exactly by sc (a power of two), then added, so that a multiply-add
-// contraction of the sum can only absorb an exact product and the value is
-// the separately rounded (w.re y.re - w.im y.im, w.re y.im + w.im y.re) of y =
-// D sc whatever instructions the code generator picks.
+// Twiddle w times the round output y = D sc (sc a power of two, so y is
+// exact): (w.re y.re - w.im y.im, w.re y.im + w.im y.re), each product
+// rounded (the library is built without multiply-add contraction).
 __device__ __forceinline__ float2 cmul_sc(float2 w, float2 D, float sc) {
-    return make_float2(
-        __fsub_rn(__fmul_rn(__fmul_rn(w.x, D.x), sc), __fmul_rn(__fmul_rn(w.y, D.y), sc)),
-        __fadd_rn(__fmul_rn(__fmul_rn(w.x, D.y), sc), __fmul_rn(__fmul_rn(w.y, D.x), sc)));
+    const float2 y = make_float2(__fmul_rn(D.x, sc), __fmul_rn(D.y, sc));
+    return make_float2(__fsub_rn(__fmul_rn(w.x, y.x), __fmul_rn(w.y, y.y)),
+                       __fadd_rn(__fmul_rn(w.x, y.y), __fmul_rn(w.y, y.x)));
 }
 
 __device__ __forceinline__ float2 scale2(float2 v, float s) {

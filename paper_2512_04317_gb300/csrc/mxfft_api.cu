@@ -490,7 +490,7 @@ PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, fl
 bool tc16_folds_stats(const mxfft_plan_s* p) {
     // the tensor-core columns pass keeps each slice's tiles on consecutive
     // tiles of a CTA except at n0 = 2048 (tiles of two columns, strided)
-    return p->path == 1 && p->n0 != 2048;
+    return p->path == 1 && p->fold_stats && p->n0 != 2048;
 }
 
 bool uses_tc2d(const mxfft_plan_s* p) {
@@ -629,6 +629,7 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
     p->kmin = -126;
     p->kmax = 126;
     p->fused2d = 0;
+    p->fold_stats = 0;
     fmt_params(format, &p->fp);
     p->recs = new (std::nothrow) std::vector<ProfRec>();
     if (!p->recs) { delete p; return MXFFT_ERR_NOMEM; }
@@ -724,6 +725,10 @@ int mxfft_set_option(mxfft_plan_t p, int key, double value) {
         case MXFFT_OPT_FUSED2D:
             if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
             p->fused2d = value != 0.0;
+            return MXFFT_OK;
+        case MXFFT_OPT_FOLD_STATS:
+            if (value != 0.0 && value != 1.0) return MXFFT_ERR_INVALID;
+            p->fold_stats = value != 0.0;
             return MXFFT_OK;
         default:
             return MXFFT_ERR_INVALID;

@@ -22,10 +22,10 @@ MXFFT_ERR_NONFINITE = 5
 MXFFT_ERR_TIMEOUT = 6
 
 FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
-OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL, OPT_FUSED2D = range(7)
+OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL, OPT_FUSED2D, OPT_FOLD_STATS = range(8)
 
 OPS = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}
-ENGINE_GRAPHS, ENGINE_TC16, ENGINE_FUSED2D, ENGINE_NO_RAGGED = 1, 2, 4, 8
+ENGINE_GRAPHS, ENGINE_TC16, ENGINE_FUSED2D, ENGINE_NO_RAGGED, ENGINE_FOLD_STATS = 1, 2, 4, 8, 16
 
 # every symbol include/mxfft.h declares
 EXPORTS = ("mxfft_plan", "mxfft_set_option", "mxfft_forward", "mxfft_inverse",
@@ -399,7 +399,7 @@ class Plan:
     def __init__(self, n0: int, n1: int, fmt="e4m3", k: int = 32, tau: float = 1e-3,
                  target: float = 0.5, tau_min: float | None = None,
                  kmin: int | None = None, kmax: int | None = None, generic: bool = False,
-                 path: str = "radix2", fused2d: bool = False):
+                 path: str = "radix2", fused2d: bool = False, fold_stats: bool = False):
         self.n0, self.n1, self.fmt, self.k = int(n0), int(n1), fmt, int(k)
         self.handle = mxfft_plan(n0, n1, fmt, k, tau, target)
         self._last = (0, 0)   # (batch, op)
@@ -417,6 +417,8 @@ class Plan:
             mxfft_set_option(self.handle, OPT_PATH, 1)
             if fused2d:
                 mxfft_set_option(self.handle, OPT_FUSED2D, 1)
+            if fold_stats:
+                mxfft_set_option(self.handle, OPT_FOLD_STATS, 1)
         self.path = path
 
     def _run(self, name, x, out):
@@ -486,9 +488,11 @@ class Engine:
     current torch stream, with the same bits as the per-plan calls."""
 
     def __init__(self, tau: float = 1e-3, target: float = 0.5, graphs: bool = False,
-                 tc16: bool = False, fused2d: bool = False, ragged: bool = True):
+                 tc16: bool = False, fused2d: bool = False, ragged: bool = True,
+                 fold_stats: bool = False):
         flags = ((ENGINE_GRAPHS if graphs else 0) | (ENGINE_TC16 if tc16 else 0) |
-                 (ENGINE_FUSED2D if fused2d else 0) | (0 if ragged else ENGINE_NO_RAGGED))
+                 (ENGINE_FUSED2D if fused2d else 0) | (0 if ragged else ENGINE_NO_RAGGED) |
+                 (ENGINE_FOLD_STATS if fold_stats else 0))
         self.handle = mxfft_engine_create(tau, target, flags)
         self._slices = 0
 

@@ -17,7 +17,7 @@ def lib():
 
 def test_engine_and_server_argument_checks(lib):
     h = ctypes.c_void_p()
-    for tau, target, flags in [(0.0, 0.5, 0), (1.0, 0.5, 0), (1e-3, -1.0, 0), (1e-3, 0.5, 16)]:
+    for tau, target, flags in [(0.0, 0.5, 0), (1.0, 0.5, 0), (1e-3, -1.0, 0), (1e-3, 0.5, 32)]:
         assert lib.mxfft_engine_create(tau, target, flags, ctypes.byref(h)) == mxfft.MXFFT_ERR_INVALID
     assert lib.mxfft_engine_create(1e-3, 0.3, 0, ctypes.byref(h)) == mxfft.MXFFT_ERR_UNSUPPORTED
     assert lib.mxfft_engine_create(1e-3, 0.5, 0, None) == mxfft.MXFFT_ERR_INVALID

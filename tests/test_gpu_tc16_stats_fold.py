@@ -1,7 +1,7 @@
-"""The round trip on the tensor-core path takes the inverse transform's Alg. 1
-statistics inside the forward columns pass (every stored value goes through
-the same accumulator as the statistics kernel; each CTA flushes one segment
-per run of tiles of a slice).  The inverse exponent it selects must equal the
+"""With MXFFT_OPT_FOLD_STATS the round trip on the tensor-core path takes the
+inverse transform's Alg. 1 statistics inside the forward columns pass (every
+stored value goes through the same accumulator as the statistics kernel; each
+CTA flushes one segment per run of tiles of a slice).  The inverse exponent it selects must equal the
 one the stand-alone statistics kernel selects on the same forward output, for
 every slice, whatever the slices' scales and however the tiles of a slice are
 split between CTAs; the round trip itself stays equal to the emulation and,
@@ -65,7 +65,7 @@ def test_folded_inverse_exponents_equal_statistics_kernel(n0, n1, batch, fmt, cu
 
     from paper_2512_04317_gb300 import mxfft
     x = torch.from_numpy(scaled_slices(batch, n0, n1, seed=n0 + n1 + batch)).cuda()
-    with mxfft.Plan(n0, n1, fmt, 32, path="tc16") as p:
+    with mxfft.Plan(n0, n1, fmt, 32, path="tc16", fold_stats=True) as p:
         y = p.forward(x)
         torch.cuda.synchronize()
         _, flags_f, k_f = p.status()
@@ -85,9 +85,13 @@ def test_folded_round_trip_matches_emulation(n0, n1, batch, cuda_device):
 
     from paper_2512_04317_gb300 import mxfft
     x = scaled_slices(batch, n0, n1, seed=7 * batch)
-    with mxfft.Plan(n0, n1, "e4m3", 32, path="tc16") as p:
-        got = p.roundtrip(torch.from_numpy(x).cuda()).cpu().numpy()
+    xt = torch.from_numpy(x).cuda()
+    with mxfft.Plan(n0, n1, "e4m3", 32, path="tc16", fold_stats=True) as p:
+        got = p.roundtrip(xt).cpu().numpy()
         assert p.status()[1] == 0
+    with mxfft.Plan(n0, n1, "e4m3", 32, path="tc16") as p:
+        unfolded = p.roundtrip(xt).cpu().numpy()
+    np.testing.assert_array_equal(got.view(np.uint32), unfolded.view(np.uint32))
     want = tc16_ref.mxfft2d(x, "e4m3", "roundtrip")
     assert_close_to_emulation(got, want, (n0, n1, batch))
 
@@ -108,18 +112,19 @@ def test_engine_folds_only_round_trip_slices(cuda_device):
         kb = p.status()[2]
         wc = p.roundtrip(xc).cpu().numpy()
         kc = p.status()[2]
-    with mxfft.Engine(tc16=True, graphs=True) as eng:
-        ya, yb, yc = torch.empty_like(xa), torch.empty_like(xb), torch.empty_like(xc)
-        eng.run([("forward", xa, ya, "e4m3", 32), ("roundtrip", xb, yb, "e4m3", 32),
-                 ("roundtrip", xc, yc, "e4m3", 32)])
-        torch.cuda.synchronize()
-        flags, k = eng.status()
-        launches = eng.launches_per_run()
-    assert flags == 0
-    for got, want in ((ya, wa), (yb, wb), (yc, wc)):
-        np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), want.view(np.uint32))
-    assert [kk[1] for kk in k[5:11]] == [kk[1] for kk in kb]
-    assert [kk[1] for kk in k[11:]] == [kk[1] for kk in kc]
-    # statistics, rows, columns (with the inverse statistics), inverse rows,
-    # inverse columns: no second statistics launch
-    assert launches == 5
+    for fold in (True, False):
+        with mxfft.Engine(tc16=True, graphs=True, fold_stats=fold) as eng:
+            ya, yb, yc = torch.empty_like(xa), torch.empty_like(xb), torch.empty_like(xc)
+            eng.run([("forward", xa, ya, "e4m3", 32), ("roundtrip", xb, yb, "e4m3", 32),
+                     ("roundtrip", xc, yc, "e4m3", 32)])
+            torch.cuda.synchronize()
+            flags, k = eng.status()
+            launches = eng.launches_per_run()
+        assert flags == 0
+        for got, want in ((ya, wa), (yb, wb), (yc, wc)):
+            np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), want.view(np.uint32))
+        assert [kk[1] for kk in k[5:11]] == [kk[1] for kk in kb]
+        assert [kk[1] for kk in k[11:]] == [kk[1] for kk in kc]
+        # statistics, rows, columns, (statistics of the forward outputs,)
+        # inverse rows, inverse columns
+        assert launches == (5 if fold else 6)

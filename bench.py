@@ -776,37 +776,53 @@ def main():
     e2e_mode = "one stream, steps in sequence"
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if engine is not None:
-        # the way a caller streams batches through the executor: steps round-robin
-        # over 3 streams, each with its own device buffers and engine, so one
-        # step's copy in, another's transforms and a third's copy out overlap;
-        # every step still copies its inputs in and its results out
-        e2e_mode = "3 streams, one step in flight per stream"
+        # the way a caller streams batches through the executor: one stream
+        # copies inputs in, one copies results out, and steps rotate over 3
+        # device buffer sets, each with its own compute stream and engine, so
+        # the two copy directions run back to back and at the same time while
+        # the transforms overlap them; every step still copies its inputs in
+        # and its results out.  Events order a buffer set's reuse.
+        e2e_mode = "copy-in stream, copy-out stream, 3 buffer sets with a compute stream each"
+        h2d_s, d2h_s = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         lanes = []
         for j in range(3):
             b = {"xk": torch.empty_like(xk), "xi": torch.empty_like(xi), "yk": torch.empty_like(yk),
                  "yi": torch.empty_like(yi), "ok": torch.empty_like(hk).pin_memory(),
-                 "oi": torch.empty_like(hi).pin_memory()}
+                 "oi": torch.empty_like(hi).pin_memory(),
+                 "in_done": torch.cuda.Event(), "run_done": torch.cuda.Event(),
+                 "out_done": torch.cuda.Event()}
             lanes.append((torch.cuda.Stream(dev), mxfft.Engine(graphs=True, tc16=path == "tc16"), b))
 
         def e2e_step(i):
             st_, eng_j, b = lanes[i % len(lanes)]
-            with torch.cuda.stream(st_):
+            if i >= len(lanes):
+                h2d_s.wait_event(b["run_done"])      # the set's inputs were consumed
+            with torch.cuda.stream(h2d_s):
                 b["xk"].copy_(hk, non_blocking=True)
                 b["xi"].copy_(hi, non_blocking=True)
+            b["in_done"].record(h2d_s)
+            st_.wait_event(b["in_done"])
+            if i >= len(lanes):
+                st_.wait_event(b["out_done"])        # the set's outputs were copied out
+            with torch.cuda.stream(st_):
                 eng_j.run([("forward", b["xk"], b["yk"], w["fmt"], w["k"]),
                            ("roundtrip", b["xi"], b["yi"], w["fmt"], w["k"])])
+            b["run_done"].record(st_)
+            d2h_s.wait_event(b["run_done"])
+            with torch.cuda.stream(d2h_s):
                 b["ok"].copy_(b["yk"], non_blocking=True)
                 b["oi"].copy_(b["yi"], non_blocking=True)
+            b["out_done"].record(d2h_s)
         for i in range(2 * len(lanes)):
             e2e_step(i)
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
-        for st_, _, _ in lanes:
+        for st_ in [h2d_s, d2h_s] + [ln[0] for ln in lanes]:
             st_.wait_event(e0)
         for i in range(e2e_steps):
-            e2e_step(i)
-        for st_, _, _ in lanes:
+            e2e_step(i + 2 * len(lanes))
+        for st_ in [h2d_s, d2h_s] + [ln[0] for ln in lanes]:
             ev = torch.cuda.Event()
             ev.record(st_)
             stream.wait_event(ev)

@@ -117,9 +117,8 @@ struct Mma {
 
 // One MMA round: every thread MX-encodes its 16-element vector into its row
 // of the A operand (thread i: operand half i / 128, row i % 128), one thread
-// issues both products, all read back their row.  Leaves the 16 complex
-// DFT outputs in y without their scale and returns that scale (a power of
-// two; NaN for a non-finite block).  Ends with a CTA barrier, after which the
+// issues both products, all read back their row.  Returns the 16 complex
+// DFT outputs (scales applied) in y.  Ends with a CTA barrier, after which the
 // A operand, the accumulators and the caller's shared-memory writes made
 // before the call may be reused / are visible.
 // Vector v of a round belongs to transform t and has index q in the round's
@@ -135,7 +134,7 @@ __device__ __forceinline__ int block_member(int v, int g, int lgt, int i) {
 }
 
 template <int FMT, int DIM>
-__device__ __forceinline__ float dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
+__device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
                                             uint32_t idesc, int emax, bool issue, int g,
                                             int lgt, uint32_t* sAm) {
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -195,18 +194,16 @@ __device__ __forceinline__ float dft16_round(const float2 (&x)[16], float2 (&y)[
         mm.ok = false;
     }
     // D is exact-scaled by the vector's scale and the matrix rows' scale, which
-    // is 2^-emax for every row (each row holds an entry of magnitude 1); y
-    // receives D unscaled and the caller applies sc
+    // is 2^-emax for every row (each row holds an entry of magnitude 1)
+    const float sc = bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
+    const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
-    for (int k = 0; k < 16; k++) y[k] = make_float2(d[2 * k], d[2 * k + 1]);
-    return bad ? __int_as_float(0x7fffffff) : exp2i(sv - emax);
+    for (int k = 0; k < 16; k++) y[k] = mul2_rn(make_float2(d[2 * k], d[2 * k + 1]), sc2);
 }
 
-// Twiddle w times the round output y = D sc (sc a power of two, so y is
-// exact): (w.re y.re - w.im y.im, w.re y.im + w.im y.re), each product
-// rounded (the library is built without multiply-add contraction).
-__device__ __forceinline__ float2 cmul_sc(float2 w, float2 D, float sc) {
-    const float2 y = make_float2(__fmul_rn(D.x, sc), __fmul_rn(D.y, sc));
+// (w.re y.re - w.im y.im, w.re y.im + w.im y.re), each product rounded (the
+// library is built without multiply-add contraction)
+__device__ __forceinline__ float2 cmul(float2 w, float2 y) {
     return make_float2(__fsub_rn(__fmul_rn(w.x, y.x), __fmul_rn(w.y, y.y)),
                        __fadd_rn(__fmul_rn(w.x, y.y), __fmul_rn(w.y, y.x)));
 }
@@ -267,7 +264,10 @@ __device__ __forceinline__ void load_tile(const Args& a, const float2* in, int t
     }
 }
 
-template <int FMT, int DIM, int LOGN>
+// FOLD (columns pass, n <= 1024): also accumulate the output's statistics
+// (MXFFT_OPT_FOLD_STATS); a separate instance, so that the other passes carry
+// none of its code.
+template <int FMT, int DIM, int LOGN, bool FOLD>
 __global__ void __launch_bounds__(kThreads, 2)
 tc16_pass_kernel(const Args a) {
     using G = Geo<LOGN>;
@@ -325,14 +325,15 @@ tc16_pass_kernel(const Args a) {
     // count when the slice changes and at the end (the flush that completes
     // the slice's tiles selects k).  Not for the strided n = 2048 columns
     // pass, whose tiles of a slice are spread over all CTAs.
-    __shared__ uint32_t so_hist[kHistBins];
+    constexpr bool fold = FOLD && DIM == 0 && !kStrided;
+    __shared__ uint32_t so_hist[fold ? kHistBins : 1];
     __shared__ uint32_t so_misc[4];
-    const bool fold = DIM == 0 && !kStrided && a.stats_out != 0;
     StatAcc oacc;
     int seg_slice = -1, seg_tiles = 0;
     SliceStats* seg_st = nullptr;
     if (fold)
         for (int b = tid; b < kHistBins; b += kThreads) so_hist[b] = 0;
+    (void)seg_slice; (void)seg_tiles; (void)so_misc;
     auto flush_out = [&]() {
         if (seg_st) {
             __syncthreads();
@@ -410,13 +411,13 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
             }
-            const float sc = dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
                 const float4 w = tw[k >> 1];
-                d[slot<LOGN, DIM>(t, M * k + j2)] = cmul_sc(make_float2(w.x, w.y), y[k], sc);
-                d[slot<LOGN, DIM>(t, M * (k + 1) + j2)] = cmul_sc(make_float2(w.z, w.w), y[k + 1], sc);
+                d[slot<LOGN, DIM>(t, M * k + j2)] = cmul(make_float2(w.x, w.y), y[k]);
+                d[slot<LOGN, DIM>(t, M * (k + 1) + j2)] = cmul(make_float2(w.z, w.w), y[k + 1]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
@@ -449,13 +450,12 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
             }
-            const float sc = dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             if (r == 1) {
                 // X[k1 + 16 k2]
 #pragma unroll
                 for (int k = 0; k < 16; k++) {
-                    const float2 yk = scale2(y[k], sc);
-                    const float2 val = scale_out ? scale2(yk, post) : yk;
+                    const float2 val = scale_out ? scale2(y[k], post) : y[k];
                     if (fold_tile) oacc.add<true>(val.x, val.y, so_hist);
                     const int e = k1 + 16 * k;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + e, slice_pts)] = val;
@@ -466,9 +466,8 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int k = 0; k < 16; k += 2) {
                     const float4 w = tw[k >> 1];
-                    d[slot<LOGN, DIM>(t, M * k1 + r * k + j22)] = cmul_sc(make_float2(w.x, w.y), y[k], sc);
-                    d[slot<LOGN, DIM>(t, M * k1 + r * (k + 1) + j22)] =
-                        cmul_sc(make_float2(w.z, w.w), y[k + 1], sc);
+                    d[slot<LOGN, DIM>(t, M * k1 + r * k + j22)] = cmul(make_float2(w.x, w.y), y[k]);
+                    d[slot<LOGN, DIM>(t, M * k1 + r * (k + 1) + j22)] = cmul(make_float2(w.z, w.w), y[k + 1]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -663,11 +662,11 @@ tc16_pass_kernel(const Args a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(mm.tbase), "r"(kTmemCols));
 }
 
-template <int FMT, int DIM, int LOGN>
-cudaError_t launch_one(const Args& a, cudaStream_t s) {
+template <int FMT, int DIM, int LOGN, bool FOLD>
+cudaError_t launch_inst(const Args& a, cudaStream_t s) {
     using G = Geo<LOGN>;
     const size_t smem = kOffBuf + 2 * (size_t)G::BUF_SLOTS * sizeof(float2);
-    void (*k)(const Args) = tc16_pass_kernel<FMT, DIM, LOGN>;
+    void (*k)(const Args) = tc16_pass_kernel<FMT, DIM, LOGN, FOLD>;
     // per kernel instance: shared-memory opt-in and resident CTAs per SM
     static int resident = 0;
     if (resident == 0) {
@@ -692,6 +691,12 @@ cudaError_t launch_one(const Args& a, cudaStream_t s) {
     k<<<blocks, kThreads, smem, s>>>(a);
     note_launch();
     return cudaGetLastError();
+}
+
+template <int FMT, int DIM, int LOGN>
+cudaError_t launch_one(const Args& a, cudaStream_t s) {
+    if (DIM == 0 && LOGN <= 10 && a.stats_out) return launch_inst<FMT, 0, (LOGN <= 10 ? LOGN : 10), true>(a, s);
+    return launch_inst<FMT, DIM, LOGN, false>(a, s);
 }
 
 template <int FMT>

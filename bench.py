@@ -443,7 +443,7 @@ def serving_leg(n_req, torch, slots=8, batch_slices=64, batch_mb=64, fp32=True,
                      else "the complex coil images",
            "server": f"{slots} slots, batches of at most {batch_slices} slices and "
                      f"{batch_mb} MiB, memory budget 80% of free",
-           "path": "tensor-core plans where a request's shape allows them (256-1024), radix-2 "
+           "path": "tensor-core plans where a request's shape allows them (128-1024), radix-2 "
                    "otherwise" if tc16 else "radix-2"}
     # no garbage-collector pauses in the submitting loop while it keeps time
     gc.collect()

@@ -116,9 +116,10 @@ struct Tc16Args {
     const float2* in;
     float2* out;
     const SliceRef* ref;              // as in PassArgs
-    int n0, n1, dim, n, r;            // n = 256 r, r in {1, 2, 4, 8}
+    int n0, n1, dim, n, r;            // n = 256 r, r in {1, 2, 4, 8}, or n = 128 (r = 0)
     int batch;                        // slices (set by launch_tc16_pass)
     const uint8_t* bmat;              // B operand: 32 x 32 element codes, core-matrix layout (1 KB)
+    const uint8_t* bmat2;             // n = 128: the 8-point DFT twice on the diagonal (same layout)
     const float2* twA;                // [j2 < 16 r][k1 < 16] twiddle element values x 2^s
     const float2* twC;                // [j22 < r][k21 < 16] (r > 1)
     SliceStats* st;

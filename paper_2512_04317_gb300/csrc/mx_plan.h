@@ -32,6 +32,7 @@ struct mxfft_plan_s {
     int path;                  // 0 radix-2 MX, 1 tensor-core radix-16
     int test_stall;            // MXFFT_OPT_TEST_STALL
     uint8_t* d_bmat[2];        // [dir] tensor-core DFT matrix codes (core-matrix layout)
+    uint8_t* d_bmat8[2];       // [dir] the same for two 8-point DFTs (n = 128 axes)
     float2* d_twA[2][2];       // [axis][dir] radix-16 stage twiddles
     float2* d_twC[2][2];       // [axis][dir] twiddles before the radix-2 stage (n = 512)
     float4* d_tw4A[2][2];      // [axis][dir] radix-16 stage twiddles as (re, re, -im, im)

@@ -64,19 +64,25 @@ static_assert(kOffBuf % 16 == 0, "16-byte aligned cp.async destinations");
 
 using Args = Tc16Args;
 
-// Geometry of one transform length n = 2^LOGN.
+// Geometry of one transform length n = 2^LOGN.  n = 128 (R8): round A as
+// for the other lengths with M = 8, then one round of 8-point DFTs (see the
+// kernel), no C2.
 template <int LOGN>
 struct Geo {
     static constexpr int n = 1 << LOGN;
-    static constexpr int r = n / 256;               // 1, 2, 4, 8
+    static constexpr bool R8 = n == 128;
+    static constexpr int r = n / 256;               // 1, 2, 4, 8 (0 for n = 128)
     static constexpr int LGR = r == 1 ? 0 : (r == 2 ? 1 : (r == 4 ? 2 : 3));
-    static constexpr int M = 16 * r;
-    static constexpr int LGM = 4 + LGR;
-    static constexpr int T = kTilePts / n;          // transforms per tile (16, 8, 4, 2)
-    static constexpr int LGT = T == 16 ? 4 : (T == 8 ? 3 : (T == 4 ? 2 : 1));
-    // rows pass: [t][e], PADR pad slots after every M elements
+    static constexpr int M = R8 ? 8 : 16 * r;       // n / 16
+    static constexpr int LGM = R8 ? 3 : 4 + LGR;
+    static constexpr int T = kTilePts / n;          // transforms per tile (32, 16, 8, 4, 2)
+    static constexpr int LGT = T == 32 ? 5 : (T == 16 ? 4 : (T == 8 ? 3 : (T == 4 ? 2 : 1)));
+    // rows pass: [t][e], PADR pad slots after every 2^LGP elements (M; 16
+    // for n = 128, whose rows also get 8 more slots so that the 4 transforms
+    // a warp spans fall on alternate halves of the banks)
     static constexpr int PADR = r == 8 ? 8 : (r == 4 ? 4 : 2);
-    static constexpr int TS = n + PADR * (n / M);
+    static constexpr int LGP = R8 ? 4 : LGM;
+    static constexpr int TS = n + PADR * (n >> LGP) + (R8 ? 8 : 0);
     static constexpr int ROW_SLOTS = T * TS;
     // columns pass: [e][t]; with T < 16, T pad slots after every 16 elements
     static constexpr int COL_SLOTS = n * T + (T < 16 ? T * (n / 16) : 0);
@@ -89,14 +95,17 @@ struct Geo {
 // of M elements as 16-byte pairs (r = 1: chunks 9 k1 + c, distinct mod 8 over
 // a quarter-warp) or 8-byte elements (r = 2: slots 34 k1 + 2 j + j22; r = 4:
 // 68 k1 + 4 j + j22; r = 8: 136 k1 + 8 j + j22; distinct mod 16 over a
-// half-warp).  Columns pass: a half-warp spans 16 transforms (T = 16) or T
-// transforms x 16 / T elements whose pads put them in distinct bank groups
-// (T = 8, 4, 2).  Every pattern was
-// checked for bank conflicts by enumerating its addresses.
+// half-warp); n = 128: round A's half-warp spans 8 elements of two
+// transforms 152 slots apart, and the 8-point round reads 16 elements per
+// thread as 16-byte pairs (chunks 9 p + c, distinct mod 8 over a
+// quarter-warp).  Columns pass: a half-warp spans 16 transforms (T = 16, 32)
+// or T transforms x 16 / T elements whose pads put them in distinct bank
+// groups (T = 8, 4, 2).  Every pattern was checked for bank conflicts by
+// enumerating its addresses.
 template <int LOGN>
 __device__ __forceinline__ int slot_row(int t, int e) {
     using G = Geo<LOGN>;
-    return (int)MX_BND(t * G::TS + e + G::PADR * (e >> G::LGM), G::BUF_SLOTS);
+    return (int)MX_BND(t * G::TS + e + G::PADR * (e >> G::LGP), G::BUF_SLOTS);
 }
 template <int LOGN>
 __device__ __forceinline__ int slot_col(int t, int e) {
@@ -111,7 +120,7 @@ __device__ __forceinline__ int slot(int t, int e) {
 // Shared state of one CTA's MMA rounds.
 struct Mma {
     uint8_t* sA;
-    uint32_t sa, sb, mbar, tbase, phase;
+    uint32_t sa, sb, sb8, mbar, tbase, phase;   // sb8: the 8-point pair matrix (n = 128)
     bool ok;
 };
 
@@ -133,10 +142,13 @@ __device__ __forceinline__ int block_member(int v, int g, int lgt, int i) {
     return ((q + i) << lgt) | t;
 }
 
+// sb: the B operand (the 16-point DFT matrix, or for n = 128's second round
+// two 8-point DFTs on the diagonal, so that the row's two halves transform
+// two 8-point vectors).
 template <int FMT, int DIM>
 __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
-                                            uint32_t idesc, int emax, bool issue, int g,
-                                            int lgt, uint32_t* sAm) {
+                                            uint32_t sb, uint32_t idesc, int emax, bool issue,
+                                            int g, int lgt, uint32_t* sAm) {
     const int tid = threadIdx.x, warp = tid >> 5;
     float A = vec_max_abs(x);
     if (g > 1) {
@@ -167,7 +179,7 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0 && issue) {
-        const uint64_t bd = smem_desc(mm.sb, 128, 256);
+        const uint64_t bd = smem_desc(sb, 128, 256);
         const uint64_t a0 = smem_desc(mm.sa, 128, 256);
         const uint64_t a1 = smem_desc(mm.sa + 4096, 128, 256);
         asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
@@ -297,6 +309,9 @@ tc16_pass_kernel(const Args a) {
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (tid < 64) reinterpret_cast<uint4*>(sB)[tid] = __ldg(reinterpret_cast<const uint4*>(a.bmat) + tid);
+    // n = 128 has no C2 twiddles: its 8-point pair matrix takes their place
+    if (G::R8 && tid < 64)
+        reinterpret_cast<uint4*>(sTwC)[tid] = __ldg(reinterpret_cast<const uint4*>(a.bmat2) + tid);
     for (int i = tid; i < M * 16; i += kThreads) sTwA[(i >> 4) * kTwRow + (i & 15)] = __ldg(a.twA + i);
     if (r > 1 && tid < r * 16) sTwC[(tid >> 4) * kTwRow + (tid & 15)] = __ldg(a.twC + tid);
     // CTA b takes the contiguous tiles [tile_begin, tile_end), shares equal to
@@ -359,6 +374,7 @@ tc16_pass_kernel(const Args a) {
     mm.sA = smem;
     mm.sa = smem_u32(smem);
     mm.sb = smem_u32(sB);
+    mm.sb8 = smem_u32(sTwC);
     mm.mbar = smem_u32(&mbar);
     mm.tbase = tmem_base;
     mm.phase = 0;
@@ -411,7 +427,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM>(x, y, mm, mm.sb, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
@@ -427,6 +443,52 @@ tc16_pass_kernel(const Args a) {
         if (a.epilogue == EPI_UNSCALE) post = exp2i(-kslice);
         else if (a.epilogue == EPI_RT_FINAL) post = exp2i(-kslice - a.lg_total);
         const bool scale_out = a.epilogue != EPI_RAW;
+
+        if (G::R8) {
+            // ---- n = 128, round B: 8-point DFTs over j2 of Y[k1][j2] for the
+            // pair k1 = 2 p, 2 p + 1 (elements 16 p .. 16 p + 15 of the round-A
+            // layout): one MMA row, both vectors one MX block, the B operand
+            // two 8-point DFTs on the diagonal; X[k1 + 16 k2] ------------------
+            const int v = tid;
+            int t, p;
+            if (DIM == 1) { t = v >> 3; p = v & 7; }
+            else { t = v & (T - 1); p = v >> G::LGT; }
+            float2 x[16], y[16];
+            if (DIM == 1) {
+                const float4* g = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, 16 * p));
+#pragma unroll
+                for (int c = 0; c < 8; c++) {
+                    const float4 q = g[c];
+                    x[2 * c] = make_float2(q.x, q.y);
+                    x[2 * c + 1] = make_float2(q.z, q.w);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; j++) x[j] = d[slot_col<LOGN>(t, 16 * p + j)];
+            }
+            dft16_round<FMT, DIM>(x, y, mm, mm.sb8, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+#pragma unroll
+            for (int k2 = 0; k2 < 8; k2++) {
+                const float2 v0 = scale_out ? scale2(y[k2], post) : y[k2];        // X[2 p + 16 k2]
+                const float2 v1 = scale_out ? scale2(y[8 + k2], post) : y[8 + k2];  // X[2 p + 1 + 16 k2]
+                if (fold_tile) {
+                    oacc.add<true>(v0.x, v0.y, so_hist);
+                    oacc.add<true>(v1.x, v1.y, so_hist);
+                }
+                const int e = 2 * p + 16 * k2;
+                if (DIM == 1) {
+                    *reinterpret_cast<float4*>(out + MX_BND((size_t)(t0 + t) * a.n1 + e, slice_pts - 1)) =
+                        make_float4(v0.x, v0.y, v1.x, v1.y);
+                } else {
+                    out[MX_BND((size_t)e * a.n1 + t0 + t, slice_pts)] = v0;
+                    out[MX_BND((size_t)(e + 1) * a.n1 + t0 + t, slice_pts)] = v1;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            // the tile is done and its buffer free for the next prefetch
+            if (__syncthreads_or(!mm.ok)) break;
+            continue;
+        }
 
         // ---- round C1: vector (t, k1, j22), elements Y[M k1 + r j21 + j22] -
         {
@@ -450,7 +512,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM>(x, y, mm, mm.sb, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             if (r == 1) {
                 // X[k1 + 16 k2]
 #pragma unroll
@@ -701,6 +763,7 @@ cudaError_t launch_one(const Args& a, cudaStream_t s) {
 
 template <int FMT>
 cudaError_t launch_fmt(const Args& a, cudaStream_t s) {
+    if (a.n == 128) return a.dim == 1 ? launch_one<FMT, 1, 7>(a, s) : launch_one<FMT, 0, 7>(a, s);
     if (a.n == 256) return a.dim == 1 ? launch_one<FMT, 1, 8>(a, s) : launch_one<FMT, 0, 8>(a, s);
     if (a.n == 512) return a.dim == 1 ? launch_one<FMT, 1, 9>(a, s) : launch_one<FMT, 0, 9>(a, s);
     if (a.n == 1024) return a.dim == 1 ? launch_one<FMT, 1, 10>(a, s) : launch_one<FMT, 0, 10>(a, s);
@@ -710,8 +773,9 @@ cudaError_t launch_fmt(const Args& a, cudaStream_t s) {
 }  // namespace tc16
 
 bool tc16_supported(int n, int other, int fmt) {
-    // n = 256 r (r = 1, 2, 4, 8), 8-bit element formats, whole tiles of 4096 / n transforms
-    if (n != 256 && n != 512 && n != 1024 && n != 2048) return false;
+    // n = 128 or 256 r (r = 1, 2, 4, 8), 8-bit element formats, whole tiles of
+    // 4096 / n transforms
+    if (n != 128 && n != 256 && n != 512 && n != 1024 && n != 2048) return false;
     const int T = tc16::kTilePts / n;
     return other >= T && other % T == 0 && (fmt == 0 || fmt == 1);
 }

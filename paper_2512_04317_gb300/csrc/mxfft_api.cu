@@ -179,6 +179,7 @@ void twiddle_block16(long m, long N, int sgn, const FmtHost& f, float2* out) {
 void free_plan_device(mxfft_plan_s* p) {
     for (int d = 0; d < 2; d++) {
         if (p->d_bmat[d]) cudaFree(p->d_bmat[d]);
+        if (p->d_bmat8[d]) cudaFree(p->d_bmat8[d]);
         for (int a = 0; a < 2; a++) {
             if (p->d_twA[a][d]) cudaFree(p->d_twA[a][d]);
             if (p->d_twC[a][d]) cudaFree(p->d_twC[a][d]);
@@ -214,21 +215,25 @@ int ensure_stats(mxfft_plan_s* p, int batch) {
     return MXFFT_OK;
 }
 
-// Real 32 x 32 matrix of the 16-point DFT (sign sgn) for interleaved re/im
+// Real 32 x 32 matrix of the P-point DFT (sign sgn) for interleaved re/im
 // vectors, each output row an MX block: element codes in the K-major
-// core-matrix layout of the tensor-core B operand, and the row scales.
-void build_dft16_matrix(int sgn, int fmt, const FmtHost& f, std::vector<uint8_t>& codes,
-                        std::vector<float>& scales) {
+// core-matrix layout of the tensor-core B operand, and the row scales.  P =
+// 16: one 16-point DFT; P = 8: the 8-point DFT twice on the diagonal (rows
+// and columns 16 b .. 16 b + 15 for the b-th of two 8-point vectors).
+void build_dft_matrix(int P, int sgn, int fmt, const FmtHost& f, std::vector<uint8_t>& codes,
+                      std::vector<float>& scales) {
     codes.assign(1024, 0);
     scales.assign(32, 0.f);
     for (int m = 0; m < 16; m++) {
-        double row[2][32];
-        for (int j = 0; j < 16; j++) {
+        double row[2][32] = {};
+        const int b = m / P, mm = m % P;            // diagonal block, output index in it
+        for (int j = 0; j < P; j++) {
             double c, s;
-            unit_root_full((long)(j * m) % 16, 16, &c, &s);
+            unit_root_full((long)(j * mm) % P, P, &c, &s);
             s *= sgn;                                  // W = c + i s
-            row[0][2 * j] = c;  row[0][2 * j + 1] = -s;    // Re y: a c - b s
-            row[1][2 * j] = s;  row[1][2 * j + 1] = c;     // Im y: a s + b c
+            const int col = 2 * (b * P + j);
+            row[0][col] = c;  row[0][col + 1] = -s;    // Re y: a c - b s
+            row[1][col] = s;  row[1][col + 1] = c;     // Im y: a s + b c
         }
         for (int part = 0; part < 2; part++) {
             const int nrow = 2 * m + part;
@@ -265,20 +270,25 @@ int build_tc16_tables(mxfft_plan_s* p) {
     for (int d = 0; d < 2 && rc == MXFFT_OK; d++) {
         if (p->d_bmat[d]) continue;
         const int sgn = d == 0 ? -1 : 1;
-        std::vector<uint8_t> codes;
-        std::vector<float> scales;
-        build_dft16_matrix(sgn, p->fmt, f, codes, scales);
+        std::vector<uint8_t> codes, codes8;
+        std::vector<float> scales, scales8;
+        build_dft_matrix(16, sgn, p->fmt, f, codes, scales);
+        build_dft_matrix(8, sgn, p->fmt, f, codes8, scales8);
         // the kernel folds the row scales into one constant: every row of the
         // matrix holds an entry of magnitude 1, so each row scale is 2^-emax
         for (float sc : scales)
             if (sc != (float)std::ldexp(1.0, -f.emax)) return MXFFT_ERR_UNSUPPORTED;
+        for (float sc : scales8)
+            if (sc != (float)std::ldexp(1.0, -f.emax)) return MXFFT_ERR_UNSUPPORTED;
         rc = upload(&p->d_bmat[d], codes);
+        // n = 128 axes: the second round's pairs of 8-point DFTs
+        if (rc == MXFFT_OK && (p->n0 == 128 || p->n1 == 128)) rc = upload(&p->d_bmat8[d], codes8);
         for (int axis = 0; axis < 2 && rc == MXFFT_OK; axis++) {
             const int n = axis == 0 ? p->n0 : p->n1;
-            const int r = n / 256, M = 16 * r;
+            const int r = std::max(n / 256, 1), M = n / 16;
             std::vector<float2> twa((size_t)M * 16), twc((size_t)std::max(r, 1) * 16);
             for (int j2 = 0; j2 < M; j2++) twiddle_block16(j2, n, sgn, f, &twa[(size_t)j2 * 16]);
-            for (int j22 = 0; j22 < r; j22++) twiddle_block16(j22, M, sgn, f, &twc[(size_t)j22 * 16]);
+            for (int j22 = 0; n >= 512 && j22 < r; j22++) twiddle_block16(j22, M, sgn, f, &twc[(size_t)j22 * 16]);
             rc = upload(&p->d_twA[axis][d], twa);
             if (rc == MXFFT_OK) rc = upload(&p->d_twC[axis][d], twc);
             // the same twiddles as (re, re, -im, im) for packed multiplies
@@ -550,6 +560,7 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
         t.n = a.n;
         t.r = a.n / 256;
         t.bmat = p->d_bmat[dir];
+        t.bmat2 = p->d_bmat8[dir];
         t.twA = p->d_twA[a.dim][dir];
         t.twC = p->d_twC[a.dim][dir];
         t.st = a.st;

@@ -85,8 +85,8 @@ def tc16_supported(n0: int, n1: int, fmt, k: int) -> bool:
     """Whether a plan of this shape, format and k can take the tensor-core
     variant (MXFFT_OPT_PATH = 1)."""
     f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
-    return (n0 in (256, 512, 1024, 2048) and n1 in (256, 512, 1024, 2048) and f in (0, 1)
-            and k in (32, 64, 128))
+    sizes = (128, 256, 512, 1024, 2048)
+    return n0 in sizes and n1 in sizes and f in (0, 1) and k in (32, 64, 128)
 
 
 class MxfftError(RuntimeError):

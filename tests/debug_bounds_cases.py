@@ -26,6 +26,9 @@ CASES = [
     (256, 512, 2, "e4m3", 32, "roundtrip", {"path": "tc16"}),
     (1024, 256, 1, "e5m2", 64, "forward", {"path": "tc16"}),
     (2048, 256, 1, "e4m3", 32, "roundtrip", {"path": "tc16"}),
+    (128, 128, 9, "e4m3", 32, "roundtrip", {"path": "tc16"}),
+    (128, 512, 2, "e5m2", 64, "forward", {"path": "tc16", "fold_stats": True}),
+    (512, 128, 2, "e4m3", 32, "roundtrip", {"path": "tc16", "fold_stats": True}),
     (256, 256, 5, "e4m3", 32, "forward", {"path": "tc16", "fused2d": True}),
     (512, 512, 2, "e5m2", 32, "roundtrip", {"path": "tc16", "fused2d": True}),
 ]

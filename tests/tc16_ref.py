@@ -1,5 +1,6 @@
 """numpy emulation of the tensor-core radix-16 variant (MXFFT_OPT_PATH = 1),
-written from its description: four-step n = 16 x 16 r, each 16-point input
+written from its description: four-step n = 16 x 16 r (n = 128: 16 x 8, the
+second round 8-point DFTs of pairs of vectors), each 16-point input
 vector one MX block (k = 32; for k = 64 / 128 a block is 2 / 4 consecutive
 vectors of a transform), the real 32 x 32 DFT matrix quantised with one shared
 scale per output row, products exact and accumulated in FP64 (the hardware
@@ -54,10 +55,32 @@ def dft16_matrix(sgn, fmt):
     return Fq, sF
 
 
-def dft16_mx(V, fmt, sgn, g=1, vec_axes=1):
+def dft8pair_matrix(sgn, fmt):
+    """The 8-point DFT twice on the diagonal of the real 32 x 32 matrix (a row
+    of 16 complex elements = two 8-point vectors), quantised like the
+    16-point matrix: (element values, row scale exponents)."""
+    F = np.zeros((32, 32))
+    for b in range(2):
+        for m in range(8):
+            for j in range(8):
+                ang = 2 * np.pi * ((j * m) % 8) / 8
+                c, s = np.cos(ang), sgn * np.sin(ang)
+                c = 0.0 if abs(c) < 1e-12 else c
+                s = 0.0 if abs(s) < 1e-12 else s
+                r0, c0 = 2 * (8 * b + m), 2 * (8 * b + j)
+                F[r0, c0], F[r0, c0 + 1] = c, -s
+                F[r0 + 1, c0], F[r0 + 1, c0 + 1] = s, c
+    sF = _scale_exp(np.abs(F).max(axis=1), EMAX[fmt])
+    Fq = oracle.quantize(np.ldexp(F, -sF[:, None]), fmt)
+    return Fq, sF
+
+
+def dft16_mx(V, fmt, sgn, g=1, vec_axes=1, matrix=None):
     """V: complex64 [..., vectors, 16] -> complex64 [..., vectors, 16].  With
     k = 32 g one MX block is g consecutive vectors of a transform (the last
-    vec_axes axes before the element axis, flattened in order)."""
+    vec_axes axes before the element axis, flattened in order).  matrix:
+    (element values, row scale exponents) of another 32 x 32 real matrix than
+    the 16-point DFT's."""
     r = np.stack([V.real, V.imag], -1).reshape(V.shape[:-1] + (32,)).astype(np.float32)
     amax = np.abs(r).max(-1)
     if g > 1:
@@ -66,7 +89,7 @@ def dft16_mx(V, fmt, sgn, g=1, vec_axes=1):
         amax = np.broadcast_to(a, lead + (a.shape[-2], g)).reshape(amax.shape)
     sv = _scale_exp(amax, EMAX[fmt])
     q = _q(r * np.exp2(-sv)[..., None].astype(np.float32), fmt)
-    Fq, sF = dft16_matrix(sgn, fmt)
+    Fq, sF = dft16_matrix(sgn, fmt) if matrix is None else matrix
     D = (q @ Fq.T).astype(np.float32)                    # exact products, FP32 result
     y = (D * np.exp2(sF).astype(np.float32)) * np.exp2(sv)[..., None].astype(np.float32)
     return (y[..., 0::2] + 1j * y[..., 1::2]).astype(np.complex64)
@@ -80,16 +103,22 @@ def cmul32(w, y):
 
 
 def fft1d(x, fmt, sgn, g=1):
-    """x: complex64 [..., n], n in {256, 512, 1024, 2048}; transforms the last axis."""
+    """x: complex64 [..., n], n in {128, 256, 512, 1024, 2048}; transforms the last axis."""
     n = x.shape[-1]
     r = n // 256
-    M = 16 * r
+    M = n // 16
     X = x.reshape(x.shape[:-1] + (16, M))                # [j1][j2]
     V = np.swapaxes(X, -1, -2)                          # [j2][j1]
     Y = dft16_mx(V, fmt, sgn, g)                        # [j2][k1]
     TA = np.stack([twiddle_block(j2, n, sgn, fmt) for j2 in range(M)])  # [j2][k1]
     Y = cmul32(TA, Y)
     Y = np.swapaxes(Y, -1, -2)                          # [k1][j2]
+    if n == 128:
+        # pairs (k1 = 2 p, 2 p + 1) of 8-point vectors over j2, one MMA row each
+        P = Y.reshape(Y.shape[:-2] + (8, 16))           # [p][(k1 parity, j2)]
+        Z = dft16_mx(P, fmt, sgn, g, matrix=dft8pair_matrix(sgn, fmt))   # [p][(parity, k2)]
+        Z = Z.reshape(Y.shape[:-2] + (16, 8))           # [k1][k2]
+        return np.swapaxes(Z, -1, -2).reshape(x.shape)  # X[k1 + 16 k2]
     if r == 1:
         Z = dft16_mx(Y, fmt, sgn, g)                    # [k1][k2]
         return np.swapaxes(Z, -1, -2).reshape(x.shape)  # X[k1 + 16 k2]

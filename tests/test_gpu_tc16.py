@@ -1,5 +1,6 @@
 """Tensor-core radix-16 variant (MXFFT_OPT_PATH = 1): radix-16 sub-DFTs as
-MXFP8 tcgen05 matrix products, n in {256, 512, 1024, 2048}.  Not bit-exact
+MXFP8 tcgen05 matrix products, n in {128, 256, 512, 1024, 2048} (n = 128:
+16 x 8, the second round's 8-point DFTs in pairs per matrix row).  Not bit-exact
 with the radix-2 oracle by design; checked (1) against a numpy emulation of
 the same algorithm to FP32 accumulation-order level, and (2) against FP64 with the stated tolerance:
 NRMSE <= 1.10 x the radix-2 oracle's NRMSE on the same input."""
@@ -37,7 +38,8 @@ def nrmse(a, ref):
 
 
 @pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (512, 256), (1024, 1024),
-                                   (256, 1024), (1024, 512)])
+                                   (256, 1024), (1024, 512), (128, 128), (128, 256), (256, 128),
+                                   (128, 1024), (2048, 128)])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("op", ["forward", "inverse", "roundtrip"])
 def test_tc16_matches_emulation(n0, n1, fmt, op, cuda_device):
@@ -61,7 +63,8 @@ def test_tc16_2048_matches_emulation(n0, n1, fmt, op, cuda_device):
     assert_close_to_emulation(got, want, (n0, n1, fmt, op))
 
 
-@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (1024, 256), (2048, 256)])
+@pytest.mark.parametrize("n0,n1", [(256, 256), (512, 512), (256, 512), (1024, 256), (2048, 256),
+                                   (128, 128), (128, 512)])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("k", [64, 128])
 def test_tc16_shared_block_scales_match_emulation(n0, n1, fmt, k, cuda_device):
@@ -74,7 +77,7 @@ def test_tc16_shared_block_scales_match_emulation(n0, n1, fmt, k, cuda_device):
         assert_close_to_emulation(got, want, (n0, n1, fmt, k, op))
 
 
-@pytest.mark.parametrize("n", [256, 512, 1024])
+@pytest.mark.parametrize("n", [128, 256, 512, 1024])
 @pytest.mark.parametrize("fmt", ["e4m3", "e5m2"])
 @pytest.mark.parametrize("k", [32, 64, 128])
 def test_tc16_within_stated_tolerance(n, fmt, k, cuda_device):
@@ -100,7 +103,7 @@ def test_tc16_2048_within_stated_tolerance(fmt, cuda_device):
 
 def test_tc16_option_validation(cuda_device):
     from paper_2512_04317_gb300 import mxfft
-    for args in [(128, 256, "e4m3", 32), (256, 256, "e2m3", 32), (256, 256, "e4m3", 16)]:
+    for args in [(64, 256, "e4m3", 32), (256, 256, "e2m3", 32), (256, 256, "e4m3", 16)]:
         with pytest.raises(mxfft.MxfftError) as ei:
             mxfft.Plan(*args, path="tc16")
         assert ei.value.status == mxfft.MXFFT_ERR_UNSUPPORTED
@@ -112,7 +115,8 @@ def test_tc16_option_validation(cuda_device):
 
 @pytest.mark.parametrize("n0,n1,batch", [(256, 256, 40), (512, 512, 6), (512, 256, 11),
                                          (1024, 1024, 3), (1024, 256, 5), (2048, 2048, 2),
-                                         (2048, 256, 9)])
+                                         (2048, 256, 9), (128, 128, 97), (128, 512, 7),
+                                         (512, 128, 13)])
 def test_tc16_many_tiles_per_cta(n0, n1, batch, cuda_device):
     # more 4096-point tiles than resident CTAs: every CTA walks several tiles,
     # an uneven number each, through both shared buffers

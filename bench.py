@@ -70,6 +70,10 @@ def parse():
                     help="tc16: radix-16 tcgen05 variant (within the stated NRMSE; the default "
                          "where the workload's shape allows it); radix2: the bit-exact radix-2 "
                          "MX path (always timed beside the headline)")
+    ap.add_argument("--fused2d", action="store_true",
+                    help="tensor-core path: the fused 2D kernel (MXFFT_OPT_FUSED2D: a whole "
+                         "transform per launch on one thread-block cluster per slice) where the "
+                         "shape allows it")
     ap.add_argument("--api", choices=["engine", "plan"], default="engine",
                     help="engine: one batch-executor run per step, replayed as a CUDA graph; "
                          "plan: mxfft_forward + mxfft_roundtrip calls")
@@ -638,14 +642,15 @@ def main():
     yk = torch.empty_like(xk)
     yi = torch.empty_like(xi)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"], path=path)
+    fused2d = args.fused2d and path == "tc16"
+    plan = mxfft.Plan(n0, n1, w["fmt"], w["k"], path=path, fused2d=fused2d)
     stream = torch.cuda.current_stream(dev)
     engine = None
     if args.api == "engine":
         # one run per step: a statistics launch over both batches, the forward
         # passes of both as one launch per axis, then the round trip's
         # statistics and inverse passes; captured once, replayed as a graph
-        engine = mxfft.Engine(graphs=True, tc16=path == "tc16")
+        engine = mxfft.Engine(graphs=True, tc16=path == "tc16", fused2d=fused2d)
         work = [("forward", xk, yk, w["fmt"], w["k"]), ("roundtrip", xi, yi, w["fmt"], w["k"])]
 
         def step():
@@ -791,7 +796,8 @@ def main():
                  "oi": torch.empty_like(hi).pin_memory(),
                  "in_done": torch.cuda.Event(), "run_done": torch.cuda.Event(),
                  "out_done": torch.cuda.Event()}
-            lanes.append((torch.cuda.Stream(dev), mxfft.Engine(graphs=True, tc16=path == "tc16"), b))
+            lanes.append((torch.cuda.Stream(dev), mxfft.Engine(graphs=True, tc16=path == "tc16",
+                                                               fused2d=fused2d), b))
 
         def e2e_step(i):
             st_, eng_j, b = lanes[i % len(lanes)]
@@ -898,7 +904,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype_label(w["fmt"]), "data": "synthetic",
-            "config": {"workload": args.workload, "desc": w["desc"], "path": path,
+            "config": {"workload": args.workload, "desc": w["desc"],
+                       "path": path + ("+fused2d" if fused2d else ""),
                        "api": args.api, "tuning": tuning,
                        "n0": n0, "n1": n1,
                        "batch_per_gpu": batch, "format": w["fmt"], "k": w["k"],

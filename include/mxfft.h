@@ -341,12 +341,14 @@ int mxfft_engine_launches(mxfft_engine_t e, int *launches);
 int mxfft_engine_destroy(mxfft_engine_t e);
 
 /* ======================================================================
- * Launch-geometry autotuner.  Measures the CTA shapes of the radix-2 pass
- * kernel (transform groups per CTA) for a plan's passes at a given batch
- * and keeps the fastest in a process-wide table that later launches of the
- * same (length, other extent, axis, format, block size, batch class) use.
- * Every shape computes the same bits.  The table can be saved to and loaded
- * from a JSON file.
+ * Launch-geometry autotuner.  Measures, for a plan's passes at a given
+ * batch, the CTA shapes of the radix-2 pass kernel (transform groups per CTA)
+ * or, on the tensor-core path (MXFFT_OPT_PATH = 1), the resident CTAs per SM
+ * of its persistent grid (1 or 2), and keeps the fastest in a process-wide
+ * table that later launches of the same (length, other extent, axis,
+ * format, block size, batch class) use.  Every shape computes the same bits.
+ * The table can be saved to and loaded from a JSON file (tensor-core entries
+ * carry "kind": 1 and "ctas_per_sm").
  *
  * mxfft_tune -- synchronous; allocates a scratch batch on the device,
  *   times each candidate with CUDA events on the stream, frees the scratch.

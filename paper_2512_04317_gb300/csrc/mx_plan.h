@@ -60,6 +60,8 @@ KParams kparams(const mxfft_plan_s* p);
 PassArgs pass_args(const mxfft_plan_s* p, int dim, int dir, const float2* in, float2* out);
 // Whether a plan's forward / inverse transforms run as the fused 2D
 // tensor-core kernel; its arguments for one launch (dir 0 forward, 1 inverse).
+// Arguments of the tensor-core pass for pass a of plan p in direction dir.
+mxfft::Tc16Args tc16_args(const mxfft_plan_s* p, const mxfft::PassArgs& a, int dir);
 // true when the tensor-core columns pass of a round trip accumulates the
 // inverse's prescale statistics of its output (no separate statistics pass)
 bool tc16_folds_stats(const mxfft_plan_s* p);

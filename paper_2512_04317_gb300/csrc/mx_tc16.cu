@@ -725,28 +725,29 @@ tc16_pass_kernel(const Args a) {
 }
 
 template <int FMT, int DIM, int LOGN, bool FOLD>
-cudaError_t launch_inst(const Args& a, cudaStream_t s) {
+cudaError_t launch_inst(const Args& a, int cps, cudaStream_t s) {
     using G = Geo<LOGN>;
     const size_t smem = kOffBuf + 2 * (size_t)G::BUF_SLOTS * sizeof(float2);
     void (*k)(const Args) = tc16_pass_kernel<FMT, DIM, LOGN, FOLD>;
-    // per kernel instance: shared-memory opt-in and resident CTAs per SM
-    static int resident = 0;
-    if (resident == 0) {
+    // per kernel instance: shared-memory opt-in and the SM count
+    static int sms = 0;
+    if (sms == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
-        if (e != cudaSuccess) return e;
+        int dev = 0, count = 0;
         e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        // the occupancy query reports 1 CTA per SM for these kernels; the
-        // shared-memory and register budgets hold 2, as __launch_bounds__ asks
-        resident = (per_sm > 2 ? per_sm : 2) * sms;
+        sms = count;
     }
+    // the shared-memory and register budgets hold 2 CTAs per SM, as
+    // __launch_bounds__ asks (the occupancy query, which does not see that
+    // the kernel's tensor memory fits twice, reports 1)
+    const int per_sm = cps >= 1 && cps <= kTc16MaxCtasPerSm ? cps : kTc16MaxCtasPerSm;
+    const int resident = per_sm * sms;
     const int other = DIM == 1 ? a.n0 : a.n1;
     const int ntiles = a.batch * (other / G::T);
     const int blocks = ntiles < resident ? ntiles : resident;
@@ -756,18 +757,20 @@ cudaError_t launch_inst(const Args& a, cudaStream_t s) {
 }
 
 template <int FMT, int DIM, int LOGN>
-cudaError_t launch_one(const Args& a, cudaStream_t s) {
-    if (DIM == 0 && LOGN <= 10 && a.stats_out) return launch_inst<FMT, 0, (LOGN <= 10 ? LOGN : 10), true>(a, s);
-    return launch_inst<FMT, DIM, LOGN, false>(a, s);
+cudaError_t launch_one(const Args& a, int cps, cudaStream_t s) {
+    if (DIM == 0 && LOGN <= 10 && a.stats_out)
+        return launch_inst<FMT, 0, (LOGN <= 10 ? LOGN : 10), true>(a, cps, s);
+    return launch_inst<FMT, DIM, LOGN, false>(a, cps, s);
 }
 
 template <int FMT>
-cudaError_t launch_fmt(const Args& a, cudaStream_t s) {
-    if (a.n == 128) return a.dim == 1 ? launch_one<FMT, 1, 7>(a, s) : launch_one<FMT, 0, 7>(a, s);
-    if (a.n == 256) return a.dim == 1 ? launch_one<FMT, 1, 8>(a, s) : launch_one<FMT, 0, 8>(a, s);
-    if (a.n == 512) return a.dim == 1 ? launch_one<FMT, 1, 9>(a, s) : launch_one<FMT, 0, 9>(a, s);
-    if (a.n == 1024) return a.dim == 1 ? launch_one<FMT, 1, 10>(a, s) : launch_one<FMT, 0, 10>(a, s);
-    return a.dim == 1 ? launch_one<FMT, 1, 11>(a, s) : launch_one<FMT, 0, 11>(a, s);
+cudaError_t launch_fmt(const Args& a, int cps, cudaStream_t s) {
+    const bool rows = a.dim == 1;
+    if (a.n == 128) return rows ? launch_one<FMT, 1, 7>(a, cps, s) : launch_one<FMT, 0, 7>(a, cps, s);
+    if (a.n == 256) return rows ? launch_one<FMT, 1, 8>(a, cps, s) : launch_one<FMT, 0, 8>(a, cps, s);
+    if (a.n == 512) return rows ? launch_one<FMT, 1, 9>(a, cps, s) : launch_one<FMT, 0, 9>(a, cps, s);
+    if (a.n == 1024) return rows ? launch_one<FMT, 1, 10>(a, cps, s) : launch_one<FMT, 0, 10>(a, cps, s);
+    return rows ? launch_one<FMT, 1, 11>(a, cps, s) : launch_one<FMT, 0, 11>(a, cps, s);
 }
 
 }  // namespace tc16
@@ -780,13 +783,19 @@ bool tc16_supported(int n, int other, int fmt) {
     return other >= T && other % T == 0 && (fmt == 0 || fmt == 1);
 }
 
-cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s) {
+cudaError_t launch_tc16_pass_ctas(const Tc16Args& a, int fmt, int batch, int ctas_per_sm,
+                                  cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
     Tc16Args b = a;
     b.batch = batch;
-    if (fmt == 0) return tc16::launch_fmt<0>(b, s);
-    if (fmt == 1) return tc16::launch_fmt<1>(b, s);
+    if (fmt == 0) return tc16::launch_fmt<0>(b, ctas_per_sm, s);
+    if (fmt == 1) return tc16::launch_fmt<1>(b, ctas_per_sm, s);
     return cudaErrorNotSupported;
+}
+
+cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s) {
+    const int other = a.dim == 1 ? a.n0 : a.n1;
+    return launch_tc16_pass_ctas(a, fmt, batch, tc16_ctas_tuned(a.n, other, a.dim, fmt, a.g, batch), s);
 }
 
 MX_BOUNDS_COUNTER(tc16)

@@ -1,9 +1,11 @@
-// Launch-geometry autotuner of the register-resident radix-2 pass: the
-// number of transform groups per CTA is measured per (transform length,
-// other extent, axis, element format, block size, batch class) and the
-// fastest kept in a process-wide table, which the pass launcher consults and
-// which can be saved to / merged from a JSON file.  Every geometry computes
-// the same bits: each transform is processed independently in a fixed order.
+// Launch-geometry autotuner.  Register-resident radix-2 pass: the number of
+// transform groups per CTA; tensor-core pass: the resident CTAs per SM of its
+// persistent grid (1 or 2).  Each is measured per (transform length, other
+// extent, axis, element format, block size, batch class) and the fastest kept
+// in a process-wide table, which the launchers consult and which can be saved
+// to / merged from a JSON file.  Every geometry computes the same bits: each
+// transform (tensor-core pass: each tile) is processed independently in a
+// fixed order.
 #include <cerrno>
 #include <cstdio>
 #include <cstdlib>
@@ -28,9 +30,11 @@ int batch_class(int batch) {
     return c;
 }
 
-using Key = std::tuple<int, int, int, int, int, int>;   // n, other, dim, fmt, m, class
+// n, other, dim, fmt, m (tensor-core pass: vectors per MX block), batch class,
+// kind (0 radix-2 groups per CTA, 1 tensor-core CTAs per SM)
+using Key = std::tuple<int, int, int, int, int, int, int>;
 struct Val {
-    int ng;
+    int ng;        // groups per CTA, or CTAs per SM
     double us;
 };
 
@@ -75,6 +79,26 @@ double time_ng(mxfft_plan_s* p, const PassArgs& a, int batch, int ng, cudaStream
     return us;
 }
 
+// The same for the tensor-core pass with ctas CTAs per SM.
+double time_tc16(const Tc16Args& t, int fmt, int batch, int ctas, cudaStream_t s, int warm, int reps) {
+    for (int i = 0; i < warm; i++)
+        if (launch_tc16_pass_ctas(t, fmt, batch, ctas, s) != cudaSuccess) return -1.0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
+    double us = -1.0;
+    cudaEventRecord(e0, s);
+    bool ok = true;
+    for (int i = 0; i < reps && ok; i++) ok = launch_tc16_pass_ctas(t, fmt, batch, ctas, s) == cudaSuccess;
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        us = 1000.0 * ms / reps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return us;
+}
+
 // Integer value of "key": in a flat JSON object text (no nesting).
 bool json_int(const std::string& obj, const char* key, long* v) {
     const std::string k = std::string("\"") + key + "\"";
@@ -97,13 +121,24 @@ namespace mxfft {
 
 int fast_ng_tuned(int n, int other, int dim, int fmt, int m, int batch) {
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = table().find(Key(n, other, dim, fmt, m, batch_class(batch)));
+    auto it = table().find(Key(n, other, dim, fmt, m, batch_class(batch), 0));
     return it == table().end() ? 0 : it->second.ng;
 }
 
 void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng, double us) {
     std::lock_guard<std::mutex> lk(g_mu);
-    table()[Key(n, other, dim, fmt, m, batch_class(batch))] = Val{ng, us};
+    table()[Key(n, other, dim, fmt, m, batch_class(batch), 0)] = Val{ng, us};
+}
+
+int tc16_ctas_tuned(int n, int other, int dim, int fmt, int g, int batch) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = table().find(Key(n, other, dim, fmt, g, batch_class(batch), 1));
+    return it == table().end() ? 0 : it->second.ng;
+}
+
+void tc16_ctas_store(int n, int other, int dim, int fmt, int g, int batch, int ctas, double us) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    table()[Key(n, other, dim, fmt, g, batch_class(batch), 1)] = Val{ctas, us};
 }
 
 }  // namespace mxfft
@@ -113,7 +148,7 @@ extern "C" {
 int mxfft_tune(mxfft_plan_t p, int batch, void* stream, int* n_measured) {
     if (n_measured) *n_measured = 0;
     if (!p || batch < 1) return MXFFT_ERR_INVALID;
-    if (p->path != 0 || p->force_generic) return MXFFT_OK;   // nothing to choose
+    if (p->path == 0 && p->force_generic) return MXFFT_OK;   // nothing to choose
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return MXFFT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
@@ -135,8 +170,21 @@ int mxfft_tune(mxfft_plan_t p, int batch, void* stream, int* n_measured) {
         a.st = st;
         a.prologue = dim == 1 ? PRO_PRESCALE : PRO_NONE;
         a.epilogue = dim == 1 ? EPI_RAW : EPI_UNSCALE;
-        if (!fast_pass_supported(a)) continue;
         const int other = dim == 1 ? p->n0 : p->n1;
+        if (p->path == 1) {
+            const Tc16Args t = tc16_args(p, a, 0);
+            int best = 0;
+            double best_us = 0.0;
+            for (int c = 1; c <= kTc16MaxCtasPerSm; c++) {
+                const double us = time_tc16(t, p->fmt, batch, c, s, 2, 5);
+                if (us < 0) { rc = MXFFT_ERR_CUDA; break; }
+                measured++;
+                if (best == 0 || us < best_us) { best = c; best_us = us; }
+            }
+            if (rc == MXFFT_OK) tc16_ctas_store(a.n, other, dim, p->fmt, t.g, batch, best, best_us);
+            continue;
+        }
+        if (!fast_pass_supported(a)) continue;
         int cand[16];
         const int nc = fast_ng_candidates(a.n, other, a.m, cand, 16);
         if (nc < 2) continue;
@@ -166,12 +214,20 @@ int mxfft_tune_save(const char* path) {
         bool first = true;
         for (const auto& kv : table()) {
             char buf[256];
-            std::snprintf(buf, sizeof buf,
-                          "%s\n  {\"n\": %d, \"other\": %d, \"dim\": %d, \"fmt\": %d, \"m\": %d, "
-                          "\"batch_class\": %d, \"ng\": %d, \"us\": %.3f}",
-                          first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first),
-                          std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first),
-                          std::get<5>(kv.first), kv.second.ng, kv.second.us);
+            if (std::get<6>(kv.first) == 1)
+                std::snprintf(buf, sizeof buf,
+                              "%s\n  {\"kind\": 1, \"n\": %d, \"other\": %d, \"dim\": %d, \"fmt\": %d, "
+                              "\"m\": %d, \"batch_class\": %d, \"ctas_per_sm\": %d, \"us\": %.3f}",
+                              first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first),
+                              std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first),
+                              std::get<5>(kv.first), kv.second.ng, kv.second.us);
+            else
+                std::snprintf(buf, sizeof buf,
+                              "%s\n  {\"n\": %d, \"other\": %d, \"dim\": %d, \"fmt\": %d, \"m\": %d, "
+                              "\"batch_class\": %d, \"ng\": %d, \"us\": %.3f}",
+                              first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first),
+                              std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first),
+                              std::get<5>(kv.first), kv.second.ng, kv.second.us);
             out += buf;
             first = false;
         }
@@ -200,17 +256,24 @@ int mxfft_tune_load(const char* path) {
         const size_t end = text.find('}', at);
         if (end == std::string::npos) return MXFFT_ERR_INVALID;
         const std::string obj = text.substr(at, end - at + 1);
-        long n, other, dim, fmt, m, bc, ng;
+        long n, other, dim, fmt, m, bc, ng, kind = 0;
+        if (json_int(obj, "kind", &kind) && kind != 0 && kind != 1) return MXFFT_ERR_INVALID;
         if (!json_int(obj, "n", &n) || !json_int(obj, "other", &other) || !json_int(obj, "dim", &dim) ||
             !json_int(obj, "fmt", &fmt) || !json_int(obj, "m", &m) ||
-            !json_int(obj, "batch_class", &bc) || !json_int(obj, "ng", &ng))
+            !json_int(obj, "batch_class", &bc) || !json_int(obj, kind == 1 ? "ctas_per_sm" : "ng", &ng))
             return MXFFT_ERR_INVALID;
-        int cand[16];
-        const int nc = fast_ng_candidates((int)n, (int)other, (int)m, cand, 16);
         bool valid = false;
-        for (int i = 0; i < nc; i++) valid = valid || cand[i] == ng;
+        if (kind == 1) {
+            valid = ng >= 1 && ng <= kTc16MaxCtasPerSm && tc16_supported((int)n, (int)other, (int)fmt) &&
+                    (m == 1 || m == 2 || m == 4);
+        } else {
+            int cand[16];
+            const int nc = fast_ng_candidates((int)n, (int)other, (int)m, cand, 16);
+            for (int i = 0; i < nc; i++) valid = valid || cand[i] == ng;
+        }
         if (!valid || (dim != 0 && dim != 1) || bc < 0 || bc > 30) return MXFFT_ERR_INVALID;
-        parsed.push_back({Key((int)n, (int)other, (int)dim, (int)fmt, (int)m, (int)bc), Val{(int)ng, 0.0}});
+        parsed.push_back({Key((int)n, (int)other, (int)dim, (int)fmt, (int)m, (int)bc, (int)kind),
+                          Val{(int)ng, 0.0}});
         at = end + 1;
     }
     std::lock_guard<std::mutex> lk(g_mu);

@@ -542,6 +542,37 @@ cudaError_t timed_tc2d(mxfft_plan_s* p, const Tc2dArgs& a, int batch, cudaStream
     return e;
 }
 
+Tc16Args tc16_args(const mxfft_plan_s* p, const PassArgs& a, int dir) {
+    Tc16Args t;
+    std::memset(&t, 0, sizeof(t));
+    t.in = a.in;
+    t.out = a.out;
+    t.ref = a.ref;
+    t.n0 = a.n0;
+    t.n1 = a.n1;
+    t.dim = a.dim;
+    t.n = a.n;
+    t.r = a.n / 256;
+    t.bmat = p->d_bmat[dir];
+    t.bmat2 = p->d_bmat8[dir];
+    t.twA = p->d_twA[a.dim][dir];
+    t.twC = p->d_twC[a.dim][dir];
+    t.st = a.st;
+    t.prologue = a.prologue;
+    t.epilogue = a.epilogue;
+    t.lg_total = a.lg_total;
+    const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
+    t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    t.err = p->d_err;
+    t.stall = p->test_stall;
+    t.g = p->kblk / 32;
+    t.inv = dir;
+    t.st_out = a.st_out;
+    t.stats_out = a.stats_out;
+    t.kp = a.kp;
+    return t;
+}
+
 // The tensor-core pass when that path is selected, else the register-resident
 // kernel where it applies (n in [64, 2048], m <= 16; m = 32, 64 for n >= 128),
 // else the generic shared-memory kernel.
@@ -549,33 +580,7 @@ cudaError_t timed_pass(mxfft_plan_s* p, const PassArgs& a, int batch, cudaStream
     NvtxRange range(a.dim == 1 ? "mxfft rows pass" : "mxfft columns pass");
     const int dir = a.tw == p->d_tw[a.dim][1] ? 1 : 0;
     if (p->path == 1) {
-        Tc16Args t;
-        std::memset(&t, 0, sizeof(t));
-        t.in = a.in;
-        t.out = a.out;
-        t.ref = a.ref;
-        t.n0 = a.n0;
-        t.n1 = a.n1;
-        t.dim = a.dim;
-        t.n = a.n;
-        t.r = a.n / 256;
-        t.bmat = p->d_bmat[dir];
-        t.bmat2 = p->d_bmat8[dir];
-        t.twA = p->d_twA[a.dim][dir];
-        t.twC = p->d_twC[a.dim][dir];
-        t.st = a.st;
-        t.prologue = a.prologue;
-        t.epilogue = a.epilogue;
-        t.lg_total = a.lg_total;
-        const uint32_t ft = p->fmt == MXFFT_E5M2 ? 1u : 0u;
-        t.idesc = (1u << 4) | (ft << 7) | (ft << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-        t.err = p->d_err;
-        t.stall = p->test_stall;
-        t.g = p->kblk / 32;
-        t.inv = dir;
-        t.st_out = a.st_out;
-        t.stats_out = a.stats_out;
-        t.kp = a.kp;
+        const Tc16Args t = tc16_args(p, a, dir);
         ProfRec* r = prof_begin(p, 3, s);
         cudaError_t e = launch_tc16_pass(t, p->fmt, batch, s);
         prof_end(r, s);

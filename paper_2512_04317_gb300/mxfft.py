@@ -332,7 +332,8 @@ def rss(z, coils: int, out=None):
 # ---- autotuner -------------------------------------------------------------------
 
 def mxfft_tune(plan, batch: int, stream=None) -> int:
-    """Measure the radix-2 pass geometries of `plan` at `batch`; returns the
+    """Measure the launch geometries of `plan`'s passes at `batch` (radix-2:
+    groups per CTA; tensor-core path: resident CTAs per SM); returns the
     number of candidates timed."""
     n = ctypes.c_int(0)
     _check(load().mxfft_tune(plan, int(batch), stream, ctypes.byref(n)), "mxfft_tune")

@@ -63,6 +63,17 @@ def test_tuning_file_round_trip(lib, tmp_path):
     got = json.loads(out.read_text())["entries"]
     assert len(got) == 1
     assert {k: got[0][k] for k in entry if k != "us"} == {k: entry[k] for k in entry if k != "us"}
+    # a tensor-core entry (resident CTAs per SM of its persistent grid) beside it
+    tc = {"kind": 1, "n": 512, "other": 512, "dim": 0, "fmt": 0, "m": 1, "batch_class": 9,
+          "ctas_per_sm": 1, "us": 2.0}
+    f.write_text(json.dumps({"mxfft_tune": 1, "entries": [tc]}))
+    mxfft.mxfft_tune_load(str(f))
+    mxfft.mxfft_tune_save(str(out))
+    got = json.loads(out.read_text())["entries"]
+    assert len(got) == 2
+    kinds = {g.get("kind", 0): g for g in got}
+    assert {k: kinds[1][k] for k in tc if k != "us"} == {k: tc[k] for k in tc if k != "us"}
+    assert "ctas_per_sm" not in kinds[0] and kinds[0]["ng"] == 2
     mxfft.mxfft_tune_clear()
     mxfft.mxfft_tune_save(str(out))
     assert json.loads(out.read_text())["entries"] == []
@@ -76,6 +87,16 @@ def test_tuning_file_round_trip(lib, tmp_path):
     ' "batch_class": 6, "ng": 3}]}',                                       # not a candidate
     '{"mxfft_tune": 1, "entries": [{"n": 256, "other": 256, "dim": 1, "fmt": 0, "m": 16,'
     ' "batch_class": 6, "ng": 8}]}',                                       # 1024 threads
+    '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 512, "other": 512, "dim": 1, "fmt": 0,'
+    ' "m": 1, "batch_class": 6, "ctas_per_sm": 3}]}',                      # above 2 per SM
+    '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 64, "other": 512, "dim": 1, "fmt": 0,'
+    ' "m": 1, "batch_class": 6, "ctas_per_sm": 1}]}',                      # no tensor-core pass
+    '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 512, "other": 512, "dim": 1, "fmt": 2,'
+    ' "m": 1, "batch_class": 6, "ctas_per_sm": 1}]}',                      # 6-bit format
+    '{"mxfft_tune": 1, "entries": [{"kind": 2, "n": 256, "other": 256, "dim": 1, "fmt": 0,'
+    ' "m": 16, "batch_class": 6, "ng": 2}]}',                              # unknown kind
+    '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 512, "other": 512, "dim": 1, "fmt": 0,'
+    ' "m": 1, "batch_class": 6, "ng": 1}]}',                               # field of the other kind
 ])
 def test_tuning_file_rejects_malformed(lib, tmp_path, bad):
     f = tmp_path / "bad.json"

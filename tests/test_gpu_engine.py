@@ -163,6 +163,33 @@ def test_tuned_geometries_give_the_same_bits(k, cuda_device, tmp_path):
     mxfft.mxfft_tune_clear()
 
 
+@pytest.mark.parametrize("n0,n1,batch", [(512, 512, 24), (128, 1024, 9)])
+def test_tuned_tensor_core_grid_gives_the_same_bits(n0, n1, batch, cuda_device, tmp_path):
+    # the tensor-core pass's persistent grid with 1 or 2 CTAs per SM: every
+    # CTA count walks the same tiles with the same arithmetic
+    import torch
+
+    from paper_2512_04317_gb300 import mxfft
+    x = torch.from_numpy(phantom.mri_batch(n0, n1, batch, 1, config_id=43, domain="image")).cuda()
+    mxfft.mxfft_tune_clear()
+    with mxfft.Plan(n0, n1, "e4m3", 32, path="tc16") as p:
+        want = p.roundtrip(x).cpu().numpy()
+        assert mxfft.mxfft_tune(p.handle, batch) == 4          # 2 CTA counts x 2 axes
+        path = tmp_path / "tune.json"
+        mxfft.mxfft_tune_save(str(path))
+        entries = json.loads(path.read_text())["entries"]
+        assert {(e["kind"], e["dim"]) for e in entries} == {(1, 0), (1, 1)}
+        for ctas in (1, 2):
+            for e in entries:
+                e["ctas_per_sm"] = ctas
+            path.write_text(json.dumps({"mxfft_tune": 1, "entries": entries}))
+            mxfft.mxfft_tune_load(str(path))
+            np.testing.assert_array_equal(p.roundtrip(x).cpu().numpy().view(np.uint32),
+                                          want.view(np.uint32))
+            assert p.status()[1] == 0
+    mxfft.mxfft_tune_clear()
+
+
 def test_engine_many_groups_beyond_fork_streams(cuda_device):
     # 12 (plan, direction) groups share 8 fork streams; round trips of several
     # plans run as the second stage

@@ -343,12 +343,14 @@ int mxfft_engine_destroy(mxfft_engine_t e);
 /* ======================================================================
  * Launch-geometry autotuner.  Measures, for a plan's passes at a given
  * batch, the CTA shapes of the radix-2 pass kernel (transform groups per CTA)
- * or, on the tensor-core path (MXFFT_OPT_PATH = 1), the resident CTAs per SM
- * of its persistent grid (1 or 2), and keeps the fastest in a process-wide
- * table that later launches of the same (length, other extent, axis,
- * format, block size, batch class) use.  Every shape computes the same bits.
- * The table can be saved to and loaded from a JSON file (tensor-core entries
- * carry "kind": 1 and "ctas_per_sm").
+ * or, on the tensor-core path (MXFFT_OPT_PATH = 1), the tile and the
+ * resident CTAs per SM of its persistent grid (4096-point tiles on 256
+ * threads, 1 or 2 per SM; for n <= 1024 also 2048-point tiles on 128
+ * threads, 2 to 6 per SM), and keeps the fastest in a process-wide table
+ * that later launches of the same (length, other extent, axis, format, block
+ * size, batch class) use.  Every shape computes the same bits.  The table can
+ * be saved to and loaded from a JSON file (tensor-core entries carry
+ * "kind": 1, "tile" and "ctas_per_sm").
  *
  * mxfft_tune -- synchronous; allocates a scratch batch on the device,
  *   times each candidate with CUDA events on the stream, frees the scratch.

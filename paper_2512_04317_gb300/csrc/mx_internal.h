@@ -234,16 +234,20 @@ bool tc2d_supported(int n0, int n1, int fmt, int kblk);
 int tc2d_resident_clusters(int n0, int n1, int fmt);
 cudaError_t launch_tc2d(const Tc2dArgs& a, int fmt, cudaStream_t s);
 // Tensor-core radix-16 pass: n in {128, 256, 512, 1024, 2048}, 8-bit formats,
-// other a multiple of 4096 / n.  The persistent grid holds ctas_per_sm CTAs
-// per SM (1 or 2; 0: the tuned value, else 2).
+// other a multiple of 4096 / n.  Launch geometry: tiles of 4096 points on
+// CTAs of 256 threads, or (n <= 1024) tiles of 2048 points on CTAs of 128
+// threads; the persistent grid holds ctas_per_sm CTAs per SM (at most what
+// an SM holds; 0: all of them).  launch_tc16_pass takes the tuned geometry
+// (tile 0: 4096, all that fit).
 bool tc16_supported(int n, int other, int fmt);
 cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s);
-cudaError_t launch_tc16_pass_ctas(const Tc16Args& a, int fmt, int batch, int ctas_per_sm,
-                                  cudaStream_t s);
-constexpr int kTc16MaxCtasPerSm = 2;
-// Resident CTAs per SM of the tensor-core pass: the tuned value for a launch
-// (0 if none) and the autotuner's table (mx_tune.cu).
-int tc16_ctas_tuned(int n, int other, int dim, int fmt, int g, int batch);
-void tc16_ctas_store(int n, int other, int dim, int fmt, int g, int batch, int ctas, double us);
+cudaError_t launch_tc16_pass_geo(const Tc16Args& a, int fmt, int batch, int tile, int ctas_per_sm,
+                                 cudaStream_t s);
+constexpr int kTc16MaxCtasPerSm = 8;
+// The autotuner's table (mx_tune.cu): the tuned (tile, CTAs per SM) of a
+// tensor-core launch (0, 0 if none), and storing one.
+void tc16_geo_tuned(int n, int other, int dim, int fmt, int g, int batch, int* tile, int* ctas);
+void tc16_geo_store(int n, int other, int dim, int fmt, int g, int batch, int tile, int ctas,
+                    double us);
 
 }  // namespace mxfft

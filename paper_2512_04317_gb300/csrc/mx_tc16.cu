@@ -49,25 +49,28 @@ namespace tc16 {
 
 using namespace tcg;
 
-constexpr int kThreads = 256;
-constexpr int kTilePts = 4096;        // points per tile = 256 vectors x 16
-constexpr uint32_t kTmemCols = 64;    // two 128 x 32 FP32 accumulators
-// Dynamic shared memory: A operand (2 x 128 rows x 32 B), B operand (32 x 32
-// B), twiddles (rows of 16 padded to 18 values so that a quarter-warp's 16-byte
-// reads of 8 consecutive rows hit distinct banks), then the two tile buffers.
+// Two CTA shapes, NT threads on tiles of 16 NT points (NT vectors of 16, one
+// per thread and round): NT = 256, two MMAs of 128 rows per round with
+// accumulators in 64 tensor-memory columns, 2 CTAs per SM; NT = 128 (n <=
+// 1024), one MMA per round, 32 columns, and up to 6 CTAs per SM, so that
+// more independent tile pipelines share an SM.  Both compute the same bits.
+template <int NT>
+struct Cta {
+    static constexpr int tile = 16 * NT;
+    static constexpr uint32_t tmem_cols = NT == 256 ? 64 : 32;
+    static constexpr int off_b = NT * 32;       // after the A operand: NT rows x 32 B
+    static constexpr int min_blocks = NT == 256 ? 2 : 4;
+};
+// Twiddle rows of 16 padded to 18 values, so that a quarter-warp's 16-byte
+// reads of 8 consecutive rows hit distinct banks.
 constexpr int kTwRow = 18;
-constexpr int kOffB = 8192;
-constexpr int kOffTwA = kOffB + 1024;                  // up to 128 rows
-constexpr int kOffTwC = kOffTwA + 128 * kTwRow * 8;    // up to 8 rows
-constexpr int kOffBuf = kOffTwC + 8 * kTwRow * 8;
-static_assert(kOffBuf % 16 == 0, "16-byte aligned cp.async destinations");
 
 using Args = Tc16Args;
 
 // Geometry of one transform length n = 2^LOGN.  n = 128 (R8): round A as
 // for the other lengths with M = 8, then one round of 8-point DFTs (see the
 // kernel), no C2.
-template <int LOGN>
+template <int LOGN, int NT>
 struct Geo {
     static constexpr int n = 1 << LOGN;
     static constexpr bool R8 = n == 128;
@@ -75,8 +78,8 @@ struct Geo {
     static constexpr int LGR = r == 1 ? 0 : (r == 2 ? 1 : (r == 4 ? 2 : 3));
     static constexpr int M = R8 ? 8 : 16 * r;       // n / 16
     static constexpr int LGM = R8 ? 3 : 4 + LGR;
-    static constexpr int T = kTilePts / n;          // transforms per tile (32, 16, 8, 4, 2)
-    static constexpr int LGT = T == 32 ? 5 : (T == 16 ? 4 : (T == 8 ? 3 : (T == 4 ? 2 : 1)));
+    static constexpr int T = Cta<NT>::tile / n;     // transforms per tile (32 .. 1)
+    static constexpr int LGT = T == 32 ? 5 : (T == 16 ? 4 : (T == 8 ? 3 : (T == 4 ? 2 : (T == 2 ? 1 : 0))));
     // rows pass: [t][e], PADR pad slots after every 2^LGP elements (M; 16
     // for n = 128, whose rows also get 8 more slots so that the 4 transforms
     // a warp spans fall on alternate halves of the banks)
@@ -87,7 +90,17 @@ struct Geo {
     // columns pass: [e][t]; with T < 16, T pad slots after every 16 elements
     static constexpr int COL_SLOTS = n * T + (T < 16 ? T * (n / 16) : 0);
     static constexpr int BUF_SLOTS = ROW_SLOTS > COL_SLOTS ? ROW_SLOTS : COL_SLOTS;
-    static_assert(T * M == kThreads, "one vector per thread per stage");
+    static_assert(T * M == NT, "one vector per thread per stage");
+    static_assert(T >= 2, "columns tiles of at least two columns (16-byte copies)");
+    // dynamic shared memory: A operand, B operand (32 x 32 B), twiddles of
+    // round A (M rows), of C1 (up to 8 rows; for n = 128 the 8-point pair
+    // matrix), then the two tile buffers
+    static constexpr int OFF_B = Cta<NT>::off_b;
+    static constexpr int OFF_TWA = OFF_B + 1024;
+    static constexpr int OFF_TWC = OFF_TWA + M * kTwRow * 8;
+    static constexpr int OFF_BUF = (OFF_TWC + 8 * kTwRow * 8 + 127) / 128 * 128;
+    static constexpr int SMEM = OFF_BUF + 2 * BUF_SLOTS * 8;
+    static_assert(OFF_TWC % 16 == 0, "16-byte aligned matrix and twiddle rows");
 };
 
 // Slot (8 bytes) of element e of transform t.  Rows pass: round A reads 16
@@ -102,19 +115,19 @@ struct Geo {
 // or T transforms x 16 / T elements whose pads put them in distinct bank
 // groups (T = 8, 4, 2).  Every pattern was checked for bank conflicts by
 // enumerating its addresses.
-template <int LOGN>
+template <int LOGN, int NT>
 __device__ __forceinline__ int slot_row(int t, int e) {
-    using G = Geo<LOGN>;
+    using G = Geo<LOGN, NT>;
     return (int)MX_BND(t * G::TS + e + G::PADR * (e >> G::LGP), G::BUF_SLOTS);
 }
-template <int LOGN>
+template <int LOGN, int NT>
 __device__ __forceinline__ int slot_col(int t, int e) {
-    using G = Geo<LOGN>;
+    using G = Geo<LOGN, NT>;
     return (int)MX_BND(e * G::T + (G::T < 16 ? G::T * (e >> 4) : 0) + t, G::BUF_SLOTS);
 }
-template <int LOGN, int DIM>
+template <int LOGN, int DIM, int NT>
 __device__ __forceinline__ int slot(int t, int e) {
-    return DIM == 1 ? slot_row<LOGN>(t, e) : slot_col<LOGN>(t, e);
+    return DIM == 1 ? slot_row<LOGN, NT>(t, e) : slot_col<LOGN, NT>(t, e);
 }
 
 // Shared state of one CTA's MMA rounds.
@@ -145,7 +158,7 @@ __device__ __forceinline__ int block_member(int v, int g, int lgt, int i) {
 // sb: the B operand (the 16-point DFT matrix, or for n = 128's second round
 // two 8-point DFTs on the diagonal, so that the row's two halves transform
 // two 8-point vectors).
-template <int FMT, int DIM>
+template <int FMT, int DIM, int NT>
 __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[16], Mma& mm,
                                             uint32_t sb, uint32_t idesc, int emax, bool issue,
                                             int g, int lgt, uint32_t* sAm) {
@@ -181,13 +194,15 @@ __device__ __forceinline__ void dft16_round(const float2 (&x)[16], float2 (&y)[1
     if (tid == 0 && issue) {
         const uint64_t bd = smem_desc(sb, 128, 256);
         const uint64_t a0 = smem_desc(mm.sa, 128, 256);
-        const uint64_t a1 = smem_desc(mm.sa + 4096, 128, 256);
         asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
                      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
                      :: "r"(mm.tbase), "l"(a0), "l"(bd), "r"(idesc), "r"(0));
-        asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
-                     " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
-                     :: "r"(mm.tbase + 32u), "l"(a1), "l"(bd), "r"(idesc), "r"(0));
+        if (NT == 256) {
+            const uint64_t a1 = smem_desc(mm.sa + 4096, 128, 256);
+            asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;"
+                         " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
+                         :: "r"(mm.tbase + 32u), "l"(a1), "l"(bd), "r"(idesc), "r"(0));
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(mm.mbar));
     }
@@ -253,12 +268,12 @@ __device__ __forceinline__ void resolve(const Args& a, int slice, bool with_k, S
 
 // Issue the cp.async copies of one tile (transforms t0 .. t0 + T - 1 of the
 // slice whose input is in) into buffer buf (8 x 16 B per thread).
-template <int LOGN, int DIM>
+template <int LOGN, int DIM, int NT>
 __device__ __forceinline__ void load_tile(const Args& a, const float2* in, int t0, uint32_t buf) {
-    using G = Geo<LOGN>;
+    using G = Geo<LOGN, NT>;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-        const int q = threadIdx.x + i * kThreads;      // 16-byte chunk of the tile
+        const int q = threadIdx.x + i * NT;            // 16-byte chunk of the tile
         const float2* src;
         int t, e;
         const size_t slice_pts = (size_t)a.n0 * a.n1;
@@ -272,26 +287,26 @@ __device__ __forceinline__ void load_tile(const Args& a, const float2* in, int t
             t = 2 * (q & ((G::T >> 1) - 1));
             src = in + MX_BND((size_t)e * a.n1 + t0 + t, slice_pts - 1);
         }
-        cp_async16(buf + 8u * (uint32_t)slot<LOGN, DIM>(t, e), src);
+        cp_async16(buf + 8u * (uint32_t)slot<LOGN, DIM, NT>(t, e), src);
     }
 }
 
 // FOLD (columns pass, n <= 1024): also accumulate the output's statistics
 // (MXFFT_OPT_FOLD_STATS); a separate instance, so that the other passes carry
 // none of its code.
-template <int FMT, int DIM, int LOGN, bool FOLD>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int FMT, int DIM, int LOGN, bool FOLD, int NT>
+__global__ void __launch_bounds__(NT, Cta<NT>::min_blocks)
 tc16_pass_kernel(const Args a) {
-    using G = Geo<LOGN>;
+    using G = Geo<LOGN, NT>;
     constexpr int r = G::r, M = G::M, T = G::T;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    __shared__ uint32_t sAm[kThreads];   // block maxima exchange (k > 32)
-    uint8_t* sB = smem + kOffB;
-    float2* sTwA = reinterpret_cast<float2*>(smem + kOffTwA);
-    float2* sTwC = reinterpret_cast<float2*>(smem + kOffTwC);
-    float2* bufs = reinterpret_cast<float2*>(smem + kOffBuf);
+    __shared__ uint32_t sAm[NT];   // block maxima exchange (k > 32)
+    uint8_t* sB = smem + G::OFF_B;
+    float2* sTwA = reinterpret_cast<float2*>(smem + G::OFF_TWA);
+    float2* sTwC = reinterpret_cast<float2*>(smem + G::OFF_TWC);
+    float2* bufs = reinterpret_cast<float2*>(smem + G::OFF_BUF);
     const uint32_t buf_u32 = smem_u32(bufs);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int other = DIM == 1 ? a.n0 : a.n1;
@@ -301,7 +316,7 @@ tc16_pass_kernel(const Args a) {
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "r"(kTmemCols));
+                     :: "r"(smem_u32(&tmem_base)), "r"(Cta<NT>::tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -312,16 +327,17 @@ tc16_pass_kernel(const Args a) {
     // n = 128 has no C2 twiddles: its 8-point pair matrix takes their place
     if (G::R8 && tid < 64)
         reinterpret_cast<uint4*>(sTwC)[tid] = __ldg(reinterpret_cast<const uint4*>(a.bmat2) + tid);
-    for (int i = tid; i < M * 16; i += kThreads) sTwA[(i >> 4) * kTwRow + (i & 15)] = __ldg(a.twA + i);
+    for (int i = tid; i < M * 16; i += NT) sTwA[(i >> 4) * kTwRow + (i & 15)] = __ldg(a.twA + i);
     if (r > 1 && tid < r * 16) sTwC[(tid >> 4) * kTwRow + (tid & 15)] = __ldg(a.twC + tid);
     // CTA b takes the contiguous tiles [tile_begin, tile_end), shares equal to
-    // within one tile.  Exception: the columns pass of n = 2048, whose tiles
-    // are 2 columns (16 bytes of each row): there CTA b takes the tiles b, b +
+    // within one tile.  Exception: a columns pass whose tiles are 2 columns
+    // (16 bytes of each row; n = 2048 with 256 threads, n = 1024 with 128):
+    // there CTA b takes the tiles b, b +
     // grid, ..., so that the CTAs working at the same time read and write
     // adjacent columns and share every DRAM sector (a contiguous range would
     // leave each sector's other half to the same CTA's next tile, after the
     // sector has left L2).
-    constexpr bool kStrided = DIM == 0 && T == 2;
+    constexpr bool kStrided = DIM == 0 && T == 2;   // n = 2048 (NT = 256), n = 1024 (NT = 128)
     const int share = ntiles / (int)gridDim.x, extra = ntiles % (int)gridDim.x;
     const int tile_begin = kStrided ? (int)blockIdx.x
                                     : (int)blockIdx.x * share + min((int)blockIdx.x, extra);
@@ -347,7 +363,7 @@ tc16_pass_kernel(const Args a) {
     int seg_slice = -1, seg_tiles = 0;
     SliceStats* seg_st = nullptr;
     if (fold)
-        for (int b = tid; b < kHistBins; b += kThreads) so_hist[b] = 0;
+        for (int b = tid; b < kHistBins; b += NT) so_hist[b] = 0;
     (void)seg_slice; (void)seg_tiles; (void)so_misc;
     auto flush_out = [&]() {
         if (seg_st) {
@@ -355,7 +371,7 @@ tc16_pass_kernel(const Args a) {
             stats_flush_and_select_n(oacc, so_hist, so_misc, seg_st, (uint32_t)seg_tiles,
                                      (uint32_t)per_slice, a.kp);
             __syncthreads();
-            for (int b = tid; b < kHistBins; b += kThreads) so_hist[b] = 0;
+            for (int b = tid; b < kHistBins; b += NT) so_hist[b] = 0;
             oacc = StatAcc();
             __syncthreads();
         }
@@ -363,7 +379,7 @@ tc16_pass_kernel(const Args a) {
     if (my_tiles > 0) {
         const int sl = tile_begin / per_slice;
         resolve(a, sl, false, ld);
-        load_tile<LOGN, DIM>(a, ld.in, (tile_begin - sl * per_slice) * T, buf_u32);
+        load_tile<LOGN, DIM, NT>(a, ld.in, (tile_begin - sl * per_slice) * T, buf_u32);
     }
     cp_async_commit();
     asm volatile("fence.proxy.async.shared::cta;");
@@ -389,7 +405,7 @@ tc16_pass_kernel(const Args a) {
         if (it + 1 < my_tiles) {
             const int sl = next / per_slice;
             resolve(a, sl, false, ld);
-            load_tile<LOGN, DIM>(a, ld.in, (next - sl * per_slice) * T,
+            load_tile<LOGN, DIM, NT>(a, ld.in, (next - sl * per_slice) * T,
                                  buf_u32 + (uint32_t)((cur ^ 1) * G::BUF_SLOTS * 8));
         }
         cp_async_commit();
@@ -422,18 +438,18 @@ tc16_pass_kernel(const Args a) {
             if (a.prologue == PRO_PRESCALE) {
                 const float pre = exp2i(kslice);
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = mul2_rn(d[slot<LOGN, DIM>(t, M * j + j2)], make_float2(pre, pre));
+                for (int j = 0; j < 16; j++) x[j] = mul2_rn(d[slot<LOGN, DIM, NT>(t, M * j + j2)], make_float2(pre, pre));
             } else {
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * j + j2)];
+                for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM, NT>(t, M * j + j2)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, mm.sb, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM, NT>(x, y, mm, mm.sb, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             const float4* tw = reinterpret_cast<const float4*>(sTwA + j2 * kTwRow);
 #pragma unroll
             for (int k = 0; k < 16; k += 2) {
                 const float4 w = tw[k >> 1];
-                d[slot<LOGN, DIM>(t, M * k + j2)] = cmul(make_float2(w.x, w.y), y[k]);
-                d[slot<LOGN, DIM>(t, M * (k + 1) + j2)] = cmul(make_float2(w.z, w.w), y[k + 1]);
+                d[slot<LOGN, DIM, NT>(t, M * k + j2)] = cmul(make_float2(w.x, w.y), y[k]);
+                d[slot<LOGN, DIM, NT>(t, M * (k + 1) + j2)] = cmul(make_float2(w.z, w.w), y[k + 1]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncthreads();
@@ -455,7 +471,7 @@ tc16_pass_kernel(const Args a) {
             else { t = v & (T - 1); p = v >> G::LGT; }
             float2 x[16], y[16];
             if (DIM == 1) {
-                const float4* g = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, 16 * p));
+                const float4* g = reinterpret_cast<const float4*>(d + slot_row<LOGN, NT>(t, 16 * p));
 #pragma unroll
                 for (int c = 0; c < 8; c++) {
                     const float4 q = g[c];
@@ -464,9 +480,9 @@ tc16_pass_kernel(const Args a) {
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = d[slot_col<LOGN>(t, 16 * p + j)];
+                for (int j = 0; j < 16; j++) x[j] = d[slot_col<LOGN, NT>(t, 16 * p + j)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, mm.sb8, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM, NT>(x, y, mm, mm.sb8, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
 #pragma unroll
             for (int k2 = 0; k2 < 8; k2++) {
                 const float2 v0 = scale_out ? scale2(y[k2], post) : y[k2];        // X[2 p + 16 k2]
@@ -501,7 +517,7 @@ tc16_pass_kernel(const Args a) {
             float2 x[16], y[16];
             if (DIM == 1 && r == 1) {
                 // own group of 16 consecutive elements, as 16-byte pairs
-                const float4* g = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, M * k1));
+                const float4* g = reinterpret_cast<const float4*>(d + slot_row<LOGN, NT>(t, M * k1));
 #pragma unroll
                 for (int c = 0; c < 8; c++) {
                     const float4 q = g[c];
@@ -510,9 +526,9 @@ tc16_pass_kernel(const Args a) {
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM>(t, M * k1 + r * j + j22)];
+                for (int j = 0; j < 16; j++) x[j] = d[slot<LOGN, DIM, NT>(t, M * k1 + r * j + j22)];
             }
-            dft16_round<FMT, DIM>(x, y, mm, mm.sb, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
+            dft16_round<FMT, DIM, NT>(x, y, mm, mm.sb, a.idesc, emax, !a.stall, a.g, G::LGT, sAm);
             if (r == 1) {
                 // X[k1 + 16 k2]
 #pragma unroll
@@ -528,8 +544,8 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int k = 0; k < 16; k += 2) {
                     const float4 w = tw[k >> 1];
-                    d[slot<LOGN, DIM>(t, M * k1 + r * k + j22)] = cmul(make_float2(w.x, w.y), y[k]);
-                    d[slot<LOGN, DIM>(t, M * k1 + r * (k + 1) + j22)] = cmul(make_float2(w.z, w.w), y[k + 1]);
+                    d[slot<LOGN, DIM, NT>(t, M * k1 + r * k + j22)] = cmul(make_float2(w.x, w.y), y[k]);
+                    d[slot<LOGN, DIM, NT>(t, M * k1 + r * (k + 1) + j22)] = cmul(make_float2(w.z, w.w), y[k + 1]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -548,16 +564,21 @@ tc16_pass_kernel(const Args a) {
             const float sg = a.inv ? 1.0f : -1.0f;         // W_4 = sg i
 #pragma unroll 2
             for (int i = 0; i < 4; i++) {
-                const int u = tid + i * kThreads;       // (t, k1, k21), T x 16 x 16
+                const int u = tid + i * NT;       // (t, k1, k21), T x 16 x 16
                 int t, k1, k21;
                 if (DIM == 1) { k1 = u & 15; k21 = (u >> 4) & 15; t = u >> 8; }
-                else { t = u & 3; k21 = 4 * ((u >> 2) & 3) + (u >> 8); k1 = (u >> 4) & 15; }
+                else if (T == 4) { t = u & 3; k21 = 4 * ((u >> 2) & 3) + (u >> 8); k1 = (u >> 4) & 15; }
+                else {   // T = 2 (NT = 128): the half-warp covers k21 bits 0, 2, 3
+                    t = u & 1;
+                    k21 = (((u >> 1) & 3) << 2) | ((u >> 3) & 1) | (((u >> 8) & 1) << 1);
+                    k1 = (u >> 4) & 15;
+                }
                 const int e = M * k1 + 4 * k21;
                 float2 U0, U1, U2, U3;
                 if (DIM == 1) {
                     // two 16-byte reads; lanes with k1 bit 2 set read the upper
                     // pair first, so a quarter-warp covers 8 distinct chunks
-                    const float4* q = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, e));
+                    const float4* q = reinterpret_cast<const float4*>(d + slot_row<LOGN, NT>(t, e));
                     const int par = (k1 >> 2) & 1;
                     const float4 f0 = q[par], f1 = q[par ^ 1];
                     const float4 lo = par ? f1 : f0, hi = par ? f0 : f1;
@@ -566,10 +587,10 @@ tc16_pass_kernel(const Args a) {
                     U2 = make_float2(hi.x, hi.y);
                     U3 = make_float2(hi.z, hi.w);
                 } else {
-                    U0 = d[slot_col<LOGN>(t, e)];
-                    U1 = d[slot_col<LOGN>(t, e + 1)];
-                    U2 = d[slot_col<LOGN>(t, e + 2)];
-                    U3 = d[slot_col<LOGN>(t, e + 3)];
+                    U0 = d[slot_col<LOGN, NT>(t, e)];
+                    U1 = d[slot_col<LOGN, NT>(t, e + 1)];
+                    U2 = d[slot_col<LOGN, NT>(t, e + 2)];
+                    U3 = d[slot_col<LOGN, NT>(t, e + 3)];
                 }
                 const float2 a0 = make_float2(__fadd_rn(U0.x, U2.x), __fadd_rn(U0.y, U2.y));
                 const float2 a1 = make_float2(__fsub_rn(U0.x, U2.x), __fsub_rn(U0.y, U2.y));
@@ -600,7 +621,7 @@ tc16_pass_kernel(const Args a) {
             const float c8 = 0.70710678118654752f;          // sqrt(1/2), rounded to FP32
 #pragma unroll 1
             for (int i = 0; i < 2; i++) {
-                const int u = tid + i * kThreads;       // (t, k1, k21), T x 16 x 16
+                const int u = tid + i * NT;       // (t, k1, k21), T x 16 x 16
                 int t, k1, k21;
                 if (DIM == 1) { k1 = u & 15; k21 = (u >> 4) & 15; t = u >> 8; }
                 else { t = u & 1; k21 = 2 * ((u >> 1) & 7) + (u >> 8); k1 = (u >> 4) & 15; }
@@ -610,7 +631,7 @@ tc16_pass_kernel(const Args a) {
                     // four 16-byte reads; a lane reads its chunks in the order
                     // c ^ x, x = (k1 >> 1) & 3, so a quarter-warp covers 8
                     // distinct chunks, then undoes the permutation
-                    const float4* q = reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, e));
+                    const float4* q = reinterpret_cast<const float4*>(d + slot_row<LOGN, NT>(t, e));
                     const int x = (k1 >> 1) & 3;
                     float4 f[4];
 #pragma unroll
@@ -630,7 +651,7 @@ tc16_pass_kernel(const Args a) {
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 8; j++) U[j] = d[slot_col<LOGN>(t, e + j)];
+                    for (int j = 0; j < 8; j++) U[j] = d[slot_col<LOGN, NT>(t, e + j)];
                 }
                 float2 E[4], O[4];
 #pragma unroll
@@ -675,19 +696,24 @@ tc16_pass_kernel(const Args a) {
             // ---- C2: radix-2 over j22: X[k1 + 16 (k21 + 16 k22)] ----------
 #pragma unroll 2
             for (int i = 0; i < 8; i++) {
-                const int u = tid + i * kThreads;       // (t, k1, k21), T x 16 x 16
+                const int u = tid + i * NT;       // (t, k1, k21), T x 16 x 16
                 int t, k1, k21;
                 if (DIM == 1) { k1 = u & 15; k21 = (u >> 4) & 15; t = u >> 8; }
-                else { t = u & 7; k21 = 8 * ((u >> 3) & 1) + (u >> 8); k1 = (u >> 4) & 15; }
+                else if (T == 8) { t = u & 7; k21 = 8 * ((u >> 3) & 1) + (u >> 8); k1 = (u >> 4) & 15; }
+                else {   // T = 4 (NT = 128): the half-warp covers k21 bits 0 and 3
+                    t = u & 3;
+                    k21 = (((u >> 2) & 1) << 3) | ((u >> 3) & 1) | (((u >> 8) & 3) << 1);
+                    k1 = (u >> 4) & 15;
+                }
                 const int e = M * k1 + 2 * k21;
                 float2 p, q;
                 if (DIM == 1) {
-                    const float4 pq = *reinterpret_cast<const float4*>(d + slot_row<LOGN>(t, e));
+                    const float4 pq = *reinterpret_cast<const float4*>(d + slot_row<LOGN, NT>(t, e));
                     p = make_float2(pq.x, pq.y);
                     q = make_float2(pq.z, pq.w);
                 } else {
-                    p = d[slot_col<LOGN>(t, e)];
-                    q = d[slot_col<LOGN>(t, e + 1)];
+                    p = d[slot_col<LOGN, NT>(t, e)];
+                    q = d[slot_col<LOGN, NT>(t, e + 1)];
                 }
                 float2 s0 = make_float2(__fadd_rn(p.x, q.x), __fadd_rn(p.y, q.y));
                 float2 s1 = make_float2(__fsub_rn(p.x, q.x), __fsub_rn(p.y, q.y));
@@ -721,16 +747,38 @@ tc16_pass_kernel(const Args a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(mm.tbase), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(mm.tbase), "r"(Cta<NT>::tmem_cols));
 }
 
-template <int FMT, int DIM, int LOGN, bool FOLD>
+// CTAs of one kernel instance that an SM holds at once: registers (allocated
+// per warp in units of 256), shared memory (with the per-CTA reservation),
+// tensor-memory columns and threads.
+template <int NT>
+int fit_per_sm(const void* k, size_t smem) {
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0, reserved = 0;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+        return 1;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = 65536 / ((NT / 32) * (warp_regs > 0 ? warp_regs : 256));
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+    const int by_tmem = 512 / (int)Cta<NT>::tmem_cols;
+    int fit = by_regs < by_smem ? by_regs : by_smem;
+    fit = fit < by_tmem ? fit : by_tmem;
+    fit = fit < 2048 / NT ? fit : 2048 / NT;
+    return fit > 0 ? fit : 1;
+}
+
+template <int FMT, int DIM, int LOGN, bool FOLD, int NT>
 cudaError_t launch_inst(const Args& a, int cps, cudaStream_t s) {
-    using G = Geo<LOGN>;
-    const size_t smem = kOffBuf + 2 * (size_t)G::BUF_SLOTS * sizeof(float2);
-    void (*k)(const Args) = tc16_pass_kernel<FMT, DIM, LOGN, FOLD>;
-    // per kernel instance: shared-memory opt-in and the SM count
-    static int sms = 0;
+    using G = Geo<LOGN, NT>;
+    const size_t smem = G::SMEM;
+    void (*k)(const Args) = tc16_pass_kernel<FMT, DIM, LOGN, FOLD, NT>;
+    // per kernel instance: shared-memory opt-in, the SM count and the CTAs
+    // an SM holds
+    static int sms = 0, fit = 0;
     if (sms == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
@@ -741,36 +789,43 @@ cudaError_t launch_inst(const Args& a, int cps, cudaStream_t s) {
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
+        fit = fit_per_sm<NT>((const void*)k, smem);
         sms = count;
     }
-    // the shared-memory and register budgets hold 2 CTAs per SM, as
-    // __launch_bounds__ asks (the occupancy query, which does not see that
-    // the kernel's tensor memory fits twice, reports 1)
-    const int per_sm = cps >= 1 && cps <= kTc16MaxCtasPerSm ? cps : kTc16MaxCtasPerSm;
+    // the persistent grid: cps CTAs per SM when given (at most what fits),
+    // else all that fit (256 threads: 2)
+    const int per_sm = cps >= 1 && cps <= fit ? cps : fit;
     const int resident = per_sm * sms;
     const int other = DIM == 1 ? a.n0 : a.n1;
     const int ntiles = a.batch * (other / G::T);
     const int blocks = ntiles < resident ? ntiles : resident;
-    k<<<blocks, kThreads, smem, s>>>(a);
+    k<<<blocks, NT, smem, s>>>(a);
     note_launch();
     return cudaGetLastError();
 }
 
+// tile: 2048 for the 128-thread CTAs (n <= 1024), else the 256-thread ones
 template <int FMT, int DIM, int LOGN>
-cudaError_t launch_one(const Args& a, int cps, cudaStream_t s) {
-    if (DIM == 0 && LOGN <= 10 && a.stats_out)
-        return launch_inst<FMT, 0, (LOGN <= 10 ? LOGN : 10), true>(a, cps, s);
-    return launch_inst<FMT, DIM, LOGN, false>(a, cps, s);
+cudaError_t launch_one(const Args& a, int cps, int tile, cudaStream_t s) {
+    constexpr int L = LOGN <= 10 ? LOGN : 10;     // instances that exist for the fold / 128 threads
+    const bool fold = DIM == 0 && LOGN <= 10 && a.stats_out;
+    if (LOGN <= 10 && tile == 2048)
+        return fold ? launch_inst<FMT, 0, L, true, 128>(a, cps, s) : launch_inst<FMT, DIM, L, false, 128>(a, cps, s);
+    return fold ? launch_inst<FMT, 0, L, true, 256>(a, cps, s) : launch_inst<FMT, DIM, LOGN, false, 256>(a, cps, s);
 }
 
 template <int FMT>
-cudaError_t launch_fmt(const Args& a, int cps, cudaStream_t s) {
+cudaError_t launch_fmt(const Args& a, int cps, int tile, cudaStream_t s) {
     const bool rows = a.dim == 1;
-    if (a.n == 128) return rows ? launch_one<FMT, 1, 7>(a, cps, s) : launch_one<FMT, 0, 7>(a, cps, s);
-    if (a.n == 256) return rows ? launch_one<FMT, 1, 8>(a, cps, s) : launch_one<FMT, 0, 8>(a, cps, s);
-    if (a.n == 512) return rows ? launch_one<FMT, 1, 9>(a, cps, s) : launch_one<FMT, 0, 9>(a, cps, s);
-    if (a.n == 1024) return rows ? launch_one<FMT, 1, 10>(a, cps, s) : launch_one<FMT, 0, 10>(a, cps, s);
-    return rows ? launch_one<FMT, 1, 11>(a, cps, s) : launch_one<FMT, 0, 11>(a, cps, s);
+    if (a.n == 128)
+        return rows ? launch_one<FMT, 1, 7>(a, cps, tile, s) : launch_one<FMT, 0, 7>(a, cps, tile, s);
+    if (a.n == 256)
+        return rows ? launch_one<FMT, 1, 8>(a, cps, tile, s) : launch_one<FMT, 0, 8>(a, cps, tile, s);
+    if (a.n == 512)
+        return rows ? launch_one<FMT, 1, 9>(a, cps, tile, s) : launch_one<FMT, 0, 9>(a, cps, tile, s);
+    if (a.n == 1024)
+        return rows ? launch_one<FMT, 1, 10>(a, cps, tile, s) : launch_one<FMT, 0, 10>(a, cps, tile, s);
+    return rows ? launch_one<FMT, 1, 11>(a, cps, tile, s) : launch_one<FMT, 0, 11>(a, cps, tile, s);
 }
 
 }  // namespace tc16
@@ -779,23 +834,25 @@ bool tc16_supported(int n, int other, int fmt) {
     // n = 128 or 256 r (r = 1, 2, 4, 8), 8-bit element formats, whole tiles of
     // 4096 / n transforms
     if (n != 128 && n != 256 && n != 512 && n != 1024 && n != 2048) return false;
-    const int T = tc16::kTilePts / n;
+    const int T = 4096 / n;
     return other >= T && other % T == 0 && (fmt == 0 || fmt == 1);
 }
 
-cudaError_t launch_tc16_pass_ctas(const Tc16Args& a, int fmt, int batch, int ctas_per_sm,
-                                  cudaStream_t s) {
+cudaError_t launch_tc16_pass_geo(const Tc16Args& a, int fmt, int batch, int tile, int ctas_per_sm,
+                                 cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
     Tc16Args b = a;
     b.batch = batch;
-    if (fmt == 0) return tc16::launch_fmt<0>(b, ctas_per_sm, s);
-    if (fmt == 1) return tc16::launch_fmt<1>(b, ctas_per_sm, s);
+    if (fmt == 0) return tc16::launch_fmt<0>(b, ctas_per_sm, tile, s);
+    if (fmt == 1) return tc16::launch_fmt<1>(b, ctas_per_sm, tile, s);
     return cudaErrorNotSupported;
 }
 
 cudaError_t launch_tc16_pass(const Tc16Args& a, int fmt, int batch, cudaStream_t s) {
     const int other = a.dim == 1 ? a.n0 : a.n1;
-    return launch_tc16_pass_ctas(a, fmt, batch, tc16_ctas_tuned(a.n, other, a.dim, fmt, a.g, batch), s);
+    int tile = 0, cps = 0;
+    tc16_geo_tuned(a.n, other, a.dim, fmt, a.g, batch, &tile, &cps);
+    return launch_tc16_pass_geo(a, fmt, batch, tile, cps, s);
 }
 
 MX_BOUNDS_COUNTER(tc16)

@@ -1,6 +1,7 @@
 // Launch-geometry autotuner.  Register-resident radix-2 pass: the number of
-// transform groups per CTA; tensor-core pass: the resident CTAs per SM of its
-// persistent grid (1 or 2).  Each is measured per (transform length, other
+// transform groups per CTA; tensor-core pass: the tile (4096 points on 256
+// threads, or 2048 on 128) and the resident CTAs per SM of its persistent
+// grid.  Each is measured per (transform length, other
 // extent, axis, element format, block size, batch class) and the fastest kept
 // in a process-wide table, which the launchers consult and which can be saved
 // to / merged from a JSON file.  Every geometry computes the same bits: each
@@ -36,6 +37,7 @@ using Key = std::tuple<int, int, int, int, int, int, int>;
 struct Val {
     int ng;        // groups per CTA, or CTAs per SM
     double us;
+    int tile = 0;  // tensor-core pass: points per tile
 };
 
 std::mutex g_mu;
@@ -79,17 +81,18 @@ double time_ng(mxfft_plan_s* p, const PassArgs& a, int batch, int ng, cudaStream
     return us;
 }
 
-// The same for the tensor-core pass with ctas CTAs per SM.
-double time_tc16(const Tc16Args& t, int fmt, int batch, int ctas, cudaStream_t s, int warm, int reps) {
+// The same for the tensor-core pass with its tile and ctas CTAs per SM.
+double time_tc16(const Tc16Args& t, int fmt, int batch, int tile, int ctas, cudaStream_t s, int warm,
+                 int reps) {
     for (int i = 0; i < warm; i++)
-        if (launch_tc16_pass_ctas(t, fmt, batch, ctas, s) != cudaSuccess) return -1.0;
+        if (launch_tc16_pass_geo(t, fmt, batch, tile, ctas, s) != cudaSuccess) return -1.0;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
     double us = -1.0;
     cudaEventRecord(e0, s);
     bool ok = true;
-    for (int i = 0; i < reps && ok; i++) ok = launch_tc16_pass_ctas(t, fmt, batch, ctas, s) == cudaSuccess;
+    for (int i = 0; i < reps && ok; i++) ok = launch_tc16_pass_geo(t, fmt, batch, tile, ctas, s) == cudaSuccess;
     cudaEventRecord(e1, s);
     float ms = 0.f;
     if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
@@ -130,15 +133,17 @@ void fast_ng_store(int n, int other, int dim, int fmt, int m, int batch, int ng,
     table()[Key(n, other, dim, fmt, m, batch_class(batch), 0)] = Val{ng, us};
 }
 
-int tc16_ctas_tuned(int n, int other, int dim, int fmt, int g, int batch) {
+void tc16_geo_tuned(int n, int other, int dim, int fmt, int g, int batch, int* tile, int* ctas) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = table().find(Key(n, other, dim, fmt, g, batch_class(batch), 1));
-    return it == table().end() ? 0 : it->second.ng;
+    *tile = it == table().end() ? 0 : it->second.tile;
+    *ctas = it == table().end() ? 0 : it->second.ng;
 }
 
-void tc16_ctas_store(int n, int other, int dim, int fmt, int g, int batch, int ctas, double us) {
+void tc16_geo_store(int n, int other, int dim, int fmt, int g, int batch, int tile, int ctas,
+                    double us) {
     std::lock_guard<std::mutex> lk(g_mu);
-    table()[Key(n, other, dim, fmt, g, batch_class(batch), 1)] = Val{ctas, us};
+    table()[Key(n, other, dim, fmt, g, batch_class(batch), 1)] = Val{ctas, us, tile};
 }
 
 }  // namespace mxfft
@@ -172,16 +177,21 @@ int mxfft_tune(mxfft_plan_t p, int batch, void* stream, int* n_measured) {
         a.epilogue = dim == 1 ? EPI_RAW : EPI_UNSCALE;
         const int other = dim == 1 ? p->n0 : p->n1;
         if (p->path == 1) {
+            // 256 threads: 1 or 2 CTAs per SM; 128 threads (n <= 1024): 2 to 6
             const Tc16Args t = tc16_args(p, a, 0);
-            int best = 0;
+            const int cand[][2] = {{4096, 1}, {4096, 2}, {2048, 2}, {2048, 3}, {2048, 4}, {2048, 5},
+                                   {2048, 6}};
+            int best = -1;
             double best_us = 0.0;
-            for (int c = 1; c <= kTc16MaxCtasPerSm; c++) {
-                const double us = time_tc16(t, p->fmt, batch, c, s, 2, 5);
+            for (int i = 0; i < 7 && rc == MXFFT_OK; i++) {
+                if (cand[i][0] == 2048 && a.n > 1024) continue;
+                const double us = time_tc16(t, p->fmt, batch, cand[i][0], cand[i][1], s, 2, 5);
                 if (us < 0) { rc = MXFFT_ERR_CUDA; break; }
                 measured++;
-                if (best == 0 || us < best_us) { best = c; best_us = us; }
+                if (best < 0 || us < best_us) { best = i; best_us = us; }
             }
-            if (rc == MXFFT_OK) tc16_ctas_store(a.n, other, dim, p->fmt, t.g, batch, best, best_us);
+            if (rc == MXFFT_OK && best >= 0)
+                tc16_geo_store(a.n, other, dim, p->fmt, t.g, batch, cand[best][0], cand[best][1], best_us);
             continue;
         }
         if (!fast_pass_supported(a)) continue;
@@ -217,10 +227,12 @@ int mxfft_tune_save(const char* path) {
             if (std::get<6>(kv.first) == 1)
                 std::snprintf(buf, sizeof buf,
                               "%s\n  {\"kind\": 1, \"n\": %d, \"other\": %d, \"dim\": %d, \"fmt\": %d, "
-                              "\"m\": %d, \"batch_class\": %d, \"ctas_per_sm\": %d, \"us\": %.3f}",
+                              "\"m\": %d, \"batch_class\": %d, \"tile\": %d, \"ctas_per_sm\": %d, "
+                              "\"us\": %.3f}",
                               first ? "" : ",", std::get<0>(kv.first), std::get<1>(kv.first),
                               std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first),
-                              std::get<5>(kv.first), kv.second.ng, kv.second.us);
+                              std::get<5>(kv.first), kv.second.tile ? kv.second.tile : 4096, kv.second.ng,
+                              kv.second.us);
             else
                 std::snprintf(buf, sizeof buf,
                               "%s\n  {\"n\": %d, \"other\": %d, \"dim\": %d, \"fmt\": %d, \"m\": %d, "
@@ -256,7 +268,7 @@ int mxfft_tune_load(const char* path) {
         const size_t end = text.find('}', at);
         if (end == std::string::npos) return MXFFT_ERR_INVALID;
         const std::string obj = text.substr(at, end - at + 1);
-        long n, other, dim, fmt, m, bc, ng, kind = 0;
+        long n, other, dim, fmt, m, bc, ng, kind = 0, tile = 4096;
         if (json_int(obj, "kind", &kind) && kind != 0 && kind != 1) return MXFFT_ERR_INVALID;
         if (!json_int(obj, "n", &n) || !json_int(obj, "other", &other) || !json_int(obj, "dim", &dim) ||
             !json_int(obj, "fmt", &fmt) || !json_int(obj, "m", &m) ||
@@ -264,8 +276,9 @@ int mxfft_tune_load(const char* path) {
             return MXFFT_ERR_INVALID;
         bool valid = false;
         if (kind == 1) {
+            json_int(obj, "tile", &tile);
             valid = ng >= 1 && ng <= kTc16MaxCtasPerSm && tc16_supported((int)n, (int)other, (int)fmt) &&
-                    (m == 1 || m == 2 || m == 4);
+                    (m == 1 || m == 2 || m == 4) && (tile == 4096 || (tile == 2048 && n <= 1024));
         } else {
             int cand[16];
             const int nc = fast_ng_candidates((int)n, (int)other, (int)m, cand, 16);
@@ -273,7 +286,7 @@ int mxfft_tune_load(const char* path) {
         }
         if (!valid || (dim != 0 && dim != 1) || bc < 0 || bc > 30) return MXFFT_ERR_INVALID;
         parsed.push_back({Key((int)n, (int)other, (int)dim, (int)fmt, (int)m, (int)bc, (int)kind),
-                          Val{(int)ng, 0.0}});
+                          Val{(int)ng, 0.0, kind == 1 ? (int)tile : 0}});
         at = end + 1;
     }
     std::lock_guard<std::mutex> lk(g_mu);

@@ -65,7 +65,7 @@ def test_tuning_file_round_trip(lib, tmp_path):
     assert {k: got[0][k] for k in entry if k != "us"} == {k: entry[k] for k in entry if k != "us"}
     # a tensor-core entry (resident CTAs per SM of its persistent grid) beside it
     tc = {"kind": 1, "n": 512, "other": 512, "dim": 0, "fmt": 0, "m": 1, "batch_class": 9,
-          "ctas_per_sm": 1, "us": 2.0}
+          "tile": 2048, "ctas_per_sm": 4, "us": 2.0}
     f.write_text(json.dumps({"mxfft_tune": 1, "entries": [tc]}))
     mxfft.mxfft_tune_load(str(f))
     mxfft.mxfft_tune_save(str(out))
@@ -88,7 +88,11 @@ def test_tuning_file_round_trip(lib, tmp_path):
     '{"mxfft_tune": 1, "entries": [{"n": 256, "other": 256, "dim": 1, "fmt": 0, "m": 16,'
     ' "batch_class": 6, "ng": 8}]}',                                       # 1024 threads
     '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 512, "other": 512, "dim": 1, "fmt": 0,'
-    ' "m": 1, "batch_class": 6, "ctas_per_sm": 3}]}',                      # above 2 per SM
+    ' "m": 1, "batch_class": 6, "ctas_per_sm": 9}]}',                      # above 8 per SM
+    '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 2048, "other": 512, "dim": 1, "fmt": 0,'
+    ' "m": 1, "batch_class": 6, "tile": 2048, "ctas_per_sm": 4}]}',        # 128 threads, n > 1024
+    '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 512, "other": 512, "dim": 1, "fmt": 0,'
+    ' "m": 1, "batch_class": 6, "tile": 1024, "ctas_per_sm": 4}]}',        # no such tile
     '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 64, "other": 512, "dim": 1, "fmt": 0,'
     ' "m": 1, "batch_class": 6, "ctas_per_sm": 1}]}',                      # no tensor-core pass
     '{"mxfft_tune": 1, "entries": [{"kind": 1, "n": 512, "other": 512, "dim": 1, "fmt": 2,'

@@ -163,29 +163,38 @@ def test_tuned_geometries_give_the_same_bits(k, cuda_device, tmp_path):
     mxfft.mxfft_tune_clear()
 
 
-@pytest.mark.parametrize("n0,n1,batch", [(512, 512, 24), (128, 1024, 9)])
-def test_tuned_tensor_core_grid_gives_the_same_bits(n0, n1, batch, cuda_device, tmp_path):
-    # the tensor-core pass's persistent grid with 1 or 2 CTAs per SM: every
-    # CTA count walks the same tiles with the same arithmetic
+@pytest.mark.parametrize("n0,n1,batch,fmt,k", [(512, 512, 24, "e4m3", 32), (128, 1024, 9, "e5m2", 32),
+                                               (1024, 256, 5, "e4m3", 64), (256, 512, 7, "e4m3", 128),
+                                               (128, 128, 33, "e5m2", 64), (2048, 512, 2, "e4m3", 32)])
+def test_tuned_tensor_core_geometry_gives_the_same_bits(n0, n1, batch, fmt, k, cuda_device, tmp_path):
+    # the tensor-core pass on 256-thread CTAs (4096-point tiles) with 1 or 2
+    # CTAs per SM and on 128-thread CTAs (2048-point tiles, n <= 1024) with 2
+    # to 6: every geometry gives each vector, MX block and product the same
+    # arithmetic
     import torch
 
     from paper_2512_04317_gb300 import mxfft
     x = torch.from_numpy(phantom.mri_batch(n0, n1, batch, 1, config_id=43, domain="image")).cuda()
     mxfft.mxfft_tune_clear()
-    with mxfft.Plan(n0, n1, "e4m3", 32, path="tc16") as p:
+    with mxfft.Plan(n0, n1, fmt, k, path="tc16") as p:
         want = p.roundtrip(x).cpu().numpy()
-        assert mxfft.mxfft_tune(p.handle, batch) == 4          # 2 CTA counts x 2 axes
+        fwd = p.forward(x).cpu().numpy()
+        n_small = sum(1 for n in (n0, n1) if n <= 1024)
+        assert mxfft.mxfft_tune(p.handle, batch) == 2 * 2 + 5 * n_small
         path = tmp_path / "tune.json"
         mxfft.mxfft_tune_save(str(path))
         entries = json.loads(path.read_text())["entries"]
         assert {(e["kind"], e["dim"]) for e in entries} == {(1, 0), (1, 1)}
-        for ctas in (1, 2):
+        for tile, ctas in ((4096, 1), (4096, 2), (2048, 2), (2048, 3), (2048, 4), (2048, 6)):
             for e in entries:
-                e["ctas_per_sm"] = ctas
+                e["tile"] = tile if e["n"] <= 1024 else 4096
+                e["ctas_per_sm"] = ctas if e["tile"] == tile else 2
             path.write_text(json.dumps({"mxfft_tune": 1, "entries": entries}))
             mxfft.mxfft_tune_load(str(path))
             np.testing.assert_array_equal(p.roundtrip(x).cpu().numpy().view(np.uint32),
                                           want.view(np.uint32))
+            np.testing.assert_array_equal(p.forward(x).cpu().numpy().view(np.uint32),
+                                          fwd.view(np.uint32))
             assert p.status()[1] == 0
     mxfft.mxfft_tune_clear()
 

@@ -61,19 +61,22 @@ def test_eight_point_pair_matrix(fmt):
     assert np.abs(F[:16, :16] - R).max() <= step / 2 + 1e-12
 
 
-# ---- n = 128 geometry of the kernel ----------------------------------------
-THREADS, TILE = 256, 4096
-N, T, M = 128, 32, 8
+# ---- n = 128 geometry of the kernel (both CTA shapes) ----------------------
+N, M = 128, 8
 TS, PADR, LGP = N + 2 * (N >> 4) + 8, 2, 4        # rows: pads after every 16 elements
-BUF_SLOTS = max(T * TS, N * T)
 
 
-def slot_row(t, e):
+def geo(nt):
+    T = 16 * nt // N
+    return dict(NT=nt, T=T, LGT=T.bit_length() - 1, BUF=max(T * TS, N * T))
+
+
+def slot_row(g, t, e):
     return t * TS + e + PADR * (e >> LGP)
 
 
-def slot_col(t, e):
-    return e * T + t
+def slot_col(g, t, e):
+    return e * g["T"] + t
 
 
 def wavefronts(byte_addrs, width):
@@ -89,66 +92,75 @@ def wavefronts(byte_addrs, width):
     return max(len(v) for v in per_bank.values())
 
 
-def check_access(addrs_per_lane, width):
+def check_access(g, addrs_per_lane, width):
     """addrs_per_lane: slot index (8-byte units) per thread for one access."""
-    for w0 in range(0, THREADS, 32):
+    for w0 in range(0, g["NT"], 32):
         lanes = [addrs_per_lane[w0 + i] * 8 for i in range(32)]
-        assert all(0 <= a and a + width <= BUF_SLOTS * 8 for a in lanes)
+        assert all(0 <= a and a + width <= g["BUF"] * 8 for a in lanes)
         assert all(a % width == 0 for a in lanes), "aligned vector access"
         need = 32 * width // 128
         assert wavefronts(lanes, width) == need, (w0, wavefronts(lanes, width), need)
 
 
-def test_geometry_and_shared_memory():
-    assert T * M == THREADS
-    off_buf = 8192 + 1024 + 128 * 18 * 8 + 8 * 18 * 8
-    smem = off_buf + 2 * BUF_SLOTS * 8
-    # two CTAs per SM: 2 x (dynamic + 1152 static + 1024 reserved) <= 228 KB
-    assert 2 * (smem + 1152 + 1024) <= 228 * 1024
+@pytest.mark.parametrize("nt", [256, 128])
+def test_geometry_and_shared_memory(nt):
+    g = geo(nt)
+    assert g["T"] * M == nt
+    off_buf = (nt * 32 + 1024 + M * 18 * 8 + 8 * 18 * 8 + 127) // 128 * 128
+    smem = off_buf + 2 * g["BUF"] * 8
+    per_sm = 2 if nt == 256 else 4
+    # per_sm CTAs on an SM: per_sm x (dynamic + static + 1024 reserved) <= 228 KB
+    assert per_sm * (smem + 1152 + 1024) <= 228 * 1024
     # the 8-point pair matrix (1 KB) fits the unused C2 twiddle rows
     assert 8 * 18 * 8 >= 1024
 
 
+@pytest.mark.parametrize("nt", [256, 128])
 @pytest.mark.parametrize("dim", [1, 0])
-def test_tile_copies(dim):
-    seen = np.zeros(BUF_SLOTS, int)
+def test_tile_copies(dim, nt):
+    g = geo(nt)
+    T, NT = g["T"], nt
+    seen = np.zeros(g["BUF"], int)
     for i in range(8):
         addrs = []
-        for tid in range(THREADS):
-            q = tid + i * THREADS
+        for tid in range(NT):
+            q = tid + i * NT
             if dim == 1:
                 t, e = q >> 6, 2 * (q & 63)
-                s = slot_row(t, e)
+                s = slot_row(g, t, e)
             else:
-                e, t = q >> 4, 2 * (q & 15)
-                s = slot_col(t, e)
+                e, t = q >> (g["LGT"] - 1), 2 * (q & (T // 2 - 1))
+                s = slot_col(g, t, e)
             addrs.append(s)
             seen[s] += 1
             seen[s + 1] += 1
-        check_access(addrs, 16)
+        check_access(g, addrs, 16)
     # every element of the tile lands once
-    slots = [slot_row(t, e) if dim == 1 else slot_col(t, e) for t in range(T) for e in range(N)]
+    slots = [slot_row(g, t, e) if dim == 1 else slot_col(g, t, e) for t in range(T) for e in range(N)]
     assert sorted(slots) == sorted(np.nonzero(seen)[0].tolist())
     assert seen.max() == 1
 
 
+@pytest.mark.parametrize("nt", [256, 128])
 @pytest.mark.parametrize("dim", [1, 0])
-def test_round_a_and_eight_point_round(dim):
-    slot = slot_row if dim == 1 else slot_col
-    written = np.zeros(BUF_SLOTS, int)
+def test_round_a_and_eight_point_round(dim, nt):
+    g = geo(nt)
+    T, NT = g["T"], nt
+    slot = (lambda t, e: slot_row(g, t, e)) if dim == 1 else (lambda t, e: slot_col(g, t, e))
+    written = np.zeros(g["BUF"], int)
     for j in range(16):                      # round A: read x[M j + j2], write Y[M k1 + j2]
         addrs = []
-        for v in range(THREADS):
-            t, j2 = (v >> 3, v & 7) if dim == 1 else (v & 31, v >> 5)
+        for v in range(NT):
+            t, j2 = (v >> 3, v & 7) if dim == 1 else (v & (T - 1), v >> g["LGT"])
             addrs.append(slot(t, M * j + j2))
             written[slot(t, M * j + j2)] += 1
-        check_access(addrs, 8)
+        check_access(g, addrs, 8)
     assert written.sum() == T * N and written.max() == 1
-    read = np.zeros(BUF_SLOTS, int)
+    read = np.zeros(g["BUF"], int)
     if dim == 1:                             # 8-point round: 8 16-byte pairs per thread
         for c in range(8):
             addrs = []
-            for v in range(THREADS):
+            for v in range(NT):
                 t, p = v >> 3, v & 7
                 addrs.append(slot(t, 16 * p) + 2 * c)
                 for h in range(2):
@@ -156,13 +168,13 @@ def test_round_a_and_eight_point_round(dim):
                 # the pair is elements 16 p + 2 c, + 1: contiguous in the layout
                 assert slot(t, 16 * p) + 2 * c == slot(t, 16 * p + 2 * c)
                 assert slot(t, 16 * p + 2 * c) + 1 == slot(t, 16 * p + 2 * c + 1)
-            check_access(addrs, 16)
+            check_access(g, addrs, 16)
     else:
         for j in range(16):
             addrs = []
-            for v in range(THREADS):
-                t, p = v & 31, v >> 5
+            for v in range(NT):
+                t, p = v & (T - 1), v >> g["LGT"]
                 addrs.append(slot(t, 16 * p + j))
                 read[slot(t, 16 * p + j)] += 1
-            check_access(addrs, 8)
+            check_access(g, addrs, 8)
     np.testing.assert_array_equal(read, written)

@@ -80,9 +80,10 @@ typedef enum {
                                16-point input vector one MX block for k = 32 (k = 64 / 128: a
                                block of 2 / 4 consecutive vectors of a transform; other k
                                MXFFT_ERR_UNSUPPORTED), MX-quantised twiddles between the
-                               radix-16 stages; approximate, not bit-exact.
-                               Needs n0, n1 in {256, 512, 1024, 2048} and format E4M3 or E5M2, else
-                               MXFFT_ERR_UNSUPPORTED. */,
+                               radix-16 stages (n = 128: 16 x 8, the 8-point DFTs of the second
+                               round two per matrix row); approximate, not bit-exact.
+                               Needs n0, n1 in {128, 256, 512, 1024, 2048} and format E4M3 or
+                               E5M2, else MXFFT_ERR_UNSUPPORTED. */,
     MXFFT_OPT_TEST_STALL = 5, /* test hook of the bounded wait, 0 or 1; default 0.  1: the
                                tensor-core kernels withhold their matrix products, so every
                                CTA's wait for their completion runs out (after 100 ms), the CTA

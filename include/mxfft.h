@@ -63,7 +63,13 @@ typedef enum {
                          in FP32.  k is ignored; tau_min default 2^-24 (binary16's smallest
                          magnitude), so the prescale sets the peak to the target and stage
                          values stay below n0 n1 target (no overflow up to 256x256 at
-                         target 0.5); products overflow to infinity above 65504. */
+                         target 0.5); products overflow to infinity above 65504. */,
+    MXFFT_FP32_REF = 6 /* reference ablation, not an MX format: the same prescale, radix-2
+                         dataflow and unscale with no quantisation -- twiddles rounded once to
+                         FP32 (exact at multiples of pi/4), the butterfly's complex product and
+                         u +- wv in FP32, each operation rounded once -- so that its distance
+                         to an MX format's result is the quantisation error alone.  Default
+                         tau_min 2^-126.  Radix-2 path only. */
 } mxfft_format;
 
 /* Keys of mxfft_set_option. */

@@ -32,11 +32,13 @@ _SRC = os.path.join(_HERE, "mxfft_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle_mxfft.so")
 
-FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
+FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5, "fp32": 6}
 # tau_min defaults: 2^-10 for e4m3 and 2^-12 for e5m2 (Alg. 1 notes); 2^-10 for
-# the FP6/FP4 formats, where the paper gives none.
+# the FP6/FP4 formats, where the paper gives none; the smallest binary16
+# magnitude for the FP16 control and binary32's smallest normal for the FP32
+# reference ablation.
 TAU_MIN_DEFAULT = {"e4m3": 2.0**-10, "e5m2": 2.0**-12, "e2m3": 2.0**-10,
-                   "e3m2": 2.0**-10, "e2m1": 2.0**-10, "fp16": 2.0**-24}
+                   "e3m2": 2.0**-10, "e2m1": 2.0**-10, "fp16": 2.0**-24, "fp32": 2.0**-126}
 OP = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}
 
 _lock = threading.Lock()

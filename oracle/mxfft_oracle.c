@@ -24,6 +24,8 @@
  *   - The root-sum-of-squares coil combine of Eq. (1) (oracle_rss).
  *   - The FP16 positive control of Sec. 2.2 (format code 5): the same dataflow
  *     with binary16 inputs and outputs and binary16 twiddle products.
+ *   - An FP32 reference ablation (format code 6, reading C18): the same
+ *     prescale and radix-2 dataflow with no quantisation at all.
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   C1 k1 uses round-to-nearest; target and tau_min are powers of two.
@@ -61,6 +63,12 @@
  *       transforms; only the inverse's axis order and the missing second
  *       prescale change the result.  Not defined for the FP16 control (its
  *       binary16 products would overflow at the unscaled intermediate size).
+ *   C18 the FP32 reference ablation separates the quantisation error from
+ *       FP32 rounding: Alg. 1's prescale (default tau_min 2^-126, binary32's
+ *       smallest normal) and unscale, bit reversal and the same butterflies,
+ *       with the twiddle rounded once from FP64 to FP32 (exact values at the
+ *       multiples of pi/4) and the product (wr vr - wi vi, wr vi + wi vr)
+ *       and u +- wv in FP32, each operation rounded once.
  *
  * Floating-point contract: compile with -ffp-contract=off and without
  * fast-math.  Every FP32 result below is one IEEE operation on FP32 operands.
@@ -85,6 +93,7 @@ typedef struct {
     int emin;       /* unbiased exponent of the smallest normal: 1 - bias */
     double maxnorm; /* largest finite magnitude */
     int fp16;       /* 1: the FP16 positive control, not an MX element format */
+    int fp32;       /* 1: the FP32 reference ablation (no quantisation) */
 } elem_fmt;
 
 /* Format codes shared with the Python wrapper: 0 E4M3, 1 E5M2, 2 E2M3,
@@ -111,10 +120,13 @@ static int get_fmt(int code, elem_fmt *f)
             f->maxnorm = ldexp(1.0 + 1.0 / 2.0, f->emax); break;
     case 5: f->ebits = 5; f->mbits = 10; f->bias = 15; f->emax = 30 - 15;   /* IEEE binary16 */
             f->maxnorm = ldexp(2.0 - 1.0 / 1024.0, f->emax); break;
+    case 6: f->ebits = 8; f->mbits = 23; f->bias = 127; f->emax = 254 - 127;   /* IEEE binary32 */
+            f->maxnorm = ldexp(2.0 - ldexp(1.0, -23), f->emax); break;
     default: return -1;
     }
     f->emin = 1 - f->bias;
     f->fp16 = code == 5;
+    f->fp32 = code == 6;
     return 0;
 }
 
@@ -349,6 +361,41 @@ static void fp16_butterflies(int nb, const float *U, const float *V, const doubl
     }
 }
 
+/* exp(i sgn pi j / h), 0 <= j < h: the exact values 0, +-1, +-sqrt(1/2) at
+ * the multiples of pi/4 (where cos / sin of the rounded angle would leave a
+ * residue such as 6e-17 that FP32 keeps), cos / sin of pi j / h elsewhere. */
+static void exact_twiddle(int j, int h, double sgn, double *c, double *s)
+{
+    if ((4L * j) % h == 0) {
+        const double r = sqrt(0.5);
+        const double cs[4] = {1.0, r, 0.0, -r}, sn[4] = {0.0, r, 1.0, r};
+        int o = (int)(4L * j / h);      /* angle = o pi / 4, o = 0..3 */
+        *c = cs[o];
+        *s = sgn * sn[o];
+        return;
+    }
+    double ang = M_PI * (double)j / (double)h;
+    *c = cos(ang);
+    *s = sgn * sin(ang);
+}
+
+/* FP32 reference ablation (reading C18): the twiddle rounded once to FP32,
+ * the complex product and u +- wv in FP32, every operation rounded once. */
+static void fp32_butterflies(int nb, const float *U, const float *V, const double *Wr,
+                             const double *Wi, float *Y0, float *Y1)
+{
+    for (int b = 0; b < nb; b++) {
+        float wr = (float)Wr[b], wi = (float)Wi[b];
+        float vr = V[2 * b], vi = V[2 * b + 1];
+        float a = wr * vr, bb = wi * vi, c = wr * vi, d = wi * vr;
+        float pr = a - bb, pi = c + d;
+        Y0[2 * b] = U[2 * b] + pr;
+        Y0[2 * b + 1] = U[2 * b + 1] + pi;
+        Y1[2 * b] = U[2 * b] - pr;
+        Y1[2 * b + 1] = U[2 * b + 1] - pi;
+    }
+}
+
 /* A: n complex values (interleaved FP32), transformed in place. */
 static void fft1d_mx(float *A, int n, int kblk, int inverse, const elem_fmt *f,
                      const bf_opts *o, fft_ws *ws)
@@ -374,12 +421,18 @@ static void fft1d_mx(float *A, int n, int kblk, int inverse, const elem_fmt *f,
             ws->U[2 * b + 1] = A[2 * iu + 1];
             ws->V[2 * b] = A[2 * iv];
             ws->V[2 * b + 1] = A[2 * iv + 1];
-            double ang = M_PI * (double)j / (double)h;   /* 2 pi j / (2h) */
-            ws->Wr[b] = cos(ang);
-            ws->Wi[b] = sgn * sin(ang);
+            if (f->fp32) {
+                exact_twiddle(j, h, sgn, &ws->Wr[b], &ws->Wi[b]);
+            } else {
+                double ang = M_PI * (double)j / (double)h;   /* 2 pi j / (2h) */
+                ws->Wr[b] = cos(ang);
+                ws->Wi[b] = sgn * sin(ang);
+            }
         }
         if (f->fp16) {
             fp16_butterflies(nbf, ws->U, ws->V, ws->Wr, ws->Wi, ws->Y0, ws->Y1);
+        } else if (f->fp32) {
+            fp32_butterflies(nbf, ws->U, ws->V, ws->Wr, ws->Wi, ws->Y0, ws->Y1);
         } else {
             for (int beta = 0; beta < nbf / m; beta++) {
                 int b0 = beta * m;

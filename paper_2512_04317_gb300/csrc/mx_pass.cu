@@ -156,6 +156,26 @@ __device__ __forceinline__ void fp16_butterfly_pair(float2* A, int b0, int nb, i
     }
 }
 
+// FP32 reference ablation: the twiddle product and u +- wv in FP32, every
+// operation rounded once (the intrinsics are never contracted into an FMA).
+__device__ __forceinline__ void fp32_butterfly_pair(float2* A, int b0, int nb, int h,
+                                                    const float2* __restrict__ tw) {
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int b = b0 + 32 * r;
+        if (b >= nb) continue;
+        const int j = b & (h - 1);
+        const int iu = 2 * b - j, iv = iu + h;
+        const float2 u = A[MX_BND(iu, 2 * nb)];
+        const float2 v = A[MX_BND(iv, 2 * nb)];
+        const float2 w = __ldg(tw + (h - 1) + j);
+        const float pr = __fsub_rn(__fmul_rn(w.x, v.x), __fmul_rn(w.y, v.y));
+        const float pi = __fadd_rn(__fmul_rn(w.x, v.y), __fmul_rn(w.y, v.x));
+        A[MX_BND(iu, 2 * nb)] = make_float2(__fadd_rn(u.x, pr), __fadd_rn(u.y, pi));
+        A[MX_BND(iv, 2 * nb)] = make_float2(__fsub_rn(u.x, pr), __fsub_rn(u.y, pi));
+    }
+}
+
 __device__ __forceinline__ float to_fp16(float x) { return __half2float(__float2half_rn(x)); }
 
 __global__ void __launch_bounds__(kPassThreads)
@@ -176,7 +196,7 @@ pass_kernel(PassArgs a) {
 
     // load (with the Alg. 1 prescale on the first pass) in bit-reversed order
     const float pre = a.prologue == PRO_PRESCALE ? exp2i(stp->k) : 1.0f;
-    const bool fp16 = a.fmt == MXFFT_FP16;
+    const bool fp16 = a.fmt == MXFFT_FP16, fp32 = a.fmt == MXFFT_FP32_REF;
     const int total = tpc * n;
     for (int idx = tid; idx < total; idx += nthr) {
         int t, i;
@@ -209,6 +229,7 @@ pass_kernel(PassArgs a) {
             const int t = task / sb_per;
             const int sb = task - t * sb_per;
             if (fp16) fp16_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.tw);
+            else if (fp32) fp32_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.tw);
             else mx_butterfly_pair(sm + t * n, sb * 64 + lane, nb, h, a.m, a.tw, a.tws, a.fp);
         }
         __syncthreads();

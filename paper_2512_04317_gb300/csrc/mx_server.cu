@@ -289,7 +289,7 @@ int mxfft_server_create(const mxfft_server_config* cfg, mxfft_server_t* out) {
 
 int mxfft_server_submit(mxfft_server_t S, const mxfft_request* r) {
     if (!S || !r) return MXFFT_ERR_INVALID;
-    if (!pow2_in(r->n0, 2, 2048) || !pow2_in(r->n1, 2, 2048) || r->format < 0 || r->format > MXFFT_FP16 ||
+    if (!pow2_in(r->n0, 2, 2048) || !pow2_in(r->n1, 2, 2048) || r->format < 0 || r->format > MXFFT_FP32_REF ||
         !pow2_in(r->k, 2, 128) || r->op < 0 || r->op > 3 || r->slices < 1 || !r->host_in ||
         r->reserved != 0 || (!r->host_out && !r->host_rss))
         return MXFFT_ERR_INVALID;

@@ -55,6 +55,7 @@ bool fmt_host(int code, FmtHost* f) {
         case MXFFT_E3M2: *f = {4, -2, 2, 28.0}; return true;
         case MXFFT_E2M1: *f = {2, 0, 1, 6.0}; return true;
         case MXFFT_FP16: *f = {15, -14, 10, 65504.0}; return true;   // IEEE binary16
+        case MXFFT_FP32_REF: *f = {127, -126, 23, 3.4028234663852886e38}; return true;   // binary32
         default: return false;
     }
 }
@@ -138,7 +139,7 @@ void build_twiddles(int n, int m, const FmtHost& f, std::vector<float2>& fwd,
             int s = (ex - 1) - f.emax;
             if (s < -127) s = -127;
             if (s > 127) s = 127;
-            if (plain) s = 0;   // FP16 control: binary16 values, no block scale
+            if (plain) s = 0;   // FP16 control / FP32 ablation: plain values, no block scale
             for (int jj = 0; jj < bl; jj++) {
                 const double xr = q_host(std::ldexp(cs[jj], -s), f);
                 const double xi = q_host(std::ldexp(-sn[jj], -s), f);
@@ -641,7 +642,9 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
     p->t_exp = t_exp;
     // tail floor of Alg. 1: 2^-12 for e5m2, 2^-10 for the other MX formats; the
     // FP16 control uses binary16's smallest magnitude, 2^-24
-    p->taumin_exp = format == MXFFT_E5M2 ? -12 : (format == MXFFT_FP16 ? -24 : -10);
+    // FP32 reference ablation: binary32's smallest normal, 2^-126
+    p->taumin_exp = format == MXFFT_E5M2 ? -12
+                    : (format == MXFFT_FP16 ? -24 : (format == MXFFT_FP32_REF ? -126 : -10));
     p->kmin = -126;
     p->kmax = 126;
     p->fused2d = 0;
@@ -659,7 +662,7 @@ int mxfft_plan(int n0, int n1, int format, int k, float tau, float target, mxfft
         const int n = axis == 0 ? n0 : n1;
         std::vector<float2> fw, iv;
         std::vector<int8_t> sw;
-        build_twiddles(n, p->m[axis], f, fw, iv, sw, format == MXFFT_FP16);
+        build_twiddles(n, p->m[axis], f, fw, iv, sw, format == MXFFT_FP16 || format == MXFFT_FP32_REF);
         for (int d = 0; d < 2 && rc == MXFFT_OK; d++) {
             const std::vector<float2>& t = d == 0 ? fw : iv;
             rc = cuda_status(plan_malloc((void**)&p->d_tw[axis][d], sizeof(float2) * t.size()));

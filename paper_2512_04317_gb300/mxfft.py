@@ -21,7 +21,7 @@ MXFFT_ERR_CUDA = 4
 MXFFT_ERR_NONFINITE = 5
 MXFFT_ERR_TIMEOUT = 6
 
-FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5}
+FORMATS = {"e4m3": 0, "e5m2": 1, "e2m3": 2, "e3m2": 3, "e2m1": 4, "fp16": 5, "fp32": 6}
 OPT_TAU_MIN, OPT_K_MIN, OPT_K_MAX, OPT_GENERIC, OPT_PATH, OPT_TEST_STALL, OPT_FUSED2D, OPT_FOLD_STATS = range(8)
 
 OPS = {"forward": 0, "inverse": 1, "roundtrip": 2, "roundtrip_fused": 3}

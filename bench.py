@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=0,
                     help="smaller case of a workload (profiling): about this many slices")
     ap.add_argument("--serving-requests", type=int, default=2000)
-    ap.add_argument("--fmt", choices=["e4m3", "e5m2", "e2m3", "e3m2", "e2m1", "fp16"], default=None,
+    ap.add_argument("--fmt", choices=["e4m3", "e5m2", "e2m3", "e3m2", "e2m1", "fp16", "fp32"], default=None,
                     help="element format instead of the workload's (format / block-size sweeps)")
     ap.add_argument("--k", type=int, default=0,
                     help="MX block size k instead of the workload's (power of two, 2..128)")
@@ -139,6 +139,8 @@ def dtype_label(fmt):
     """The arithmetic the path computes in: MX element format + FP32."""
     if fmt == "fp16":
         return "fp16 products, f32 accumulate"
+    if fmt == "fp32":
+        return "f32 (reference ablation, no quantisation)"
     kind = {"e4m3": "mxfp8", "e5m2": "mxfp8", "e2m3": "mxfp6", "e3m2": "mxfp6",
             "e2m1": "mxfp4"}[fmt]
     return f"{kind}-{fmt} elements, e8m0 block scales, f32 accumulate"
@@ -533,7 +535,7 @@ def rss_image_metrics(torch, n=256, slices=2, coils=8):
     refs = {"forward": rss64(np.fft.fft2(ksp.astype(np.complex128))),
             "roundtrip": rss64(img.astype(np.complex128))}
     out = {}
-    for fmt in ("e4m3", "e5m2", "fp16"):
+    for fmt in ("e4m3", "e5m2", "fp16", "fp32"):
         for op, x in (("forward", ksp), ("roundtrip", img)):
             with mxfft.Plan(n, n, fmt, 32) as p:
                 y = getattr(p, op)(torch.from_numpy(x).cuda())

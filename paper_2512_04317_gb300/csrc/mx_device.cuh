@@ -219,6 +219,34 @@ struct StatAcc {
             atomicAdd(&sh_hist[bin], 1u);
         }
     }
+    // The same accumulation with one shared atomic per counted point (no
+    // match), into a histogram that only this warp updates.
+    __device__ __forceinline__ void add_plain(float re, float im, uint32_t* wh) {
+        const uint32_t br = __float_as_uint(re) & 0x7fffffffu;
+        const uint32_t bi = __float_as_uint(im) & 0x7fffffffu;
+        const uint32_t lo = (uint32_t)(127 - 62) << 23, hi = (uint32_t)(127 + 63) << 23;
+        int bin = -1;
+        if (min(br - 1u, bi - 1u) >= lo - 1u && max(br, bi) < hi) {
+            const uint32_t sb = __float_as_uint(__fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im)));
+            if (sb) {
+                smax_bits = max(smax_bits, sb);
+                nnz++;
+                bin = (((int)(sb >> 23) - 127) >> 1) + 149;
+            }
+        } else if (max(br, bi) >= 0x7f800000u) {
+            nonfinite = 1;
+        } else {
+            const uint32_t mb = __float_as_uint(mag_c3(re, im));
+            if (!is_finite_bits(mb)) {
+                nonfinite = 1;
+            } else if (mb != 0) {
+                amax_bits = max(amax_bits, mb);
+                nnz++;
+                bin = ilogb_bits(mb) + 149;
+            }
+        }
+        if (bin >= 0) atomicAdd(&wh[bin], 1u);
+    }
     // bits of max |x| over everything added
     __device__ __forceinline__ uint32_t amax() const {
         return max(amax_bits, __float_as_uint(__fsqrt_rn(__uint_as_float(smax_bits))));

@@ -26,9 +26,11 @@
 // slice), which is exactly 256 vectors per radix-16 stage, so a CTA of 256
 // threads runs each stage as one round of two MMAs (rows 0-127 and 128-255,
 // accumulators in tensor-memory columns 0-31 and 32-63); thread i owns
-// vector i.  CTAs are persistent: each walks a contiguous range of tiles
-// (mostly of one slice, whose buffers and exponent it resolves once; the
-// columns pass of n = 2048 walks every grid-th tile instead) and
+// vector i (the autotuner may pick, for n <= 1024, CTAs of 128 threads on
+// tiles of 2048 points, one MMA per round: see Cta).  CTAs are persistent:
+// each walks a contiguous range of tiles (mostly of one slice, whose buffers
+// and exponent it resolves once; a columns pass with tiles two columns wide
+// walks every grid-th tile instead) and
 // copies the next tile into its second shared buffer (cp.async, 16 B per
 // thread and copy) while it transforms the current one, so that HBM reads
 // overlap the MMA rounds.  The shared layouts are padded so that every

@@ -46,14 +46,14 @@ __device__ __forceinline__ void stats_cta(const float2* __restrict__ x, int npts
     stats_flush_and_select(acc, sh_hist, sh_misc, st, ctas, kp);
 }
 
-__global__ void __launch_bounds__(kStatsThreads, 6)
+__global__ void __launch_bounds__(kStatsThreads, 8)
 stats_kernel(const float2* __restrict__ x, int npts, SliceStats* __restrict__ st,
              KParams kp, uint32_t ctas_per_slice) {
     const int slice = blockIdx.y;
     stats_cta(x + (size_t)slice * npts, npts, blockIdx.x, st + slice, kp, ctas_per_slice);
 }
 
-__global__ void __launch_bounds__(kStatsThreads, 6)
+__global__ void __launch_bounds__(kStatsThreads, 8)
 stats_ref_kernel(const StatsRef* __restrict__ refs, const int2* __restrict__ cta_tab) {
     const int2 w = cta_tab[blockIdx.x];
     const StatsRef r = refs[w.x];

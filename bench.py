@@ -694,7 +694,7 @@ def main():
         fused = {"value": job_throughput_mpts(world, pts, TRANSFORMS_PER_STEP, args.steps, tf_ms),
                  "unit": "Mpts/s", "ms_per_step": tf_ms / args.steps,
                  "speedup_vs_separate_round_trip": ms_per_step / (tf_ms / args.steps),
-                 "launches_per_step": 6,
+                 "launches_per_step": engine.launches_per_run(),
                  "step": "forward of the k-space batch + fused round trip of the image batch"}
 
     # ---- the other path on the same workload and step, timed the same way:

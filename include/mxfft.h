@@ -114,8 +114,9 @@ typedef enum {
                                trip's forward columns pass accumulates the inverse's Alg. 1
                                statistics of the values it stores (n0 != 2048), so no
                                statistics pass re-reads the forward output; same exponents
-                               and results.  Off by default: on this pass the per-value
-                               histogram work costs more time than the pass it removes. */
+                               and results.  Off by default: the histogram work lands on
+                               the pass's critical path and costs about as much time as
+                               the statistics pass it removes (more at 512x512). */
 } mxfft_option;
 
 typedef struct mxfft_plan_s *mxfft_plan_t;

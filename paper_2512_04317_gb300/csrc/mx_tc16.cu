@@ -359,21 +359,35 @@ tc16_pass_kernel(const Args a) {
     // the slice's tiles selects k).  Not for the strided n = 2048 columns
     // pass, whose tiles of a slice are spread over all CTAs.
     constexpr bool fold = FOLD && DIM == 0 && !kStrided;
+    // 8 histograms by lane (a shared atomic per counted point: lane l adds
+    // into copy l % 8, so at most 4 lanes of one atomic meet in a copy, where
+    // neighbouring columns, whose values often share a bin, sit in
+    // neighbouring lanes), summed into so_hist at each flush
+    constexpr int kCopies = fold ? 8 : 1;
+    __shared__ uint32_t so_whist[kCopies][fold ? kHistBins : 1];
     __shared__ uint32_t so_hist[fold ? kHistBins : 1];
     __shared__ uint32_t so_misc[4];
+    uint32_t* so_wh = so_whist[tid % kCopies];
     StatAcc oacc;
     int seg_slice = -1, seg_tiles = 0;
     SliceStats* seg_st = nullptr;
     if (fold)
-        for (int b = tid; b < kHistBins; b += NT) so_hist[b] = 0;
-    (void)seg_slice; (void)seg_tiles; (void)so_misc;
+        for (int b = tid; b < kCopies * kHistBins; b += NT) (&so_whist[0][0])[b] = 0;
+    (void)seg_slice; (void)seg_tiles; (void)so_misc; (void)so_wh;
     auto flush_out = [&]() {
         if (seg_st) {
+            __syncthreads();
+            for (int b = tid; b < kHistBins; b += NT) {
+                uint32_t c = 0;
+#pragma unroll
+                for (int w = 0; w < kCopies; w++) c += so_whist[w][b];
+                so_hist[b] = c;
+            }
             __syncthreads();
             stats_flush_and_select_n(oacc, so_hist, so_misc, seg_st, (uint32_t)seg_tiles,
                                      (uint32_t)per_slice, a.kp);
             __syncthreads();
-            for (int b = tid; b < kHistBins; b += NT) so_hist[b] = 0;
+            for (int b = tid; b < kCopies * kHistBins; b += NT) (&so_whist[0][0])[b] = 0;
             oacc = StatAcc();
             __syncthreads();
         }
@@ -490,8 +504,8 @@ tc16_pass_kernel(const Args a) {
                 const float2 v0 = scale_out ? scale2(y[k2], post) : y[k2];        // X[2 p + 16 k2]
                 const float2 v1 = scale_out ? scale2(y[8 + k2], post) : y[8 + k2];  // X[2 p + 1 + 16 k2]
                 if (fold_tile) {
-                    oacc.add<true>(v0.x, v0.y, so_hist);
-                    oacc.add<true>(v1.x, v1.y, so_hist);
+                    oacc.add_plain(v0.x, v0.y, so_wh);
+                    oacc.add_plain(v1.x, v1.y, so_wh);
                 }
                 const int e = 2 * p + 16 * k2;
                 if (DIM == 1) {
@@ -536,7 +550,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int k = 0; k < 16; k++) {
                     const float2 val = scale_out ? scale2(y[k], post) : y[k];
-                    if (fold_tile) oacc.add<true>(val.x, val.y, so_hist);
+                    if (fold_tile) oacc.add_plain(val.x, val.y, so_wh);
                     const int e = k1 + 16 * k;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + e, slice_pts)] = val;
                     else out[MX_BND((size_t)e * a.n1 + t0 + t, slice_pts)] = val;
@@ -607,7 +621,7 @@ tc16_pass_kernel(const Args a) {
 #pragma unroll
                 for (int k22 = 0; k22 < 4; k22++) {
                     const float2 val = scale_out ? scale2(X[k22], post) : X[k22];
-                    if (fold_tile) oacc.add<true>(val.x, val.y, so_hist);
+                    if (fold_tile) oacc.add_plain(val.x, val.y, so_wh);
                     const int eo = k1 + 16 * k21 + 256 * k22;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + eo, slice_pts)] = val;
                     else out[MX_BND((size_t)eo * a.n1 + t0 + t, slice_pts)] = val;
@@ -685,7 +699,7 @@ tc16_pass_kernel(const Args a) {
                     float2 X = k < 4 ? make_float2(__fadd_rn(E[k4].x, P[k4].x), __fadd_rn(E[k4].y, P[k4].y))
                                      : make_float2(__fsub_rn(E[k4].x, P[k4].x), __fsub_rn(E[k4].y, P[k4].y));
                     if (scale_out) X = scale2(X, post);
-                    if (fold_tile) oacc.add<true>(X.x, X.y, so_hist);
+                    if (fold_tile) oacc.add_plain(X.x, X.y, so_wh);
                     const int eo = k1 + 16 * k21 + 256 * k;
                     if (DIM == 1) out[MX_BND((size_t)(t0 + t) * a.n1 + eo, slice_pts)] = X;
                     else out[MX_BND((size_t)eo * a.n1 + t0 + t, slice_pts)] = X;
@@ -721,8 +735,8 @@ tc16_pass_kernel(const Args a) {
                 float2 s1 = make_float2(__fsub_rn(p.x, q.x), __fsub_rn(p.y, q.y));
                 if (scale_out) { s0 = scale2(s0, post); s1 = scale2(s1, post); }
                 if (fold_tile) {
-                    oacc.add<true>(s0.x, s0.y, so_hist);
-                    oacc.add<true>(s1.x, s1.y, so_hist);
+                    oacc.add_plain(s0.x, s0.y, so_wh);
+                    oacc.add_plain(s1.x, s1.y, so_wh);
                 }
                 const int e0 = k1 + 16 * k21, e1 = e0 + 256;
                 if (DIM == 1) {

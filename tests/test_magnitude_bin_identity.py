@@ -39,3 +39,19 @@ def test_max_commutes_with_rounded_sqrt():
     bits = rng.integers((127 - 124) << 23, (127 + 127) << 23, size=(20000, 33), dtype=np.uint32)
     s = bits.view(np.float32)
     np.testing.assert_array_equal(np.sqrt(s).max(axis=1), np.sqrt(s.max(axis=1)))
+
+
+def test_byte_offset_of_the_bin():
+    # the statistics kernel's two-point body addresses the histogram word of
+    # bin floor(floor(log2 s) / 2) + 149 as the byte offset
+    # ((bits(s) >> 22) + 342) & ~3; every normal s (all biased exponents,
+    # both values of the top significand bit, either end of the significand)
+    e = np.arange(1, 255, dtype=np.uint32)
+    top = np.array([0, 1 << 22, (1 << 23) - 1, 1], dtype=np.uint32)
+    bits = ((e[:, None] << np.uint32(23)) | top[None, :]).ravel().astype(np.uint32)
+    want = _bin_via_s(bits.view(np.float32)) + 149
+    got = (((bits >> np.uint32(22)).astype(np.int64) + 342) & ~3) // 4
+    np.testing.assert_array_equal(got, want)
+    assert want.min() >= 0 and want.max() < 277
+    # a shift by 23 instead of 22 fails
+    assert not np.array_equal((((bits >> np.uint32(23)).astype(np.int64) + 342) & ~3) // 4, want)

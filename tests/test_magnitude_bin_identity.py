@@ -55,3 +55,30 @@ def test_byte_offset_of_the_bin():
     assert want.min() >= 0 and want.max() < 277
     # a shift by 23 instead of 22 fails
     assert not np.array_equal((((bits >> np.uint32(23)).astype(np.int64) + 342) & ~3) // 4, want)
+
+
+def test_two_point_range_test_equals_both_point_tests():
+    # the two-point body takes its fast path when min over the four
+    # components of (|bits| - 1) (wrapping) is >= lo - 1 and their max is
+    # < hi; that must hold exactly when each point passes its own test
+    # (each component zero or of magnitude in [2^-62, 2^63))
+    lo, hi = (127 - 62) << 23, (127 + 63) << 23
+    edge = np.array([0, 1, lo - 1, lo, lo + 1, hi - 1, hi, hi + 1, 0x7f800000, 0x7fc00000,
+                     127 << 23, 0x007fffff], dtype=np.uint32)
+    rng = np.random.default_rng(11)
+    comp = np.concatenate([edge, rng.integers(0, 0x7fffffff, 64, dtype=np.uint32)])
+    q = rng.integers(0, len(comp), size=(200_000, 4))
+    u = comp[q]                                           # |bits| of re0, im0, re1, im1
+    um1 = u - np.uint32(1)
+
+    def point_ok(a, b):
+        return (np.minimum(um1[:, a], um1[:, b]) >= lo - 1) & (np.maximum(u[:, a], u[:, b]) < hi)
+
+    def in_range(c):
+        return (u[:, c] == 0) | ((u[:, c] >= lo) & (u[:, c] < hi))
+
+    for a, b in ((0, 1), (2, 3)):
+        np.testing.assert_array_equal(point_ok(a, b), in_range(a) & in_range(b))
+    pair = (um1.min(axis=1) >= lo - 1) & (u.max(axis=1) < hi)
+    np.testing.assert_array_equal(pair, point_ok(0, 1) & point_ok(2, 3))
+    assert pair.any() and not pair.all()

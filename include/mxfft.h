@@ -346,6 +346,9 @@ int mxfft_engine_get_status(mxfft_engine_t e, int *device_flags, int32_t *k_out,
  *   enqueued (for a graph replay: the kernels of the captured graph); 0
  *   before the first run.  MXFFT_ERR_INVALID for NULL arguments. */
 int mxfft_engine_launches(mxfft_engine_t e, int *launches);
+/* mxfft_engine_destroy -- waits for the engine's last run, then frees its
+ *   graphs, plans, events, streams and buffers.  Unlike mxfft_destroy, NULL
+ *   returns MXFFT_ERR_INVALID. */
 int mxfft_engine_destroy(mxfft_engine_t e);
 
 /* ======================================================================
@@ -425,7 +428,8 @@ typedef struct mxfft_server_s *mxfft_server_t;
  *   timeout_s has passed (MXFFT_ERR_TIMEOUT).
  * mxfft_server_stats -- counters: batches launched, peak device bytes held by
  *   admitted requests (never above the budget), the budget.
- * mxfft_server_destroy -- finish outstanding work, stop the thread, free.
+ * mxfft_server_destroy -- finish outstanding work, stop the thread, free
+ *   (NULL returns MXFFT_ERR_INVALID).
  */
 int mxfft_server_create(const mxfft_server_config *cfg, mxfft_server_t *out);
 int mxfft_server_submit(mxfft_server_t s, const mxfft_request *r);
